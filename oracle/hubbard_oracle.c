@@ -1,0 +1,445 @@
+/*
+ * Hubbard-model HMC oracle: a plain, slow, obviously correct FP64 CPU
+ * restatement of the method of arXiv:1007.3432 (Wendt, Drut, Laehde).
+ *
+ * TEST INFRASTRUCTURE ONLY.  The test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may build, load and call this file;
+ * nothing on the product path does, and it shares no code, header, table or
+ * helper with the CUDA library.  It is single-threaded and untuned on purpose:
+ * every function is written for a reader checking it against the paper, with
+ * loops over lattice sites and explicit coordinates.
+ *
+ * Readings of passages the paper leaves open (each is listed with its
+ * justification in the design notes of the repository):
+ *   R1 (Eq. (10), coefficients A-D unspecified): the diagonal block is the
+ *      linearised 1 + dtau*K, i.e. 1 on the site and -h = -t*dtau on each of
+ *      the 2d spatial neighbours; the time link into slice tau carries
+ *      L(n, tau-1) = -(1 + A sin sigma(n, tau-1)).
+ *   R2 (Eq. (6), HS transform unspecified): compact form 1 + A sin(sigma),
+ *      flat measure, S_g = 0.
+ *   R3 (Eq. (7)): the link from slice tau' to tau'+1 carries the source slice's
+ *      field; its sign is -1 except on the wrap link N_tau-1 -> 0, which is +1
+ *      (the +B_{N_tau} corner block: antiperiodic in time).
+ *   R4 (Eqs. (11)-(12)): n_pf real Gaussian pseudofermion components,
+ *      chi_a = M^T xi_a, S_pf = 1/2 sum_a chi_a^T Q^{-1} chi_a.  Two components
+ *      give the weight det Q = (det M)^2 of Eq. (6).
+ *   R5 (Sec. 4.1, CG): x0 = 0; stop on the recursive residual, then confirm
+ *      with the true residual; if the check fails, the residual is replaced by
+ *      the true one and the iteration continues.
+ *   R6 (Sec. 4.1, MD): leapfrog with step dt; Metropolis accepts iff
+ *      u < exp(-dH).
+ *   R7 (random numbers, not specified by the paper): Philox4x64-10 with
+ *      counter (block, tag | a<<8, traj, chain) and key (seed, 0);
+ *      tags 0 sigma init, 1 momenta, 2 pseudofermion sources, 3 Metropolis.
+ */
+#include "hubbard_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Lattice geometry.                                                         */
+/* ------------------------------------------------------------------------ */
+
+static long spatial_volume(const oracle_lattice *lat)
+{
+    long v = 1;
+    for (int j = 0; j < lat->d; ++j) v *= lat->nx;
+    return v;
+}
+
+long oracle_nsites(const oracle_lattice *lat)
+{
+    return spatial_volume(lat) * lat->ntau;
+}
+
+/* Index of site (n, tau) with n = (c[0], ..., c[d-1]), c[0] = x fastest. */
+static long site_index(const oracle_lattice *lat, const int *c, int tau)
+{
+    long s = 0;
+    for (int j = lat->d - 1; j >= 0; --j) s = s * lat->nx + c[j];
+    return s + (long)tau * spatial_volume(lat);
+}
+
+/* Inverse of site_index. */
+static void site_coords(const oracle_lattice *lat, long i, int *c, int *tau)
+{
+    long v = spatial_volume(lat);
+    *tau = (int)(i / v);
+    long s = i % v;
+    for (int j = 0; j < lat->d; ++j) {
+        c[j] = (int)(s % lat->nx);
+        s /= lat->nx;
+    }
+}
+
+/* Sum of x over the 2d spatial nearest neighbours of (c, tau), periodic in
+ * every spatial direction (Sec. 2: "periodic in the spatial directions").
+ * For N_x = 2 the two neighbours along a direction coincide and both count,
+ * exactly as the Kronecker deltas of Eq. (9) do. */
+static double neighbour_sum(const oracle_lattice *lat, const double *x, const int *c, int tau)
+{
+    int cc[3];
+    double s = 0.0;
+    for (int j = 0; j < lat->d; ++j) {
+        for (int k = 0; k < lat->d; ++k) cc[k] = c[k];
+        cc[j] = (c[j] + 1) % lat->nx;
+        s += x[site_index(lat, cc, tau)];
+        cc[j] = (c[j] + lat->nx - 1) % lat->nx;
+        s += x[site_index(lat, cc, tau)];
+    }
+    return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Fermion matrix, Sec. 2 Eqs. (7)-(10).                                      */
+/* ------------------------------------------------------------------------ */
+
+/* L(n,tau) for the link from slice tau to slice tau+1 (reading R1-R3):
+ * -(1 + A sin sigma(n,tau)) for tau < N_tau-1 (the -B_j blocks of Eq. (7)) and
+ * +(1 + A sin sigma(n,N_tau-1)) on the wrap link (the +B_{N_tau} corner). */
+void oracle_links(const oracle_lattice *lat, double A, const double *sigma, double *L)
+{
+    long n = oracle_nsites(lat);
+    int c[3], tau;
+    for (long i = 0; i < n; ++i) {
+        site_coords(lat, i, c, &tau);
+        double link = 1.0 + A * sin(sigma[i]);
+        L[i] = (tau == lat->ntau - 1) ? link : -link;
+    }
+}
+
+/* (M x)(n,tau) = x(n,tau) - h sum_{+-j} x(n +- e_j, tau) + L(n,tau-1) x(n,tau-1),
+ * tau-1 taken modulo N_tau (Eq. (10): one temporal link, the site itself and
+ * 2d spatial neighbours; the wrap term is the corner block of Eq. (7)). */
+void oracle_apply_M(const oracle_lattice *lat, double h, const double *L,
+                    const double *x, double *y)
+{
+    long n = oracle_nsites(lat);
+    int c[3], tau;
+    for (long i = 0; i < n; ++i) {
+        site_coords(lat, i, c, &tau);
+        int tprev = (tau + lat->ntau - 1) % lat->ntau;
+        long iprev = site_index(lat, c, tprev);
+        y[i] = x[i] - h * neighbour_sum(lat, x, c, tau) + L[iprev] * x[iprev];
+    }
+}
+
+/* (M^T y)(n,tau) = y(n,tau) - h sum_{+-j} y(n +- e_j, tau) + L(n,tau) y(n,tau+1):
+ * the transpose of Eq. (10); the spatial hopping of Eq. (9) is symmetric. */
+void oracle_apply_MT(const oracle_lattice *lat, double h, const double *L,
+                     const double *x, double *y)
+{
+    long n = oracle_nsites(lat);
+    int c[3], tau;
+    for (long i = 0; i < n; ++i) {
+        site_coords(lat, i, c, &tau);
+        int tnext = (tau + 1) % lat->ntau;
+        long inext = site_index(lat, c, tnext);
+        y[i] = x[i] - h * neighbour_sum(lat, x, c, tau) + L[i] * x[inext];
+    }
+}
+
+/* Q x = M^T (M x), applied as two successive sweeps (Sec. 4.3). */
+void oracle_apply_MTM(const oracle_lattice *lat, double h, const double *L,
+                      const double *x, double *y)
+{
+    long n = oracle_nsites(lat);
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)n);
+    oracle_apply_M(lat, h, L, x, tmp);
+    oracle_apply_MT(lat, h, L, tmp, y);
+    free(tmp);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Conjugate gradient for Q x = b (Sec. 4.1).                               */
+/* ------------------------------------------------------------------------ */
+
+static double dot(long n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (long i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+int oracle_cg(const oracle_lattice *lat, double h, const double *L, const double *b,
+              double *x, double tol, int maxit, int *iterations, double *true_relres)
+{
+    long n = oracle_nsites(lat);
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    double *p = (double *)malloc(sizeof(double) * (size_t)n);
+    double *q = (double *)malloc(sizeof(double) * (size_t)n);
+    int status = -4, k = 0;
+    double bnorm = sqrt(dot(n, b, b));
+
+    for (long i = 0; i < n; ++i) {
+        x[i] = 0.0;
+        r[i] = b[i];
+        p[i] = b[i];
+    }
+    *true_relres = 0.0;
+    if (bnorm == 0.0) {
+        status = 0;
+        goto done;
+    }
+    double rr = dot(n, r, r);
+    *true_relres = 1.0;
+    for (k = 1; k <= maxit; ++k) {
+        oracle_apply_MTM(lat, h, L, p, q);
+        double alpha = rr / dot(n, p, q);
+        for (long i = 0; i < n; ++i) {
+            x[i] += alpha * p[i];
+            r[i] -= alpha * q[i];
+        }
+        double rr_new = dot(n, r, r);
+        if (sqrt(rr_new) <= tol * bnorm) {
+            /* Confirm with the true residual b - Q x (reading R5). */
+            oracle_apply_MTM(lat, h, L, x, q);
+            for (long i = 0; i < n; ++i) r[i] = b[i] - q[i];
+            rr_new = dot(n, r, r);
+            *true_relres = sqrt(rr_new) / bnorm;
+            if (sqrt(rr_new) <= tol * bnorm) {
+                status = 0;
+                break;
+            }
+        }
+        double beta = rr_new / rr;
+        rr = rr_new;
+        for (long i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+    }
+    if (status != 0) {
+        oracle_apply_MTM(lat, h, L, x, q);
+        for (long i = 0; i < n; ++i) r[i] = b[i] - q[i];
+        *true_relres = sqrt(dot(n, r, r)) / bnorm;
+        k = maxit;
+    }
+done:
+    *iterations = k;
+    free(r);
+    free(p);
+    free(q);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x64-10 counter-based generator (Salmon, Moraes, Dror, Shaw,        */
+/* "Parallel random numbers: as easy as 1, 2, 3", SC'11).                    */
+/* ------------------------------------------------------------------------ */
+
+void oracle_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    const uint64_t mult0 = 0xD2E7470EE14C6C93ULL, mult1 = 0xCA5A826395121157ULL;
+    const uint64_t weyl0 = 0x9E3779B97F4A7C15ULL, weyl1 = 0xBB67AE8584CAA73BULL;
+    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += weyl0;
+            k1 += weyl1;
+        }
+        unsigned __int128 prod0 = (unsigned __int128)mult0 * c0;
+        unsigned __int128 prod1 = (unsigned __int128)mult1 * c2;
+        uint64_t hi0 = (uint64_t)(prod0 >> 64), lo0 = (uint64_t)prod0;
+        uint64_t hi1 = (uint64_t)(prod1 >> 64), lo1 = (uint64_t)prod1;
+        uint64_t n0 = hi1 ^ c1 ^ k0;
+        uint64_t n1 = lo1;
+        uint64_t n2 = hi0 ^ c3 ^ k1;
+        uint64_t n3 = lo0;
+        c0 = n0;
+        c1 = n1;
+        c2 = n2;
+        c3 = n3;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+/* 53-bit uniform in [0, 1) from the top bits of a 64-bit word. */
+static double unit_uniform(uint64_t w)
+{
+    return (double)(w >> 11) * (1.0 / 9007199254740992.0);
+}
+
+static void philox_block(uint64_t seed, int tag, int a, uint64_t traj, uint64_t chain,
+                         uint64_t block, uint64_t w[4])
+{
+    uint64_t ctr[4] = {block, (uint64_t)tag | ((uint64_t)a << 8), traj, chain};
+    uint64_t key[2] = {seed, 0};
+    oracle_philox4x64(ctr, key, w);
+}
+
+/* Element i: Box-Muller on the word pair (2j, 2j+1), j = (i >> 1) & 1, of
+ * block i >> 2; even i takes the cosine branch, odd i the sine branch. */
+void oracle_gaussian(uint64_t seed, int tag, int a, uint64_t traj, uint64_t chain,
+                     long n, double *out)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    for (long i = 0; i < n; ++i) {
+        uint64_t w[4];
+        philox_block(seed, tag, a, traj, chain, (uint64_t)i >> 2, w);
+        int j = (int)((i >> 1) & 1);
+        double u1 = unit_uniform(w[2 * j]);
+        double u2 = unit_uniform(w[2 * j + 1]);
+        double rad = sqrt(-2.0 * log(1.0 - u1));
+        out[i] = (i & 1) ? rad * sin(two_pi * u2) : rad * cos(two_pi * u2);
+    }
+}
+
+double oracle_uniform(uint64_t seed, int tag, uint64_t traj, uint64_t chain, long i)
+{
+    uint64_t w[4];
+    philox_block(seed, tag, 0, traj, chain, (uint64_t)i >> 2, w);
+    return unit_uniform(w[i & 3]);
+}
+
+/* sigma ~ U[-pi, pi) (reading R2), tag 0, trajectory word 0. */
+void oracle_init_field(uint64_t seed, uint64_t chain, long n, double *sigma)
+{
+    const double pi = 3.14159265358979323846264338328;
+    for (long i = 0; i < n; ++i)
+        sigma[i] = -pi + 2.0 * pi * oracle_uniform(seed, 0, 0, chain, i);
+}
+
+/* ------------------------------------------------------------------------ */
+/* HMC phi-algorithm, Sec. 4.1.                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Pseudofermion heatbath (Eqs. (11)-(12), reading R4): chi_a = M^T xi_a with
+ * xi_a ~ N(0,1), so chi_a has covariance Q and S_pf(sigma) = 1/2 |xi|^2. */
+void oracle_heatbath(const oracle_lattice *lat, const oracle_params *p,
+                     const double *sigma, uint64_t traj, double *chi)
+{
+    long n = oracle_nsites(lat);
+    double *L = (double *)malloc(sizeof(double) * (size_t)n);
+    double *xi = (double *)malloc(sizeof(double) * (size_t)n);
+    oracle_links(lat, p->A, sigma, L);
+    for (int a = 0; a < p->n_pf; ++a) {
+        oracle_gaussian(p->seed, 2, a, traj, p->chain, n, xi);
+        oracle_apply_MT(lat, p->t * p->dtau, L, xi, chi + (long)a * n);
+    }
+    free(L);
+    free(xi);
+}
+
+/* S_pf = 1/2 sum_a chi_a^T Q^{-1} chi_a (Eq. (12) with real components). */
+double oracle_action(const oracle_lattice *lat, const oracle_params *p,
+                     const double *sigma, const double *chi, int *iters, double *relres,
+                     int *status)
+{
+    long n = oracle_nsites(lat);
+    double h = p->t * p->dtau;
+    double *L = (double *)malloc(sizeof(double) * (size_t)n);
+    double *x = (double *)malloc(sizeof(double) * (size_t)n);
+    double S = 0.0;
+    oracle_links(lat, p->A, sigma, L);
+    for (int a = 0; a < p->n_pf; ++a) {
+        int it;
+        double rr;
+        int st = oracle_cg(lat, h, L, chi + (long)a * n, x, p->cg_tol, p->cg_maxit, &it, &rr);
+        if (st != 0) *status = st;
+        *iters += it;
+        if (rr > *relres) *relres = rr;
+        S += 0.5 * dot(n, chi + (long)a * n, x);
+    }
+    free(L);
+    free(x);
+    return S;
+}
+
+/* F(n,tau) = dS_pf / dsigma(n,tau).  With x_a = Q^{-1} chi_a and y_a = M x_a,
+ * dS/dsigma = -sum_a y_a^T (dM/dsigma) x_a, and sigma(n,tau) enters M only
+ * through the link L(n,tau) at row (n,tau+1), column (n,tau), whose derivative
+ * is s(tau) A cos sigma(n,tau) with s = -1, or +1 on the wrap link. */
+void oracle_force(const oracle_lattice *lat, const oracle_params *p, const double *sigma,
+                  const double *chi, double *F, int *iters, double *relres, int *status)
+{
+    long n = oracle_nsites(lat);
+    double h = p->t * p->dtau;
+    double *L = (double *)malloc(sizeof(double) * (size_t)n);
+    double *x = (double *)malloc(sizeof(double) * (size_t)n);
+    double *y = (double *)malloc(sizeof(double) * (size_t)n);
+    int c[3], tau;
+    oracle_links(lat, p->A, sigma, L);
+    for (long i = 0; i < n; ++i) F[i] = 0.0;
+    for (int a = 0; a < p->n_pf; ++a) {
+        int it;
+        double rr;
+        int st = oracle_cg(lat, h, L, chi + (long)a * n, x, p->cg_tol, p->cg_maxit, &it, &rr);
+        if (st != 0) *status = st;
+        *iters += it;
+        if (rr > *relres) *relres = rr;
+        oracle_apply_M(lat, h, L, x, y);
+        for (long i = 0; i < n; ++i) {
+            site_coords(lat, i, c, &tau);
+            long inext = site_index(lat, c, (tau + 1) % lat->ntau);
+            double s = (tau == lat->ntau - 1) ? 1.0 : -1.0;
+            F[i] -= y[inext] * s * p->A * cos(sigma[i]) * x[i];
+        }
+    }
+    free(L);
+    free(x);
+    free(y);
+}
+
+/* Leapfrog integration of d sigma/dt = pi, d pi/dt = -F (reading R6):
+ * half momentum step, n_md full sigma steps with full momentum steps between
+ * them, half momentum step at the end; n_md + 1 force evaluations. */
+void oracle_leapfrog(const oracle_lattice *lat, const oracle_params *p, double *sigma,
+                     double *pi, const double *chi, int n_md, double dt, int *iters,
+                     double *relres, int *status)
+{
+    long n = oracle_nsites(lat);
+    double *F = (double *)malloc(sizeof(double) * (size_t)n);
+    oracle_force(lat, p, sigma, chi, F, iters, relres, status);
+    for (long i = 0; i < n; ++i) pi[i] -= 0.5 * dt * F[i];
+    for (int k = 1; k <= n_md; ++k) {
+        for (long i = 0; i < n; ++i) sigma[i] += dt * pi[i];
+        oracle_force(lat, p, sigma, chi, F, iters, relres, status);
+        double eps = (k == n_md) ? 0.5 * dt : dt;
+        for (long i = 0; i < n; ++i) pi[i] -= eps * F[i];
+    }
+    free(F);
+}
+
+/* One HMC trajectory (Sec. 4.1): momenta and pseudofermion heatbath,
+ * H0 = 1/2 |pi|^2 + S_pf, leapfrog, H1, Metropolis accept/reject. */
+int oracle_trajectory(const oracle_lattice *lat, const oracle_params *p, double *sigma,
+                      int n_md, double dt, uint64_t traj, oracle_traj_info *info)
+{
+    long n = oracle_nsites(lat);
+    double *pi = (double *)malloc(sizeof(double) * (size_t)n);
+    double *chi = (double *)malloc(sizeof(double) * (size_t)n * (size_t)p->n_pf);
+    double *sigma0 = (double *)malloc(sizeof(double) * (size_t)n);
+    int iters = 0, status = 0;
+    double relres = 0.0;
+
+    memcpy(sigma0, sigma, sizeof(double) * (size_t)n);
+    oracle_gaussian(p->seed, 1, 0, traj, p->chain, n, pi);
+    oracle_heatbath(lat, p, sigma, traj, chi);
+
+    double H0 = 0.5 * dot(n, pi, pi) + oracle_action(lat, p, sigma, chi, &iters, &relres, &status);
+    oracle_leapfrog(lat, p, sigma, pi, chi, n_md, dt, &iters, &relres, &status);
+    double H1 = 0.5 * dot(n, pi, pi) + oracle_action(lat, p, sigma, chi, &iters, &relres, &status);
+
+    double dH = H1 - H0;
+    double u = oracle_uniform(p->seed, 3, traj, p->chain, 0);
+    int accepted = u < exp(-dH);
+    if (!accepted) memcpy(sigma, sigma0, sizeof(double) * (size_t)n);
+
+    info->H0 = H0;
+    info->H1 = H1;
+    info->dH = dH;
+    info->u = u;
+    info->accepted = accepted;
+    info->cg_iterations = iters;
+    info->n_solves = p->n_pf * (n_md + 3);
+    info->max_relres = relres;
+    info->status = status;
+    free(pi);
+    free(chi);
+    free(sigma0);
+    return status;
+}

@@ -1,0 +1,423 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+None of these checks re-types an oracle formula: each compares the oracle with
+an independent route to the same number (a closed form, a library routine, a
+finite difference, an exact invariant of the algorithm), chosen so that a
+dropped term, a wrong sign, a wrong slice index or a transposed operand fails
+at least one of them.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+H = 0.05  # h = t * dtau with t = 1, dtau = 0.05
+
+
+def _free_eigs(d, nx, ntau, h, c):
+    """Closed-form spectrum of M for a uniform link factor c = 1 + A sin sigma0.
+
+    Plane waves exp(i k.n + i w tau) with lattice momenta k_j = 2 pi m_j / N_x
+    (periodic, Sec. 2) and antiperiodic Matsubara frequencies
+    w = pi (2m + 1) / N_tau diagonalise M with eigenvalue
+    lambda = 1 - 2h sum_j cos k_j - c exp(-i w)."""
+    eps = []
+    for ms in itertools.product(range(nx), repeat=d):
+        eps.append(1.0 - 2.0 * h * sum(np.cos(2 * np.pi * m / nx) for m in ms))
+    out = []
+    for e in eps:
+        for m in range(ntau):
+            w = np.pi * (2 * m + 1) / ntau
+            out.append(e - c * np.exp(-1j * w))
+    return np.array(out)
+
+
+def _match_spectra(a, b):
+    """Greedy nearest matching of two multisets of complex numbers."""
+    b = list(b)
+    worst = 0.0
+    for z in a:
+        j = int(np.argmin([abs(z - w) for w in b]))
+        worst = max(worst, abs(z - b[j]))
+        b.pop(j)
+    return worst
+
+
+@pytest.mark.parametrize("d,nx,ntau", [(1, 6, 8), (1, 4, 5), (3, 3, 4), (3, 2, 3)])
+@pytest.mark.parametrize("sigma0", [0.0, 0.7])
+def test_uniform_field_spectrum_closed_form(orc, d, nx, ntau, sigma0):
+    A = 0.5
+    lat = orc.lattice(d, nx, ntau)
+    n = orc.nsites(lat)
+    L = orc.links(lat, A, np.full(n, sigma0))
+    M = orc.dense(lat, H, L, "M")
+    got = np.linalg.eigvals(M)
+    want = _free_eigs(d, nx, ntau, H, 1.0 + A * np.sin(sigma0))
+    assert _match_spectra(got, want) < 1e-10
+
+
+@pytest.mark.parametrize("d,nx,ntau", [(1, 8, 6), (3, 4, 4)])
+def test_plane_waves_are_eigenvectors_per_element(orc, d, nx, ntau):
+    """M v = lambda v and M^T v = conj(lambda) v, element by element, for a
+    plane wave with a lattice momentum and an antiperiodic frequency."""
+    A, sigma0 = 0.5, -1.1
+    c = 1.0 + A * np.sin(sigma0)
+    lat = orc.lattice(d, nx, ntau)
+    n = orc.nsites(lat)
+    L = orc.links(lat, A, np.full(n, sigma0))
+    V = nx ** d
+    idx = np.arange(n)
+    tau = idx // V
+    s = idx % V
+    coords = [(s // nx ** j) % nx for j in range(d)]
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        ms = rng.integers(0, nx, size=d)
+        m = rng.integers(0, ntau)
+        k = 2 * np.pi * ms / nx
+        w = np.pi * (2 * m + 1) / ntau
+        phase = sum(k[j] * coords[j] for j in range(d)) + w * tau
+        v = np.exp(1j * phase)
+        lam = 1.0 - 2.0 * H * np.sum(np.cos(k)) - c * np.exp(-1j * w)
+        Mv = orc.apply_M(lat, H, L, v.real) + 1j * orc.apply_M(lat, H, L, v.imag)
+        MTv = orc.apply_MT(lat, H, L, v.real) + 1j * orc.apply_MT(lat, H, L, v.imag)
+        assert np.max(np.abs(Mv - lam * v)) < 1e-13
+        assert np.max(np.abs(MTv - np.conj(lam) * v)) < 1e-13
+
+
+@pytest.mark.parametrize("d,nx,ntau", [(1, 6, 8), (3, 3, 4)])
+def test_free_determinant_closed_form(orc, d, nx, ntau):
+    """det M = prod_k (eps_k^N_tau + c^N_tau) for a uniform link factor c."""
+    A, sigma0 = 0.5, 0.3
+    c = 1.0 + A * np.sin(sigma0)
+    lat = orc.lattice(d, nx, ntau)
+    n = orc.nsites(lat)
+    L = orc.links(lat, A, np.full(n, sigma0))
+    sign, logdet = np.linalg.slogdet(orc.dense(lat, H, L, "M"))
+    want = 1.0
+    for ms in itertools.product(range(nx), repeat=d):
+        e = 1.0 - 2.0 * H * sum(np.cos(2 * np.pi * m / nx) for m in ms)
+        want *= e ** ntau + c ** ntau
+    assert sign == np.sign(want)
+    assert abs(logdet - np.log(abs(want))) < 1e-11
+
+
+@pytest.mark.parametrize("d,nx,ntau", [(1, 5, 6), (1, 2, 4), (3, 3, 3), (3, 2, 4)])
+def test_random_field_determinant_block_reduction(orc, d, nx, ntau):
+    """det M = det(D)^N_tau det(1 + T_{N-1} ... T_0), T_tau = D^{-1} diag(c_tau),
+    with D = 1 - h K_hop the time-diagonal block and c = 1 + A sin sigma: the
+    block-cyclic structure of Eq. (7) with the link signs -1 and the +1 corner.
+    Built here from sigma directly, as V x V products, not from the oracle."""
+    A = 0.5
+    lat = orc.lattice(d, nx, ntau)
+    n = orc.nsites(lat)
+    V = nx ** d
+    rng = np.random.default_rng(5)
+    sigma = rng.uniform(-np.pi, np.pi, n)
+    L = orc.links(lat, A, sigma)
+    sign_o, logdet_o = np.linalg.slogdet(orc.dense(lat, H, L, "M"))
+
+    hop = np.zeros((V, V))
+    for s in range(V):
+        c = [(s // nx ** j) % nx for j in range(d)]
+        for j in range(d):
+            for step in (1, -1):
+                cc = list(c)
+                cc[j] = (cc[j] + step) % nx
+                t = sum(cc[q] * nx ** q for q in range(d))
+                hop[s, t] += 1.0
+    D = np.eye(V) - H * hop
+    Dinv = np.linalg.inv(D)
+    prod = np.eye(V)
+    for tau in range(ntau):
+        c_tau = 1.0 + A * np.sin(sigma[tau * V:(tau + 1) * V])
+        prod = Dinv @ np.diag(c_tau) @ prod
+    sD, lD = np.linalg.slogdet(D)
+    sP, lP = np.linalg.slogdet(np.eye(V) + prod)
+    assert sign_o == sD ** ntau * sP
+    assert abs(logdet_o - (ntau * lD + lP)) < 1e-10
+
+
+@pytest.mark.parametrize("d,nx,ntau", [(1, 7, 5), (1, 2, 3), (3, 3, 4), (3, 2, 2)])
+def test_transpose_and_normal_matrix_are_exact(orc, d, nx, ntau):
+    lat = orc.lattice(d, nx, ntau)
+    n = orc.nsites(lat)
+    rng = np.random.default_rng(9)
+    L = orc.links(lat, 0.5, rng.uniform(-np.pi, np.pi, n))
+    M = orc.dense(lat, H, L, "M")
+    MT = orc.dense(lat, H, L, "MT")
+    Q = orc.dense(lat, H, L, "MTM")
+    assert np.array_equal(MT, M.T)
+    assert np.allclose(Q, M.T @ M, rtol=0, atol=1e-14)
+    assert np.min(np.linalg.eigvalsh(Q)) > 0
+
+
+@pytest.mark.parametrize("d,nx,ntau", [(1, 6, 4), (1, 2, 4), (3, 3, 3), (3, 2, 3)])
+def test_sparsity_pattern_of_eq10(orc, d, nx, ntau):
+    """Each row has the site, 2d spatial neighbours and one temporal link
+    (2d + 2 reads per site, Sec. 4.3); neighbours coincide when N_x = 2."""
+    lat = orc.lattice(d, nx, ntau)
+    n = orc.nsites(lat)
+    rng = np.random.default_rng(2)
+    L = orc.links(lat, 0.5, rng.uniform(-np.pi, np.pi, n))
+    M = orc.dense(lat, H, L, "M")
+    nnz = np.count_nonzero(M, axis=1)
+    expect = 2 * d + 2 if nx > 2 else d + 2
+    assert np.all(nnz == expect)
+    assert np.all(np.diag(M) == 1.0)
+    offdiag_spatial = M[np.abs(M + H * (1 if nx > 2 else 2)) < 1e-15]
+    assert offdiag_spatial.size == n * 2 * d // (1 if nx > 2 else 2)
+
+
+def test_adjointness_large(orc):
+    lat = orc.lattice(3, 5, 7)
+    n = orc.nsites(lat)
+    rng = np.random.default_rng(4)
+    L = orc.links(lat, 0.5, rng.uniform(-np.pi, np.pi, n))
+    x, y = rng.standard_normal(n), rng.standard_normal(n)
+    lhs = orc.apply_M(lat, H, L, x) @ y
+    rhs = x @ orc.apply_MT(lat, H, L, y)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs) + 1e-12
+
+
+@pytest.mark.parametrize("d,nx,ntau", [(1, 4, 8), (1, 16, 12), (3, 3, 4)])
+def test_cg_matches_dense_lu(orc, d, nx, ntau):
+    lat = orc.lattice(d, nx, ntau)
+    n = orc.nsites(lat)
+    rng = np.random.default_rng(12)
+    L = orc.links(lat, 0.5, rng.uniform(-np.pi, np.pi, n))
+    b = rng.standard_normal(n)
+    x, st, it, relres = orc.cg(lat, H, L, b, tol=1e-10)
+    assert st == 0 and relres <= 1e-10
+    M = orc.dense(lat, H, L, "M")
+    Q = M.T @ M
+    x_lu = np.linalg.solve(Q, b)
+    kappa = np.linalg.cond(Q)
+    assert np.linalg.norm(x - x_lu) <= 2 * kappa * 1e-10 * np.linalg.norm(x_lu)
+    assert np.linalg.norm(b - Q @ x) <= 1.01e-10 * np.linalg.norm(b)
+
+
+def test_cg_zero_rhs_and_maxit(orc):
+    lat = orc.lattice(1, 8, 8)
+    n = orc.nsites(lat)
+    rng = np.random.default_rng(1)
+    L = orc.links(lat, 0.5, rng.uniform(-np.pi, np.pi, n))
+    x, st, it, rr = orc.cg(lat, H, L, np.zeros(n))
+    assert st == 0 and it == 0 and not np.any(x)
+    x, st, it, rr = orc.cg(lat, H, L, rng.standard_normal(n), tol=1e-10, maxit=3)
+    assert st == -4 and it == 3 and rr > 1e-10
+
+
+def _dense_action(orc, lat, prm, sigma, chi):
+    """S_pf = 1/2 sum_a chi_a^T (M^T M)^{-1} chi_a with a dense LU solve."""
+    L = orc.links(lat, prm.A, sigma)
+    M = orc.dense(lat, prm.t * prm.dtau, L, "M")
+    Q = M.T @ M
+    return 0.5 * sum(c @ np.linalg.solve(Q, c) for c in chi)
+
+
+@pytest.mark.parametrize("d,nx,ntau", [(1, 4, 6), (3, 2, 3)])
+def test_force_matches_finite_differences(orc, d, nx, ntau):
+    lat = orc.lattice(d, nx, ntau)
+    n = orc.nsites(lat)
+    prm = orc.params(cg_tol=1e-13, seed=77)
+    rng = np.random.default_rng(8)
+    sigma = rng.uniform(-np.pi, np.pi, n)
+    chi = rng.standard_normal((prm.n_pf, n))
+    F, it, rr, st = orc.force(lat, prm, sigma, chi)
+    assert st == 0
+    eps = 1e-5
+    for i in rng.choice(n, size=min(n, 8), replace=False):
+        sp, sm = sigma.copy(), sigma.copy()
+        sp[i] += eps
+        sm[i] -= eps
+        fd = (_dense_action(orc, lat, prm, sp, chi) - _dense_action(orc, lat, prm, sm, chi)) / (2 * eps)
+        assert abs(F[i] - fd) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_action_matches_dense_and_heatbath_identity(orc):
+    """S_pf(chi = M^T xi) = 1/2 |xi|^2 (Eqs. (11)-(12)); xi from NumPy's Philox."""
+    lat = orc.lattice(1, 8, 16)
+    n = orc.nsites(lat)
+    prm = orc.params(seed=2024, chain=3)
+    rng = np.random.default_rng(21)
+    sigma = rng.uniform(-np.pi, np.pi, n)
+    chi = orc.heatbath(lat, prm, sigma, traj=5)
+    S, it, rr, st = orc.action(lat, prm, sigma, chi)
+    xi = np.stack([_numpy_gaussian(prm.seed, 2, a, 5, 3, n) for a in range(prm.n_pf)])
+    assert st == 0
+    assert abs(S - 0.5 * np.sum(xi * xi)) < 1e-8 * S
+    assert abs(S - _dense_action(orc, lat, prm, sigma, chi)) < 1e-8 * S
+
+
+# --- Philox and the random streams ------------------------------------------
+
+
+def _numpy_philox_block(ctr, key):
+    """Philox4x64-10 from NumPy; its generator increments the counter before it
+    encrypts, so the stored counter is ctr - 1 (as a 256-bit integer)."""
+    c = sum(int(v) << (64 * j) for j, v in enumerate(ctr))
+    c = (c - 1) % (1 << 256)
+    words = np.array([(c >> (64 * j)) & ((1 << 64) - 1) for j in range(4)], dtype=np.uint64)
+    bg = np.random.Philox(counter=words, key=np.array(key, dtype=np.uint64))
+    return [int(v) for v in bg.random_raw(4)]
+
+
+def _numpy_gaussian(seed, tag, a, traj, chain, n):
+    out = np.empty(n)
+    for i in range(n):
+        w = _numpy_philox_block([i >> 2, tag | (a << 8), traj, chain], [seed, 0])
+        j = (i >> 1) & 1
+        u1 = (w[2 * j] >> 11) * 2.0 ** -53
+        u2 = (w[2 * j + 1] >> 11) * 2.0 ** -53
+        r = np.sqrt(-2.0 * np.log(1.0 - u1))
+        out[i] = r * (np.sin(2 * np.pi * u2) if i & 1 else np.cos(2 * np.pi * u2))
+    return out
+
+
+@pytest.mark.parametrize("ctr,key", [
+    ([0, 0, 0, 0], [0, 0]),
+    ([1, 0, 0, 0], [5, 0]),
+    ([2 ** 64 - 1, 7, 9, 11], [123456789, 987654321]),
+    ([0, 2 ** 64 - 1, 2 ** 63, 3], [2 ** 64 - 1, 2 ** 64 - 1]),
+    ([31337, 2 | (1 << 8), 17, 4], [1008, 0]),
+])
+def test_philox_matches_numpy(orc, ctr, key):
+    assert orc.philox4x64(ctr, key) == _numpy_philox_block(ctr, key)
+
+
+def test_gaussian_and_uniform_streams(orc):
+    g = orc.gaussian(99, 1, 0, 4, 2, 37)
+    assert np.allclose(g, _numpy_gaussian(99, 1, 0, 4, 2, 37), rtol=0, atol=1e-15)
+    big = orc.gaussian(7, 2, 1, 0, 0, 200000)
+    assert abs(big.mean()) < 0.01 and abs(big.var() - 1) < 0.01
+    for i in (0, 1, 2, 3, 4, 1001):
+        w = _numpy_philox_block([i >> 2, 3, 8, 1], [42, 0])
+        assert orc.uniform(42, 3, 8, 1, i) == (w[i & 3] >> 11) * 2.0 ** -53
+    s = orc.init_field(5, 2, 1000)
+    assert s.min() >= -np.pi and s.max() < np.pi
+    w = _numpy_philox_block([0, 0, 0, 2], [5, 0])
+    assert s[1] == -np.pi + 2 * np.pi * ((w[1] >> 11) * 2.0 ** -53)
+
+
+# --- molecular dynamics and the Markov chain -------------------------------
+
+
+def _md_setup(orc, d=1, nx=6, ntau=8, seed=31):
+    lat = orc.lattice(d, nx, ntau)
+    n = orc.nsites(lat)
+    prm = orc.params(cg_tol=1e-12, seed=seed)
+    rng = np.random.default_rng(seed)
+    sigma = rng.uniform(-np.pi, np.pi, n)
+    pi = rng.standard_normal(n)
+    chi = orc.heatbath(lat, prm, sigma, traj=0)
+    return lat, prm, sigma, pi, chi
+
+
+def test_leapfrog_reversible(orc):
+    lat, prm, sigma, pi, chi = _md_setup(orc)
+    s1, p1, *_ = orc.leapfrog(lat, prm, sigma, pi, chi, 10, 0.05)
+    s2, p2, *_ = orc.leapfrog(lat, prm, s1, -p1, chi, 10, 0.05)
+    assert np.max(np.abs(s2 - sigma)) < 1e-9
+    assert np.max(np.abs(p2 + pi)) < 1e-9
+    assert np.max(np.abs(s1 - sigma)) > 1e-2
+
+
+def _hamiltonian(orc, lat, prm, sigma, pi, chi):
+    return 0.5 * pi @ pi + orc.action(lat, prm, sigma, chi)[0]
+
+
+def test_energy_violation_scales_as_dt_squared(orc):
+    lat, prm, sigma, pi, chi = _md_setup(orc, nx=4, ntau=6, seed=3)
+    pi = 0.5 * pi
+    H0 = _hamiltonian(orc, lat, prm, sigma, pi, chi)
+    steps = np.array([16, 32, 64])
+    dH = []
+    for n_md in steps:
+        s1, p1, *_ = orc.leapfrog(lat, prm, sigma, pi, chi, int(n_md), 0.25 / n_md)
+        dH.append(abs(_hamiltonian(orc, lat, prm, s1, p1, chi) - H0))
+    slope = np.polyfit(np.log(0.25 / steps), np.log(dH), 1)[0]
+    assert 1.8 < slope < 2.2, (dH, slope)
+
+
+@pytest.mark.slow
+def test_creutz_equality_mean_exp_minus_dH_is_one(orc):
+    """<exp(-dH)> = 1 for an area-preserving, reversible integrator (Sec. 4.1:
+    the Metropolis step makes HMC exact)."""
+    lat = orc.lattice(1, 4, 6)
+    n = orc.nsites(lat)
+    prm = orc.params(seed=4242)
+    sigma = np.random.default_rng(0).uniform(-np.pi, np.pi, n)
+    vals = []
+    for traj in range(400):
+        sigma, info = orc.trajectory(lat, prm, sigma, 8, 1.0 / 8, traj)
+        assert info["status"] == 0
+        assert info["accepted"] == (info["u"] < np.exp(-info["dH"]))
+        if traj >= 20:
+            vals.append(np.exp(-info["dH"]))
+    vals = np.array(vals)
+    blocks = vals[: len(vals) // 20 * 20].reshape(20, -1).mean(axis=1)
+    err = blocks.std(ddof=1) / np.sqrt(len(blocks))
+    assert abs(vals.mean() - 1.0) < 3 * err + 1e-3, (vals.mean(), err)
+
+
+def test_trajectory_draws_and_metropolis(orc):
+    lat = orc.lattice(1, 8, 8)
+    n = orc.nsites(lat)
+    prm = orc.params(seed=606, chain=2)
+    sigma = np.random.default_rng(1).uniform(-np.pi, np.pi, n)
+    pi = _numpy_gaussian(606, 1, 0, 9, 2, n)
+    xi = np.stack([_numpy_gaussian(606, 2, a, 9, 2, n) for a in range(2)])
+    s1, info = orc.trajectory(lat, prm, sigma, 6, 1.0 / 6, 9)
+    assert abs(info["H0"] - 0.5 * (pi @ pi + np.sum(xi * xi))) < 1e-8 * info["H0"]
+    assert info["u"] == orc.uniform(606, 3, 9, 2, 0)
+    assert info["accepted"] == (info["u"] < np.exp(-info["dH"]))
+    assert info["n_solves"] == 2 * (6 + 3)
+    if not info["accepted"]:
+        assert np.array_equal(s1, sigma)
+    # A huge step must be rejected and leave sigma untouched.
+    s2, info2 = orc.trajectory(lat, prm, sigma, 2, 2.0, 10)
+    if not info2["accepted"]:
+        assert np.array_equal(s2, sigma)
+        assert info2["u"] >= np.exp(-info2["dH"])
+
+
+@pytest.mark.slow
+def test_hmc_reproduces_exact_expectation_on_2x2(orc):
+    """On N_x = N_tau = 2 (4 sites), <sin^2 sigma> under the weight det(M)^2
+    (Eq. (6) with S_g = 0) by quadrature must match the HMC average."""
+    A = 0.5
+    lat = orc.lattice(1, 2, 2)
+    g = 28
+    th = -np.pi + 2 * np.pi * (np.arange(g) + 0.5) / g
+    S = np.stack(np.meshgrid(th, th, th, th, indexing="ij"), -1).reshape(-1, 4)
+    # Dense M for every grid point via the oracle's own links is too slow;
+    # the 4x4 matrix is assembled from its definition in Eq. (10) instead:
+    # sites i = x + 2 tau; neighbours of x are both 1 - x (coefficient -2h).
+    c = 1.0 + A * np.sin(S)
+    Mg = np.zeros((S.shape[0], 4, 4))
+    for tau in range(2):
+        for x in range(2):
+            i = x + 2 * tau
+            Mg[:, i, i] = 1.0
+            Mg[:, i, (1 - x) + 2 * tau] = -2 * H
+            j = x + 2 * (1 - tau)
+            sign = 1.0 if (1 - tau) == 1 else -1.0
+            Mg[:, i, j] = sign * c[:, j]
+    # cross-check the hand assembly against the oracle on one point
+    Lone = orc.links(lat, A, S[123])
+    assert np.allclose(orc.dense(lat, H, Lone, "M"), Mg[123], atol=1e-15)
+    w = np.linalg.det(Mg) ** 2
+    exact = np.sum(w * np.mean(np.sin(S) ** 2, axis=1)) / np.sum(w)
+
+    prm = orc.params(seed=99)
+    sigma = np.zeros(4)
+    obs = []
+    for traj in range(3000):
+        sigma, info = orc.trajectory(lat, prm, sigma, 5, 0.3, traj)
+        if traj >= 100:
+            obs.append(np.mean(np.sin(sigma) ** 2))
+    obs = np.array(obs)
+    blocks = obs[: len(obs) // 50 * 50].reshape(50, -1).mean(axis=1)
+    err = blocks.std(ddof=1) / np.sqrt(len(blocks))
+    assert abs(obs.mean() - exact) < 4 * err, (obs.mean(), exact, err)
