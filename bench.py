@@ -1,0 +1,349 @@
+"""Benchmark of the Hubbard HMC path on GB300.
+
+A step is one HMC trajectory (Sec. 4.1 of arXiv:1007.3432): momentum and
+pseudofermion heatbath, n_md + 1 CG solves of Q x = chi for two pseudofermion
+components, n_md + 1 force evaluations with momentum updates, the sigma steps,
+both Hamiltonians and the Metropolis test.  The default workload is the d = 1,
+N_x = 1024, N_tau = 512 lattice (524,288 sites) with 20 leapfrog steps, CG to a
+true relative residual of 1e-10, in FP64.
+
+value: M^T M applies per second inside the CG solves of the timed
+trajectories (every CG step and every FP64 true-residual recomputation applies
+Q = M^T M once per right-hand side), with sigma resident on the device when a
+step's timed region starts.  e2e: the same count over wall time of the public
+calls hh_set_field(host) -> hh_trajectory -> hh_get_field(host) per step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload c0|c1|c2] [--precision fp64|mixed]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"] if os.path.exists(
+    os.path.join(ROOT, "BASELINE.json")) else "MTM applies/s"
+UNIT = "MTM applies/s"
+WORKLOADS = {"c0": workloads.C0, "c1": workloads.C1, "c2": workloads.C2}
+
+# Algorithmic work per site (see the design notes): FP64 flops of one CG step
+# (p update, M p with |Mp|^2, M^T t, x and r updates, |r|^2) and of one FP64
+# true-residual step (M x, M^T t, b - Q x, |r|^2; + x accumulate when mixed).
+def flops_per_site(d, kind, precision):
+    m = 2 * d + 3
+    if kind == "cg":
+        return 2 * m + 10
+    return 2 * m + 3 + (1 if precision == "mixed" else 0)
+
+
+# Bytes per site: a CG step reads r, p, p, L, t, L, x, p, r and writes p, t,
+# x, r (13 words); the minimum for one M^T M apply is x, L in and y out.
+def bytes_per_site(kind, precision):
+    if kind == "cg":
+        return 13 * (8 if precision == "fp64" else 4)
+    return 8 * 8 + (12 if precision == "mixed" else 0)
+
+
+def fp64_peak_tflops():
+    """FP64 peak of GB300 from unit counts and clocks: 152 SMs x 2 DFMA per
+    clock per SM x 2 flops x 2.07 GHz (maximum SM clock) = 1.26 TFLOP/s, the
+    nominal 1.25 TFLOP/s of the part."""
+    return 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, value):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_baseline(wl, seconds=15.0):
+    """The oracle, as it stands, on this host: CG iterations on the same
+    lattice and field for about `seconds`, as M^T M applies per second."""
+    import oracle
+    lat = oracle.lattice(wl.d, wl.nx, wl.ntau)
+    n = wl.nsites
+    sigma = workloads.sigma_field(n, seed=wl.seed)
+    L = oracle.links(lat, workloads.A_HS, sigma)
+    b = workloads.source(n, seed=wl.seed)
+    h = workloads.T_HOP * workloads.DTAU
+    t0 = time.perf_counter()
+    oracle.cg(lat, h, L, b, 1e-10, 2)
+    per_it = max((time.perf_counter() - t0) / 3.0, 1e-6)
+    iters = max(3, int(seconds / per_it))
+    t0 = time.perf_counter()
+    _, st, it, rr = oracle.cg(lat, h, L, b, 1e-10, iters)
+    dt = time.perf_counter() - t0
+    applies = it + 1  # it CG steps + one final true-residual apply
+    return {"value": applies / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "oracle FP64 CG on the %s lattice (seed %d): %d CG iterations (%d M^T M applies) in %.1f s, single thread"
+                      % (wl.name, wl.seed, it, applies, dt)}
+
+
+def run_reference(args, wl, world, rank):
+    """The oracle timed as the reference arm (rank 0 only)."""
+    if rank != 0:
+        return
+    per_step = max(2.0, 40.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(wl, seconds=min(per_step, 3.0))
+    vals, samples = [], []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = cpu_baseline(wl, seconds=per_step)
+        vals.append(r["value"])
+        samples.append(r["sample"])
+    wall = time.perf_counter() - t0
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(args, wl),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": samples[-1] if samples else ""},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args, wl):
+    return {"workload": wl.name, "d": wl.d, "nx": wl.nx, "ntau": wl.ntau, "sites": wl.nsites,
+            "t": workloads.T_HOP, "dtau": workloads.DTAU, "A": workloads.A_HS, "seed": wl.seed,
+            "n_md": args.n_md, "dt": 1.0 / args.n_md, "n_pf": 2, "cg_tol": 1e-10,
+            "precision": args.precision, "step": "one HMC trajectory",
+            "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas%d" % args.gpus}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--n-md", type=int, default=None)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.n_md is None:
+        args.n_md = wl.n_md
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, wl, world, rank)
+        return
+
+    import torch
+    from __graft_entry__ import build
+    from paper_1007_3432_gb300 import Context
+
+    if rank == 0:
+        build()
+    barrier(world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    n = wl.nsites
+    sigma_h = workloads.sigma_field(n, seed=wl.seed, chain=rank)
+    ctx = Context(wl.d, wl.nx, wl.ntau, seed=wl.seed, n_pf=2, chain_id=rank, precision=args.precision,
+                  stream=stream)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    dt = 1.0 / args.n_md
+
+    def step(traj, timed):
+        flush.fill_(float(traj))
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        w0 = time.perf_counter()
+        e0.record(stream)
+        ctx.set_field(sigma_h)              # host -> device (the step's input)
+        e1.record(stream)
+        info = ctx.trajectory(args.n_md, dt, traj, info=False)
+        e2.record(stream)
+        ctx.get_field(sigma_h)              # device -> host (the step's output)
+        w1 = time.perf_counter()
+        torch.cuda.synchronize(dev)
+        return e1.elapsed_time(e2), (w1 - w0) * 1000.0, info
+
+    for w in range(args.warmup):
+        step(w, False)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    ctx.counters_reset(profile_engine=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    dev_ms, wall_ms = [], []
+    for k in range(args.steps):
+        a, b, _ = step(args.warmup + k, True)
+        dev_ms.append(a)
+        wall_ms.append(b)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    barrier(world)
+    cnt = ctx.counters()
+
+    applies = cnt["cg_steps"] + cnt["ru_steps"]
+    t_dev = max_over_ranks(world, sum(dev_ms) / 1000.0)
+    t_wall = max_over_ranks(world, sum(wall_ms) / 1000.0)
+    tot_applies = sum_over_ranks(world, float(applies))
+    tot_solves = sum_over_ranks(world, float(cnt["solves"]))
+    value = tot_applies / t_dev
+    e2e = tot_applies / t_wall
+
+    # Roofline of the dominant kernel: the persistent CG engine.
+    f_cg = flops_per_site(wl.d, "cg", args.precision)
+    f_ru = flops_per_site(wl.d, "ru", args.precision)
+    peaks, src = measured_peaks()
+    eng_s = cnt["engine_ms"] / 1000.0
+    per_launch = eng_s / max(1, cnt["engine_launches"])
+    if args.precision == "fp64":
+        flops = n * (cnt["cg_steps"] * f_cg + cnt["ru_steps"] * f_ru)
+        achieved = flops / eng_s / 1e12 if eng_s > 0 else 0.0
+        peak = fp64_peak_tflops()
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "engine_kernel (persistent FP64 CG)",
+                "peak_source": "FP64 from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "launch_ms": per_launch * 1000.0}
+    else:
+        byts = n * (cnt["cg_steps"] * bytes_per_site("cg", "mixed") + cnt["ru_steps"] * bytes_per_site("ru", "mixed"))
+        achieved = byts / eng_s / 1e9 if eng_s > 0 else 0.0
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "engine_kernel (persistent FP32-inner CG)",
+                "peak_source": "%s MEASURED_PEAKS.json hbm_gbs" % src, "launch_ms": per_launch * 1000.0}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic", "config": config_of(args, wl),
+        "solves_per_s": tot_solves / t_dev, "trajectories_per_s": world * args.steps / t_dev,
+        "cg_steps_per_solve": cnt["cg_steps"] / max(1, cnt["solves"]),
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
+        "gpu_launches": int(cnt["kernel_launches"]),
+        "clocks": clk, "roofline": roof,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    elif rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

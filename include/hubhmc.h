@@ -1,0 +1,209 @@
+/*
+ * hubhmc: Hybrid Monte Carlo for the Hubbard model on one GB300 GPU.
+ *
+ * C ABI of the library.  The method is that of K. A. Wendt, J. E. Drut and
+ * T. A. Laehde, "Toward large-scale Hybrid Monte Carlo simulations of the
+ * Hubbard model on graphics processing units" (arXiv:1007.3432):
+ *   - the fermion matrix M on a (d+1)-dimensional space-time lattice
+ *     (Sec. 2, Eqs. (7)-(10)): unit diagonal, -h = -t*dtau on the 2d spatial
+ *     nearest neighbours (periodic), and one time link per site carrying
+ *     L(n,tau) = -(1 + A sin sigma(n,tau)) into slice tau+1, with the sign
+ *     flipped on the wrap link N_tau-1 -> 0 (antiperiodic in time);
+ *   - the normal matrix Q = M^T M and the linear problem Q x = b solved by
+ *     conjugate gradient (Sec. 4.1);
+ *   - the pseudofermion action S_pf = 1/2 sum_a chi_a^T Q^{-1} chi_a
+ *     (Eqs. (11)-(12)), its force dS_pf/dsigma, leapfrog molecular dynamics and
+ *     the Metropolis accept/reject step of the phi-algorithm (Sec. 4.1).
+ *
+ * Conventions for every call:
+ *   - Arrays are indexed by site i = x + Nx*(y + Nx*(z + Nx*tau)) for d = 3 and
+ *     i = x + Nx*tau for d = 1 (x fastest).  A "vector" holds N = Nx^d * Ntau
+ *     elements; n_rhs vectors are stored back to back (vector a at a*N).
+ *   - Pointers documented as device pointers must point to CUDA device memory
+ *     of the current device; the caller owns them and keeps them alive until
+ *     the call's work on the context stream has finished.
+ *   - All GPU work of a context is ordered on the stream given at creation.
+ *     Calls that return results in host structures (an info argument, host
+ *     output pointers) synchronise that stream before they return; the other
+ *     calls only enqueue work.
+ *   - Every call returns HH_OK (0) or a negative error code; no C++ exception
+ *     crosses the ABI.  After an error the context stays valid unless the
+ *     error is HH_ECUDA from a sticky CUDA fault.
+ *   - A context is not thread safe: one host thread at a time may use it.
+ */
+#ifndef HUBHMC_H
+#define HUBHMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define HH_OK 0
+#define HH_EINVAL (-1)   /* invalid argument (shape, pointer, enum) */
+#define HH_ENOMEM (-2)   /* device or host allocation failed */
+#define HH_ECUDA (-3)    /* a CUDA runtime call failed */
+#define HH_ENOCONV (-4)  /* CG reached its iteration cap above tolerance */
+#define HH_ENUMERIC (-5) /* NaN or Inf met in a reduction */
+#define HH_ETIMEOUT (-6) /* a bounded device-side wait ran out */
+#define HH_EBUSY (-7)    /* no free slot or memory budget for the request */
+
+/* Precision of the CG solve.
+ *   HH_FP64:  every stencil apply, vector update and reduction in FP64.
+ *   HH_MIXED: FP32 inner CG (FP32 links, vectors and stencil, products summed
+ *             per thread in FP32 and across threads in FP64) with reliable
+ *             updates that accumulate the solution and recompute the true
+ *             residual b - Q x in FP64; the stopping test is on that FP64 true
+ *             residual, so both modes meet the same tolerance. */
+#define HH_FP64 0
+#define HH_MIXED 1
+
+/* Operators for hh_apply. */
+#define HH_OP_M 0   /* y = M x */
+#define HH_OP_MT 1  /* y = M^T x */
+#define HH_OP_MTM 2 /* y = M^T M x = Q x */
+
+/* Element types for hh_apply. */
+#define HH_DTYPE_F64 0
+#define HH_DTYPE_F32 1
+
+typedef struct hh_ctx hh_ctx;
+
+typedef struct {
+    int d;    /* spatial dimension: 1 or 3 */
+    int nx;   /* spatial extent N_x >= 2 (periodic) */
+    int ntau; /* time slices N_tau >= 2 (antiperiodic) */
+} hh_lattice;
+
+typedef struct {
+    double t;              /* hopping amplitude; h = t * dtau */
+    double dtau;           /* Trotter time step */
+    double A;              /* auxiliary-field coupling in 1 + A sin(sigma) */
+    int precision;         /* HH_FP64 or HH_MIXED */
+    double cg_tol;         /* stop when ||b - Q x||_2 <= cg_tol * ||b||_2 */
+    int cg_maxit;          /* cap on CG iterations per solve */
+    double reliable_delta; /* HH_MIXED: reliable update when ||r|| < delta * max ||r|| */
+    uint64_t seed;         /* Philox key for all random draws of the context */
+    int n_pf;              /* real pseudofermion components (2: weight (det M)^2) */
+    uint64_t chain_id;     /* Philox counter word identifying the Markov chain */
+} hh_params;
+
+typedef struct {
+    int iterations;       /* CG iterations of the solve (largest over right-hand sides) */
+    int reliable_updates; /* true-residual recomputations (summed over right-hand sides) */
+    double true_relres;   /* largest ||b - Q x|| / ||b|| over right-hand sides */
+    int converged;        /* 1 if every right-hand side met cg_tol */
+} hh_solve_info;
+
+typedef struct {
+    double H0, H1, dH;     /* Hamiltonian 1/2 |pi|^2 + S_pf before / after the MD */
+    double u;              /* Metropolis uniform (Philox tag 3) */
+    int accepted;          /* 1 iff u < exp(-dH); on 0 sigma is restored */
+    int cg_iterations;     /* CG iterations summed over all solves */
+    int n_solves;          /* right-hand sides solved: n_pf * (n_md + 1) */
+    double max_true_relres;/* largest true relative residual over the solves */
+} hh_traj_info;
+
+/* Fill p with the defaults t = 1, dtau = 0.05, A = 0.5, FP64, cg_tol = 1e-10,
+ * cg_maxit = 1000000, reliable_delta = 0.1, seed = 0, n_pf = 2, chain_id = 0. */
+void hh_default_params(hh_params *p);
+
+/* Create a context for one lattice and one Markov chain.  Allocates sigma,
+ * the links (FP64 and FP32), the HMC fields and the CG workspace on the
+ * current device.  stream: a cudaStream_t (NULL = legacy default stream).
+ * sigma starts at zero.  Errors: HH_EINVAL (d not 1 or 3, nx < 2, ntau < 2,
+ * N >= 2^31, n_pf < 1, unknown precision), HH_ENOMEM, HH_ECUDA. */
+int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cuda_stream);
+
+/* Free every device and host resource of the context (after synchronising
+ * its stream).  NULL is accepted. */
+int hh_destroy(hh_ctx *ctx);
+
+/* Number of sites N of the context's lattice (0 for NULL). */
+long long hh_nsites(const hh_ctx *ctx);
+
+/* Copy N doubles into the context's auxiliary field sigma (Eq. (8): the
+ * field of time slice tau lives on the link out of that slice) and recompute
+ * the links.  on_device = 1: sigma is a device pointer (copy on the stream);
+ * 0: a host pointer (synchronous copy).  Errors: HH_EINVAL for NULL. */
+int hh_set_field(hh_ctx *ctx, const double *sigma, int on_device);
+
+/* Copy the context's sigma out (N doubles), to device (on_device = 1, on the
+ * stream) or host memory (0, synchronous). */
+int hh_get_field(hh_ctx *ctx, double *sigma, int on_device);
+
+/* sigma(i) = -pi + 2 pi u_i with u_i the Philox uniform of tag 0, block i/4,
+ * word i%4, trajectory word 0 and the context's chain_id, key (seed, 0);
+ * recompute the links. */
+int hh_init_field_random(hh_ctx *ctx, uint64_t seed);
+
+/* y = op(x) for op in {HH_OP_M, HH_OP_MT, HH_OP_MTM} (Eq. (10); Q = M^T M
+ * as in Sec. 4.3).  x and y are device pointers of N elements of dtype
+ * HH_DTYPE_F64 (links in FP64) or HH_DTYPE_F32 (links rounded to FP32); they
+ * must not overlap.  Errors: HH_EINVAL. */
+int hh_apply(hh_ctx *ctx, int op, const void *x, void *y, int dtype);
+
+/* Solve Q x_a = b_a for a = 0..n_rhs-1 by CG with x0 = 0 (Sec. 4.1) in the
+ * context's precision, all right-hand sides in one persistent launch.
+ * b, x: device pointers to n_rhs * N doubles.  info may be NULL (then the call
+ * does not synchronise).  Returns HH_ENOCONV if a right-hand side missed
+ * cg_tol within cg_maxit (x then holds the last iterate), HH_ETIMEOUT if a
+ * device-side barrier wait ran out, HH_ENUMERIC on NaN/Inf. */
+int hh_solve(hh_ctx *ctx, const double *b, double *x, int n_rhs, hh_solve_info *info);
+
+/* F = dS_pf/dsigma for S_pf = 1/2 sum_a chi_a^T Q^{-1} chi_a: solves for
+ * x_a = Q^{-1} chi_a, then F(n,tau) = -sum_a (M x_a)(n,tau+1) s(tau)
+ * A cos sigma(n,tau) x_a(n,tau), s = -1 except +1 on the wrap link.
+ * chi: device, n_rhs * N doubles; F: device, N doubles.  info may be NULL. */
+int hh_force(hh_ctx *ctx, const double *chi, int n_rhs, double *F, hh_solve_info *info);
+
+/* S_pf = 1/2 sum_a chi_a^T Q^{-1} chi_a (Eq. (12)) for the current sigma.
+ * chi: device, n_rhs * N doubles; S: host double.  Synchronises. */
+int hh_action(hh_ctx *ctx, const double *chi, int n_rhs, double *S, hh_solve_info *info);
+
+/* One HMC trajectory of the phi-algorithm (Sec. 4.1) for trajectory number
+ * traj_index: momenta pi ~ N(0,1) (Philox tag 1), pseudofermion sources
+ * xi_a ~ N(0,1) (tag 2, component a in counter bits 8+), chi_a = M^T xi_a;
+ * H0; leapfrog with n_md steps of size dt (n_md + 1 force evaluations);
+ * H1; accept iff u < exp(-(H1 - H0)) with u the tag-3 uniform; on
+ * rejection sigma is restored.  info may be NULL (then nothing synchronises).
+ * Errors: HH_EINVAL (n_md < 1), solver errors as in hh_solve. */
+int hh_trajectory(hh_ctx *ctx, int n_md, double dt, uint64_t traj_index, hh_traj_info *info);
+
+/* Leapfrog only, on caller-owned fields: integrates (sigma_ctx, pi) for n_md
+ * steps of size dt at fixed chi (device, n_rhs * N), updating the context's
+ * sigma and the device array pi (N doubles) in place.  No Metropolis step. */
+int hh_leapfrog(hh_ctx *ctx, double *pi, const double *chi, int n_rhs, int n_md, double dt,
+                hh_solve_info *info);
+
+/* Work counters of a context, for throughput and roofline accounting. */
+typedef struct {
+    long long kernel_launches; /* kernels this context launched since the last reset */
+    long long engine_launches; /* persistent CG launches among them */
+    double engine_ms;          /* summed CUDA-event time of those launches on the
+                                  context stream (0 unless profiling was enabled) */
+    long long cg_steps;        /* CG steps, summed over right-hand sides */
+    long long ru_steps;        /* FP64 true-residual recomputations (checks and
+                                  reliable updates), summed over right-hand sides */
+    long long solves;          /* right-hand sides solved */
+    long long sites;           /* N of the context's lattice */
+} hh_counters;
+
+/* Zero the counters.  profile_engine = 1 records a CUDA event pair around
+ * every persistent CG launch (on the context stream) until the next reset. */
+int hh_counters_reset(hh_ctx *ctx, int profile_engine);
+
+/* Read the counters; synchronises the context stream. */
+int hh_counters_get(hh_ctx *ctx, hh_counters *out);
+
+/* Text for an error code. */
+const char *hh_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HUBHMC_H */

@@ -1,0 +1,242 @@
+"""ctypes binding of ``libhubhmc.so``: argument marshalling only.
+
+Every function here forwards to the C ABI declared in ``include/hubhmc.h``
+with the same name; tensors are passed as raw device (or host) pointers and
+the CUDA stream as the raw ``cudaStream_t`` handle.  There is no CPU fallback:
+if the library cannot be loaded, the import raises.
+"""
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libhubhmc.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "hubhmc.h")
+
+HH_OK, HH_EINVAL, HH_ENOMEM, HH_ECUDA = 0, -1, -2, -3
+HH_ENOCONV, HH_ENUMERIC, HH_ETIMEOUT, HH_EBUSY = -4, -5, -6, -7
+HH_FP64, HH_MIXED = 0, 1
+HH_OP_M, HH_OP_MT, HH_OP_MTM = 0, 1, 2
+HH_DTYPE_F64, HH_DTYPE_F32 = 0, 1
+
+
+class HHError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, _strerror(code), code))
+
+
+class hh_lattice(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("nx", ctypes.c_int), ("ntau", ctypes.c_int)]
+
+
+class hh_params(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("dtau", ctypes.c_double), ("A", ctypes.c_double),
+                ("precision", ctypes.c_int), ("cg_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
+                ("reliable_delta", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("n_pf", ctypes.c_int), ("chain_id", ctypes.c_uint64)]
+
+
+class hh_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("true_relres", ctypes.c_double), ("converged", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hh_traj_info(ctypes.Structure):
+    _fields_ = [("H0", ctypes.c_double), ("H1", ctypes.c_double), ("dH", ctypes.c_double),
+                ("u", ctypes.c_double), ("accepted", ctypes.c_int), ("cg_iterations", ctypes.c_int),
+                ("n_solves", ctypes.c_int), ("max_true_relres", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hh_counters(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_longlong), ("engine_launches", ctypes.c_longlong),
+                ("engine_ms", ctypes.c_double), ("cg_steps", ctypes.c_longlong),
+                ("ru_steps", ctypes.c_longlong), ("solves", ctypes.c_longlong),
+                ("sites", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libhubhmc.so not built (run __graft_entry__.build()): %s" % path)
+    L = ctypes.CDLL(path)
+    vp, i, d, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint64
+    sig = {
+        "hh_default_params": (None, [ctypes.POINTER(hh_params)]),
+        "hh_strerror": (ctypes.c_char_p, [i]),
+        "hh_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(hh_lattice), ctypes.POINTER(hh_params), vp]),
+        "hh_destroy": (i, [vp]),
+        "hh_nsites": (ctypes.c_longlong, [vp]),
+        "hh_set_field": (i, [vp, vp, i]),
+        "hh_get_field": (i, [vp, vp, i]),
+        "hh_init_field_random": (i, [vp, u64]),
+        "hh_apply": (i, [vp, i, vp, vp, i]),
+        "hh_solve": (i, [vp, vp, vp, i, ctypes.POINTER(hh_solve_info)]),
+        "hh_force": (i, [vp, vp, i, vp, ctypes.POINTER(hh_solve_info)]),
+        "hh_action": (i, [vp, vp, i, ctypes.POINTER(d), ctypes.POINTER(hh_solve_info)]),
+        "hh_trajectory": (i, [vp, i, d, u64, ctypes.POINTER(hh_traj_info)]),
+        "hh_leapfrog": (i, [vp, vp, vp, i, i, d, ctypes.POINTER(hh_solve_info)]),
+        "hh_counters_reset": (i, [vp, i]),
+        "hh_counters_get": (i, [vp, ctypes.POINTER(hh_counters)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _strerror(code):
+    if _lib is None:
+        return "error"
+    return _lib.hh_strerror(code).decode()
+
+
+def header_symbols(path: str = HEADER):
+    """Names of the functions declared in a public header."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hh_[a-z0-9_]+)\s*\(", text)))
+
+
+def check(code, what, allow=()):
+    if code != HH_OK and code not in allow:
+        raise HHError(code, what)
+    return code
+
+
+def _ptr(t):
+    """Raw pointer of a torch tensor or an integer address."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Context:
+    """One lattice and one Markov chain on the current CUDA device."""
+
+    def __init__(self, d, nx, ntau, t=1.0, dtau=0.05, A=0.5, precision=HH_FP64, cg_tol=1e-10,
+                 cg_maxit=1000000, reliable_delta=0.1, seed=0, n_pf=2, chain_id=0, stream=None):
+        L = load()
+        self._lib = L
+        self.lat = hh_lattice(d, nx, ntau)
+        p = hh_params()
+        L.hh_default_params(ctypes.byref(p))
+        p.t, p.dtau, p.A = t, dtau, A
+        p.precision = {"fp64": HH_FP64, "mixed": HH_MIXED}.get(precision, precision)
+        p.cg_tol, p.cg_maxit, p.reliable_delta = cg_tol, cg_maxit, reliable_delta
+        p.seed, p.n_pf, p.chain_id = seed, n_pf, chain_id
+        self.params = p
+        self.stream = stream
+        h = ctypes.c_void_p()
+        check(L.hh_create(ctypes.byref(h), ctypes.byref(self.lat), ctypes.byref(p),
+                          _stream_handle(stream)), "hh_create")
+        self._h = h
+        self.N = int(L.hh_nsites(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- field ----
+    def set_field(self, sigma, on_device=None):
+        if on_device is None:
+            on_device = getattr(sigma, "is_cuda", False)
+        ptr = _ptr(sigma) if not hasattr(sigma, "ctypes") else sigma.ctypes.data
+        check(self._lib.hh_set_field(self._h, ptr, int(bool(on_device))), "hh_set_field")
+
+    def get_field(self, out, on_device=None):
+        if on_device is None:
+            on_device = getattr(out, "is_cuda", False)
+        ptr = _ptr(out) if not hasattr(out, "ctypes") else out.ctypes.data
+        check(self._lib.hh_get_field(self._h, ptr, int(bool(on_device))), "hh_get_field")
+        return out
+
+    def init_field_random(self, seed):
+        check(self._lib.hh_init_field_random(self._h, seed), "hh_init_field_random")
+
+    # ---- operators and solves ----
+    def apply(self, op, x, y, dtype=None):
+        if dtype is None:
+            import torch
+            dtype = HH_DTYPE_F32 if x.dtype == torch.float32 else HH_DTYPE_F64
+        check(self._lib.hh_apply(self._h, op, _ptr(x), _ptr(y), dtype), "hh_apply")
+
+    def solve(self, b, x, n_rhs=1, info=True, allow=()):
+        inf = hh_solve_info() if info else None
+        rc = self._lib.hh_solve(self._h, _ptr(b), _ptr(x), n_rhs, ctypes.byref(inf) if info else None)
+        check(rc, "hh_solve", allow)
+        return (rc, inf.as_dict()) if info else rc
+
+    def force(self, chi, n_rhs, F, info=True):
+        inf = hh_solve_info() if info else None
+        rc = self._lib.hh_force(self._h, _ptr(chi), n_rhs, _ptr(F), ctypes.byref(inf) if info else None)
+        check(rc, "hh_force")
+        return inf.as_dict() if info else None
+
+    def action(self, chi, n_rhs):
+        S = ctypes.c_double()
+        inf = hh_solve_info()
+        check(self._lib.hh_action(self._h, _ptr(chi), n_rhs, ctypes.byref(S), ctypes.byref(inf)), "hh_action")
+        return S.value, inf.as_dict()
+
+    def leapfrog(self, pi, chi, n_rhs, n_md, dt, info=True):
+        inf = hh_solve_info() if info else None
+        rc = self._lib.hh_leapfrog(self._h, _ptr(pi), _ptr(chi), n_rhs, n_md, dt,
+                                   ctypes.byref(inf) if info else None)
+        check(rc, "hh_leapfrog")
+        return inf.as_dict() if info else None
+
+    def trajectory(self, n_md, dt, traj_index, info=True, allow=()):
+        inf = hh_traj_info() if info else None
+        rc = self._lib.hh_trajectory(self._h, n_md, dt, traj_index, ctypes.byref(inf) if info else None)
+        check(rc, "hh_trajectory", allow)
+        return inf.as_dict() if info else None
+
+    def counters_reset(self, profile_engine=False):
+        check(self._lib.hh_counters_reset(self._h, int(bool(profile_engine))), "hh_counters_reset")
+
+    def counters(self):
+        c = hh_counters()
+        check(self._lib.hh_counters_get(self._h, ctypes.byref(c)), "hh_counters_get")
+        return c.as_dict()

@@ -1,0 +1,720 @@
+// C ABI of the library: contexts, solves and the HMC trajectory driver.
+// Every step of the path runs in the kernels of hh_kernels.cu and
+// hh_engine.cu; this file only allocates, validates, plans and enqueues.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/hubhmc.h"
+#include "hh_engine.cuh"
+#include "hh_kernels.cuh"
+
+using namespace hh;
+
+namespace {
+
+struct EngStats {
+    long long cg_iters;     // summed CG steps
+    int max_iters;          // largest CG steps of one system
+    int n_solves;
+    int n_ru;
+    int worst_status;       // most severe status among systems
+    int error;              // barrier / launch error
+    int pad;
+    double max_relres;
+};
+
+__global__ void k_engine_reset(EngState *s0, EngState *s1, int nsys, BarrierCtl *ctl,
+                               long long timeout_ns)
+{
+    for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
+        EngState z;
+        memset(&z, 0, sizeof(z));
+        z.mode = MODE_NEW;
+        s0[s] = z;
+        s1[s] = z;
+    }
+    if (threadIdx.x == 0) {
+        ctl->count = 0;
+        ctl->error = 0;
+        ctl->active = nsys;
+        ctl->k = 0;
+        ctl->timeout_ns = timeout_ns;
+    }
+}
+
+__device__ int severity(int st)
+{
+    // ETIMEOUT and ENUMERIC outrank ENOCONV.
+    if (st == HH_ETIMEOUT) return 3;
+    if (st == HH_ENUMERIC) return 2;
+    if (st == HH_ENOCONV) return 1;
+    return 0;
+}
+
+// Running totals across solves (not cleared by k_zero_stats).
+struct EngTotals {
+    long long cg_steps, ru_steps, solves;
+};
+
+__global__ void k_engine_fold(EngState *s0, EngState *s1, int nsys, const BarrierCtl *ctl,
+                              EngStats *stats, EngTotals *tot)
+{
+    if (threadIdx.x != 0) return;
+    const EngState *st = (ctl->k & 1) ? s1 : s0;
+    if (ctl->error != 0 && severity(ctl->error) > severity(stats->worst_status))
+        stats->worst_status = ctl->error;
+    if (ctl->error != 0) stats->error = ctl->error;
+    for (int s = 0; s < nsys; ++s) {
+        EngState S = st[s];
+        int status = S.status;
+        if (S.mode != MODE_DONE && status == 0) status = HH_ETIMEOUT;
+        stats->cg_iters += S.cg_steps;
+        tot->cg_steps += S.cg_steps;
+        tot->ru_steps += S.n_ru;
+        tot->solves += 1;
+        if (S.cg_steps > stats->max_iters) stats->max_iters = S.cg_steps;
+        stats->n_solves += 1;
+        stats->n_ru += S.n_ru;
+        if (S.true_relres > stats->max_relres || S.true_relres != S.true_relres)
+            stats->max_relres = S.true_relres;
+        if (severity(status) > severity(stats->worst_status)) stats->worst_status = status;
+    }
+}
+
+__global__ void k_zero_stats(EngStats *stats)
+{
+    if (threadIdx.x == 0) memset(stats, 0, sizeof(EngStats));
+}
+
+// Plan of one engine launch: the system table and tiles in device memory.
+struct Plan {
+    int nsys = 0, ntiles = 0, grid = 0;
+    int precision = -1;
+    const double *b = nullptr;
+    double *x = nullptr;
+};
+
+}  // namespace
+
+struct hh_ctx {
+    hh_lattice lat;
+    hh_params prm;
+    cudaStream_t stream;
+    Geo geo;
+    int N;
+    int cap_rhs;
+    int max_grid;
+    long long timeout_ns;
+    // fields
+    double *sigma, *sigma0, *L64, *pi, *chi, *xsol, *tmp, *F;
+    float *L32, *tmp32a, *tmp32b;
+    // CG workspace (cap_rhs vectors each)
+    double *r, *p, *t;
+    float *r32, *p32, *t32, *x32;
+    // engine
+    EngSystem *d_sys;
+    EngState *d_state[2];
+    EngTile *d_tiles;
+    double *d_part_tt, *d_part_rr;
+    BarrierCtl *d_ctl;
+    EngStats *d_stats;
+    int max_tiles;
+    Plan plan;
+    EngTotals *d_totals;
+    // counters and optional CUDA-event profile of the engine launches
+    long long n_launch, n_engine;
+    int profile;
+    int ev_cap, ev_used;
+    cudaEvent_t *ev;
+    // HMC scalars
+    HmcScalars *d_sc;
+    double *d_energy_part;
+    double *d_energy_out;   // [0] S or H scratch
+    void *h_pinned;         // host readback buffer
+};
+
+namespace {
+
+#define HH_TRY(expr)                      \
+    do {                                  \
+        cudaError_t e__ = (expr);         \
+        if (e__ != cudaSuccess) return HH_ECUDA; \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc((void **)p, n * sizeof(T));
+}
+
+void free_ctx(hh_ctx *c)
+{
+    void *ptrs[] = {c->sigma, c->sigma0, c->L64, c->pi, c->chi, c->xsol, c->tmp, c->F, c->L32,
+                    c->tmp32a, c->tmp32b, c->r, c->p, c->t, c->r32, c->p32, c->t32, c->x32,
+                    c->d_sys, c->d_state[0], c->d_state[1], c->d_tiles, c->d_part_tt,
+                    c->d_part_rr, c->d_ctl, c->d_stats, c->d_sc, c->d_energy_part,
+                    c->d_energy_out};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    if (c->d_totals) cudaFree(c->d_totals);
+    if (c->ev) {
+        for (int i = 0; i < c->ev_cap; ++i)
+            if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+        free(c->ev);
+    }
+}
+
+int engine_tiles_per_system(const hh_ctx *c, int nsys)
+{
+    // Enough tiles to give every block of the grid work, at least 256 sites each.
+    int by_size = (c->N + 255) / 256;
+    int want = (c->max_grid + nsys - 1) / nsys;
+    if (want < 1) want = 1;
+    return by_size < want ? by_size : want;
+}
+
+// Build (or reuse) the engine plan for n_rhs systems b_a -> x_a.
+int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
+{
+    Plan &P = c->plan;
+    if (P.nsys == n_rhs && P.b == b && P.x == x && P.precision == c->prm.precision) return HH_OK;
+    int tps = engine_tiles_per_system(c, n_rhs);
+    int ntiles = tps * n_rhs;
+    if (ntiles > c->max_tiles) return HH_EINVAL;
+    int grid = ntiles < c->max_grid ? ntiles : c->max_grid;
+    std::vector<EngSystem> sys(n_rhs);
+    std::vector<EngTile> tiles;
+    tiles.reserve(ntiles);
+    int chunk = (c->N + tps - 1) / tps;
+    chunk = (chunk + 31) / 32 * 32;
+    for (int a = 0; a < n_rhs; ++a) {
+        EngSystem &Y = sys[a];
+        memset(&Y, 0, sizeof(Y));
+        Y.g = c->geo;
+        Y.h = c->prm.t * c->prm.dtau;
+        Y.L64 = c->L64;
+        Y.L32 = c->L32;
+        Y.b = b + (size_t)a * c->N;
+        Y.x = x + (size_t)a * c->N;
+        size_t off = (size_t)a * c->N;
+        Y.r = c->r + off;
+        Y.p = c->p + off;
+        Y.t = c->t + off;
+        Y.r32 = c->r32 + off;
+        Y.p32 = c->p32 + off;
+        Y.t32 = c->t32 + off;
+        Y.x32 = c->x32 + off;
+        Y.tile0 = (int)tiles.size();
+        for (int s0 = 0; s0 < c->N; s0 += chunk) {
+            EngTile T;
+            T.sys = a;
+            T.begin = s0;
+            T.end = s0 + chunk < c->N ? s0 + chunk : c->N;
+            tiles.push_back(T);
+        }
+        Y.ntiles = (int)tiles.size() - Y.tile0;
+        Y.owner = Y.tile0 % grid;
+        Y.precision = c->prm.precision;
+        Y.tol2 = c->prm.cg_tol * c->prm.cg_tol;
+        Y.delta2 = c->prm.reliable_delta * c->prm.reliable_delta;
+        Y.maxit = c->prm.cg_maxit;
+    }
+    ntiles = (int)tiles.size();
+    grid = ntiles < c->max_grid ? ntiles : c->max_grid;
+    for (auto &Y : sys) Y.owner = Y.tile0 % grid;
+    // Pageable sources: the copies have consumed the host buffers on return.
+    HH_TRY(cudaMemcpyAsync(c->d_sys, sys.data(), sizeof(EngSystem) * n_rhs, cudaMemcpyHostToDevice,
+                           c->stream));
+    HH_TRY(cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(EngTile) * ntiles,
+                           cudaMemcpyHostToDevice, c->stream));
+    P.nsys = n_rhs;
+    P.ntiles = ntiles;
+    P.grid = grid;
+    P.b = b;
+    P.x = x;
+    P.precision = c->prm.precision;
+    return HH_OK;
+}
+
+// Enqueue one complete solve of the current plan and fold its statistics.
+int run_engine(hh_ctx *c)
+{
+    const Plan &P = c->plan;
+    k_engine_reset<<<1, 64, 0, c->stream>>>(c->d_state[0], c->d_state[1], P.nsys, c->d_ctl,
+                                            c->timeout_ns);
+    HH_TRY(cudaGetLastError());
+    EngLaunch L;
+    L.sys = c->d_sys;
+    L.state[0] = c->d_state[0];
+    L.state[1] = c->d_state[1];
+    L.tiles = c->d_tiles;
+    L.part_tt = c->d_part_tt;
+    L.part_rr = c->d_part_rr;
+    L.ctl = c->d_ctl;
+    L.nsys = P.nsys;
+    L.ntiles = P.ntiles;
+    // Each CG step is one engine iteration, each true-residual check one more;
+    // the cap is a safety bound well above maxit.
+    L.max_iters = 3LL * (long long)c->prm.cg_maxit + 64;
+    bool rec = c->profile && c->ev_used + 2 <= c->ev_cap;
+    if (rec) HH_TRY(cudaEventRecord(c->ev[c->ev_used], c->stream));
+    HH_TRY(engine_launch(L, P.grid, ENGINE_BLOCK, c->stream));
+    if (rec) {
+        HH_TRY(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
+        c->ev_used += 2;
+    }
+    k_engine_fold<<<1, 32, 0, c->stream>>>(c->d_state[0], c->d_state[1], P.nsys, c->d_ctl,
+                                           c->d_stats, c->d_totals);
+    HH_TRY(cudaGetLastError());
+    c->n_launch += 3;
+    c->n_engine += 1;
+    return HH_OK;
+}
+
+int read_stats(hh_ctx *c, EngStats *out)
+{
+    HH_TRY(cudaMemcpyAsync(c->h_pinned, c->d_stats, sizeof(EngStats), cudaMemcpyDeviceToHost,
+                           c->stream));
+    HH_TRY(cudaStreamSynchronize(c->stream));
+    memcpy(out, c->h_pinned, sizeof(EngStats));
+    return HH_OK;
+}
+
+int stats_status(const EngStats &s)
+{
+    if (s.error != 0) return s.error;
+    return s.worst_status;
+}
+
+void fill_solve_info(const EngStats &s, hh_solve_info *info)
+{
+    if (!info) return;
+    info->iterations = s.max_iters;
+    info->reliable_updates = s.n_ru;
+    info->true_relres = s.max_relres;
+    info->converged = (s.worst_status == 0 && s.error == 0) ? 1 : 0;
+}
+
+int ensure_rhs(hh_ctx *c, int n_rhs)
+{
+    return n_rhs >= 1 && n_rhs <= c->cap_rhs ? HH_OK : HH_EINVAL;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hh_default_params(hh_params *p)
+{
+    if (!p) return;
+    p->t = 1.0;
+    p->dtau = 0.05;
+    p->A = 0.5;
+    p->precision = HH_FP64;
+    p->cg_tol = 1e-10;
+    p->cg_maxit = 1000000;
+    p->reliable_delta = 0.1;
+    p->seed = 0;
+    p->n_pf = 2;
+    p->chain_id = 0;
+}
+
+const char *hh_strerror(int code)
+{
+    switch (code) {
+    case HH_OK: return "ok";
+    case HH_EINVAL: return "invalid argument";
+    case HH_ENOMEM: return "out of memory";
+    case HH_ECUDA: return "CUDA runtime error";
+    case HH_ENOCONV: return "CG did not converge within cg_maxit";
+    case HH_ENUMERIC: return "NaN or Inf in a reduction";
+    case HH_ETIMEOUT: return "device-side wait timed out";
+    case HH_EBUSY: return "no free slot or memory budget";
+    default: return "unknown error";
+    }
+}
+
+int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cuda_stream)
+{
+    if (!out || !lat || !p) return HH_EINVAL;
+    *out = nullptr;
+    if (lat->d != 1 && lat->d != 3) return HH_EINVAL;
+    if (lat->nx < 2 || lat->ntau < 2) return HH_EINVAL;
+    if (p->n_pf < 1 || p->n_pf > 64) return HH_EINVAL;
+    if (p->precision != HH_FP64 && p->precision != HH_MIXED) return HH_EINVAL;
+    if (!(p->cg_tol > 0.0) || p->cg_maxit < 1) return HH_EINVAL;
+    long long V = lat->d == 1 ? lat->nx : (long long)lat->nx * lat->nx * lat->nx;
+    long long N = V * lat->ntau;
+    if (N >= (1LL << 31) - 1024) return HH_EINVAL;
+
+    hh_ctx *c = new (std::nothrow) hh_ctx;
+    if (!c) return HH_ENOMEM;
+    memset(c, 0, sizeof(*c));
+    c->lat = *lat;
+    c->prm = *p;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->geo = make_geo(lat->d, lat->nx, lat->ntau);
+    c->N = (int)N;
+    c->cap_rhs = p->n_pf > 4 ? p->n_pf : 4;
+    c->timeout_ns = 5LL * 1000 * 1000 * 1000;
+    const char *bps = getenv("HH_ENGINE_BLOCKS_PER_SM");
+    int max_grid = engine_max_grid(ENGINE_BLOCK);
+    if (max_grid <= 0) {
+        delete c;
+        return HH_ECUDA;
+    }
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int per = bps ? atoi(bps) : 2;
+    if (per < 1) per = 1;
+    if (per * nsm < max_grid) max_grid = per * nsm;
+    c->max_grid = max_grid;
+    c->max_tiles = c->cap_rhs * (max_grid + 1) + 64;
+
+    size_t n = (size_t)N, nr = (size_t)c->cap_rhs * n;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = dalloc(&c->sigma, n);
+    if (e == cudaSuccess) e = dalloc(&c->sigma0, n);
+    if (e == cudaSuccess) e = dalloc(&c->L64, n);
+    if (e == cudaSuccess) e = dalloc(&c->pi, n);
+    if (e == cudaSuccess) e = dalloc(&c->tmp, n);
+    if (e == cudaSuccess) e = dalloc(&c->F, n);
+    if (e == cudaSuccess) e = dalloc(&c->L32, n);
+    if (e == cudaSuccess) e = dalloc(&c->tmp32a, n);
+    if (e == cudaSuccess) e = dalloc(&c->tmp32b, n);
+    if (e == cudaSuccess) e = dalloc(&c->chi, nr);
+    if (e == cudaSuccess) e = dalloc(&c->xsol, nr);
+    if (e == cudaSuccess) e = dalloc(&c->r, nr);
+    if (e == cudaSuccess) e = dalloc(&c->p, nr);
+    if (e == cudaSuccess) e = dalloc(&c->t, nr);
+    if (e == cudaSuccess) e = dalloc(&c->r32, nr);
+    if (e == cudaSuccess) e = dalloc(&c->p32, nr);
+    if (e == cudaSuccess) e = dalloc(&c->t32, nr);
+    if (e == cudaSuccess) e = dalloc(&c->x32, nr);
+    if (e == cudaSuccess) e = dalloc(&c->d_sys, (size_t)c->cap_rhs);
+    if (e == cudaSuccess) e = dalloc(&c->d_state[0], (size_t)c->cap_rhs);
+    if (e == cudaSuccess) e = dalloc(&c->d_state[1], (size_t)c->cap_rhs);
+    if (e == cudaSuccess) e = dalloc(&c->d_tiles, (size_t)c->max_tiles);
+    if (e == cudaSuccess) e = dalloc(&c->d_part_tt, (size_t)c->max_tiles);
+    if (e == cudaSuccess) e = dalloc(&c->d_part_rr, (size_t)c->max_tiles);
+    if (e == cudaSuccess) e = dalloc(&c->d_ctl, 1);
+    if (e == cudaSuccess) e = dalloc(&c->d_stats, 1);
+    if (e == cudaSuccess) e = dalloc(&c->d_sc, 1);
+    if (e == cudaSuccess) e = dalloc(&c->d_totals, 1);
+    if (e == cudaSuccess) e = dalloc(&c->d_energy_part, (size_t)energy_blocks(c->N));
+    if (e == cudaSuccess) e = dalloc(&c->d_energy_out, 4);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_pinned, 4096);
+    if (e != cudaSuccess) {
+        free_ctx(c);
+        delete c;
+        return e == cudaErrorMemoryAllocation ? HH_ENOMEM : HH_ECUDA;
+    }
+    e = cudaMemsetAsync(c->sigma, 0, n * sizeof(double), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_ctl, 0, sizeof(BarrierCtl), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_sc, 0, sizeof(HmcScalars), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_totals, 0, sizeof(EngTotals), c->stream);
+    if (e == cudaSuccess) e = launch_links(c->geo, p->A, c->sigma, c->L64, c->L32, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        free_ctx(c);
+        delete c;
+        return HH_ECUDA;
+    }
+    *out = c;
+    return HH_OK;
+}
+
+int hh_destroy(hh_ctx *c)
+{
+    if (!c) return HH_OK;
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+    delete c;
+    return HH_OK;
+}
+
+long long hh_nsites(const hh_ctx *c)
+{
+    return c ? (long long)c->N : 0;
+}
+
+int hh_set_field(hh_ctx *c, const double *sigma, int on_device)
+{
+    if (!c || !sigma) return HH_EINVAL;
+    size_t bytes = (size_t)c->N * sizeof(double);
+    if (on_device) {
+        HH_TRY(cudaMemcpyAsync(c->sigma, sigma, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        HH_TRY(cudaMemcpyAsync(c->sigma, sigma, bytes, cudaMemcpyHostToDevice, c->stream));
+    }
+    HH_TRY(launch_links(c->geo, c->prm.A, c->sigma, c->L64, c->L32, c->stream));
+    c->n_launch += 1;
+    if (!on_device) HH_TRY(cudaStreamSynchronize(c->stream));
+    return HH_OK;
+}
+
+int hh_get_field(hh_ctx *c, double *sigma, int on_device)
+{
+    if (!c || !sigma) return HH_EINVAL;
+    size_t bytes = (size_t)c->N * sizeof(double);
+    if (on_device) {
+        HH_TRY(cudaMemcpyAsync(sigma, c->sigma, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        HH_TRY(cudaMemcpyAsync(sigma, c->sigma, bytes, cudaMemcpyDeviceToHost, c->stream));
+        HH_TRY(cudaStreamSynchronize(c->stream));
+    }
+    return HH_OK;
+}
+
+int hh_init_field_random(hh_ctx *c, uint64_t seed)
+{
+    if (!c) return HH_EINVAL;
+    HH_TRY(launch_init_field(c->sigma, c->N, seed, c->prm.chain_id, c->stream));
+    HH_TRY(launch_links(c->geo, c->prm.A, c->sigma, c->L64, c->L32, c->stream));
+    c->n_launch += 2;
+    return HH_OK;
+}
+
+int hh_apply(hh_ctx *c, int op, const void *x, void *y, int dtype)
+{
+    if (!c || !x || !y || x == y) return HH_EINVAL;
+    if (op != HH_OP_M && op != HH_OP_MT && op != HH_OP_MTM) return HH_EINVAL;
+    const double h = c->prm.t * c->prm.dtau;
+    if (dtype == HH_DTYPE_F64) {
+        const double *xd = (const double *)x;
+        double *yd = (double *)y;
+        if (op == HH_OP_MTM) {
+            HH_TRY(launch_apply_f64(c->geo, 0, h, c->L64, xd, c->tmp, c->stream));
+            HH_TRY(launch_apply_f64(c->geo, 1, h, c->L64, c->tmp, yd, c->stream));
+        } else {
+            HH_TRY(launch_apply_f64(c->geo, op, h, c->L64, xd, yd, c->stream));
+        }
+    } else if (dtype == HH_DTYPE_F32) {
+        const float *xf = (const float *)x;
+        float *yf = (float *)y;
+        if (op == HH_OP_MTM) {
+            HH_TRY(launch_apply_f32(c->geo, 0, (float)h, c->L32, xf, c->tmp32a, c->stream));
+            HH_TRY(launch_apply_f32(c->geo, 1, (float)h, c->L32, c->tmp32a, yf, c->stream));
+        } else {
+            HH_TRY(launch_apply_f32(c->geo, op, (float)h, c->L32, xf, yf, c->stream));
+        }
+    } else {
+        return HH_EINVAL;
+    }
+    c->n_launch += (op == HH_OP_MTM) ? 2 : 1;
+    return HH_OK;
+}
+
+int hh_solve(hh_ctx *c, const double *b, double *x, int n_rhs, hh_solve_info *info)
+{
+    if (!c || !b || !x) return HH_EINVAL;
+    int rc = ensure_rhs(c, n_rhs);
+    if (rc) return rc;
+    rc = make_plan(c, b, x, n_rhs);
+    if (rc) return rc;
+    k_zero_stats<<<1, 32, 0, c->stream>>>(c->d_stats);
+    HH_TRY(cudaGetLastError());
+    c->n_launch += 1;
+    rc = run_engine(c);
+    if (rc) return rc;
+    if (!info) return HH_OK;
+    EngStats s;
+    rc = read_stats(c, &s);
+    if (rc) return rc;
+    fill_solve_info(s, info);
+    return stats_status(s);
+}
+
+int hh_force(hh_ctx *c, const double *chi, int n_rhs, double *F, hh_solve_info *info)
+{
+    if (!c || !chi || !F) return HH_EINVAL;
+    int rc = ensure_rhs(c, n_rhs);
+    if (rc) return rc;
+    rc = make_plan(c, chi, c->xsol, n_rhs);
+    if (rc) return rc;
+    k_zero_stats<<<1, 32, 0, c->stream>>>(c->d_stats);
+    HH_TRY(cudaGetLastError());
+    c->n_launch += 1;
+    rc = run_engine(c);
+    if (rc) return rc;
+    HH_TRY(launch_force(c->geo, c->prm.t * c->prm.dtau, c->prm.A, c->sigma, c->L64, c->xsol, n_rhs,
+                        nullptr, 0.0, F, c->stream));
+    c->n_launch += 1;
+    if (!info) return HH_OK;
+    EngStats s;
+    rc = read_stats(c, &s);
+    if (rc) return rc;
+    fill_solve_info(s, info);
+    return stats_status(s);
+}
+
+int hh_action(hh_ctx *c, const double *chi, int n_rhs, double *S, hh_solve_info *info)
+{
+    if (!c || !chi || !S) return HH_EINVAL;
+    int rc = ensure_rhs(c, n_rhs);
+    if (rc) return rc;
+    rc = make_plan(c, chi, c->xsol, n_rhs);
+    if (rc) return rc;
+    k_zero_stats<<<1, 32, 0, c->stream>>>(c->d_stats);
+    HH_TRY(cudaGetLastError());
+    c->n_launch += 1;
+    rc = run_engine(c);
+    if (rc) return rc;
+    HH_TRY(launch_energy(c->N, nullptr, chi, c->xsol, n_rhs, c->d_energy_part, c->d_energy_out,
+                         c->stream));
+    c->n_launch += 2;
+    EngStats s;
+    rc = read_stats(c, &s);
+    if (rc) return rc;
+    HH_TRY(cudaMemcpy(S, c->d_energy_out, sizeof(double), cudaMemcpyDeviceToHost));
+    fill_solve_info(s, info);
+    return stats_status(s);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Leapfrog on (ctx sigma, pi) at fixed chi (Sec. 4.1).  If h0/h1 are non-null
+// the Hamiltonian before/after is written to those device doubles, reusing the
+// first and last solves.  Enqueues only.
+int leapfrog_enqueue(hh_ctx *c, double *pi, const double *chi, int n_rhs, int n_md, double dt,
+                     double *h0, double *h1)
+{
+    const double h = c->prm.t * c->prm.dtau, A = c->prm.A;
+    int rc = make_plan(c, chi, c->xsol, n_rhs);
+    if (rc) return rc;
+    rc = run_engine(c);
+    if (rc) return rc;
+    if (h0) HH_TRY(launch_energy(c->N, pi, chi, c->xsol, n_rhs, c->d_energy_part, h0, c->stream));
+    HH_TRY(launch_force(c->geo, h, A, c->sigma, c->L64, c->xsol, n_rhs, pi, 0.5 * dt, nullptr,
+                        c->stream));
+    for (int k = 1; k <= n_md; ++k) {
+        HH_TRY(launch_sigma_step(c->geo, A, dt, c->sigma, pi, c->L64, c->L32, c->stream));
+        rc = run_engine(c);
+        if (rc) return rc;
+        double eps = (k == n_md) ? 0.5 * dt : dt;
+        HH_TRY(launch_force(c->geo, h, A, c->sigma, c->L64, c->xsol, n_rhs, pi, eps, nullptr,
+                            c->stream));
+    }
+    if (h1) HH_TRY(launch_energy(c->N, pi, chi, c->xsol, n_rhs, c->d_energy_part, h1, c->stream));
+    c->n_launch += (h0 ? 2 : 0) + (h1 ? 2 : 0) + (n_md + 1) + n_md;
+    return HH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hh_leapfrog(hh_ctx *c, double *pi, const double *chi, int n_rhs, int n_md, double dt,
+                hh_solve_info *info)
+{
+    if (!c || !pi || !chi || n_md < 1) return HH_EINVAL;
+    int rc = ensure_rhs(c, n_rhs);
+    if (rc) return rc;
+    k_zero_stats<<<1, 32, 0, c->stream>>>(c->d_stats);
+    HH_TRY(cudaGetLastError());
+    c->n_launch += 1;
+    rc = leapfrog_enqueue(c, pi, chi, n_rhs, n_md, dt, nullptr, nullptr);
+    if (rc) return rc;
+    if (!info) return HH_OK;
+    EngStats s;
+    rc = read_stats(c, &s);
+    if (rc) return rc;
+    fill_solve_info(s, info);
+    return stats_status(s);
+}
+
+int hh_trajectory(hh_ctx *c, int n_md, double dt, uint64_t traj, hh_traj_info *info)
+{
+    if (!c || n_md < 1) return HH_EINVAL;
+    const int npf = c->prm.n_pf;
+    const double h = c->prm.t * c->prm.dtau;
+    const uint64_t seed = c->prm.seed, chain = c->prm.chain_id;
+    k_zero_stats<<<1, 32, 0, c->stream>>>(c->d_stats);
+    HH_TRY(cudaGetLastError());
+    c->n_launch += 1;
+    // Momenta and pseudofermion heatbath chi_a = M^T xi_a (Eqs. (11)-(12)).
+    HH_TRY(launch_gaussian(c->pi, c->N, seed, 1, 0, traj, chain, c->stream));
+    for (int a = 0; a < npf; ++a) {
+        HH_TRY(launch_gaussian(c->tmp, c->N, seed, 2, a, traj, chain, c->stream));
+        HH_TRY(launch_apply_f64(c->geo, 1, h, c->L64, c->tmp, c->chi + (size_t)a * c->N, c->stream));
+    }
+    HH_TRY(cudaMemcpyAsync(c->sigma0, c->sigma, (size_t)c->N * sizeof(double),
+                           cudaMemcpyDeviceToDevice, c->stream));
+    int rc = leapfrog_enqueue(c, c->pi, c->chi, npf, n_md, dt, &c->d_sc->H0, &c->d_sc->H1);
+    if (rc) return rc;
+    HH_TRY(launch_metropolis(c->d_sc, seed, traj, chain, c->stream));
+    HH_TRY(launch_restore(c->geo, c->prm.A, c->d_sc, c->sigma, c->sigma0, c->L64, c->L32, c->stream));
+    c->n_launch += (1 + npf) + npf + 2;
+    if (!info) return HH_OK;
+    char *hp = (char *)c->h_pinned;
+    HH_TRY(cudaMemcpyAsync(hp, c->d_stats, sizeof(EngStats), cudaMemcpyDeviceToHost, c->stream));
+    HH_TRY(cudaMemcpyAsync(hp + 256, c->d_sc, sizeof(HmcScalars), cudaMemcpyDeviceToHost, c->stream));
+    HH_TRY(cudaStreamSynchronize(c->stream));
+    EngStats s;
+    HmcScalars sc;
+    memcpy(&s, hp, sizeof(s));
+    memcpy(&sc, hp + 256, sizeof(sc));
+    info->H0 = sc.H0;
+    info->H1 = sc.H1;
+    info->dH = sc.dH;
+    info->u = sc.u;
+    info->accepted = sc.accepted;
+    info->cg_iterations = (int)s.cg_iters;
+    info->n_solves = s.n_solves;
+    info->max_true_relres = s.max_relres;
+    return stats_status(s);
+}
+
+int hh_counters_reset(hh_ctx *c, int profile_engine)
+{
+    if (!c) return HH_EINVAL;
+    HH_TRY(cudaStreamSynchronize(c->stream));
+    c->n_launch = 0;
+    c->n_engine = 0;
+    c->ev_used = 0;
+    c->profile = profile_engine ? 1 : 0;
+    if (c->profile && !c->ev) {
+        const int cap = 16384;
+        c->ev = (cudaEvent_t *)calloc(cap, sizeof(cudaEvent_t));
+        if (!c->ev) return HH_ENOMEM;
+        c->ev_cap = cap;
+        for (int i = 0; i < cap; ++i) HH_TRY(cudaEventCreate(&c->ev[i]));
+    }
+    HH_TRY(cudaMemsetAsync(c->d_totals, 0, sizeof(EngTotals), c->stream));
+    HH_TRY(cudaStreamSynchronize(c->stream));
+    return HH_OK;
+}
+
+int hh_counters_get(hh_ctx *c, hh_counters *out)
+{
+    if (!c || !out) return HH_EINVAL;
+    EngTotals t;
+    HH_TRY(cudaMemcpyAsync(c->h_pinned, c->d_totals, sizeof(EngTotals), cudaMemcpyDeviceToHost,
+                           c->stream));
+    HH_TRY(cudaStreamSynchronize(c->stream));
+    memcpy(&t, c->h_pinned, sizeof(t));
+    double ms = 0.0;
+    for (int i = 0; i + 1 < c->ev_used; i += 2) {
+        float m = 0.0f;
+        HH_TRY(cudaEventElapsedTime(&m, c->ev[i], c->ev[i + 1]));
+        ms += m;
+    }
+    out->kernel_launches = c->n_launch;
+    out->engine_launches = c->n_engine;
+    out->engine_ms = ms;
+    out->cg_steps = t.cg_steps;
+    out->ru_steps = t.ru_steps;
+    out->solves = t.solves;
+    out->sites = c->N;
+    return HH_OK;
+}
+
+}  // extern "C"

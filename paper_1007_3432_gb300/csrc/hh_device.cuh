@@ -1,0 +1,262 @@
+// Device-side building blocks of the GB300 Hubbard HMC library: lattice
+// geometry with division by invariant integers, the stencil of the fermion
+// matrix, the Philox counter generator, deterministic block reductions and a
+// grid barrier whose waits are bounded in time.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hh {
+
+// ---------------------------------------------------------------------------
+// Division by a run-time invariant 32-bit divisor (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994, round-up
+// variant with a 33-bit multiplier): q = (umulhi(n, m) + n) >> s.
+// ---------------------------------------------------------------------------
+struct FastDiv {
+    uint32_t d, m, s;
+};
+
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    FastDiv f;
+    f.d = d;
+    uint32_t s = 0;
+    while ((1ull << s) < d) ++s;
+    f.s = s;
+    // m = floor(2^32 (2^s - d) / d) + 1 ; zero when d is a power of two.
+    uint64_t num = ((1ull << s) - d) << 32;
+    f.m = (uint32_t)(num / d + 1ull);
+    if (d == 1) f.m = 0;
+    if ((1ull << s) == d) f.m = 0;
+    return f;
+}
+
+__host__ __device__ inline uint32_t fd_div(uint32_t n, const FastDiv &f)
+{
+#ifdef __CUDA_ARCH__
+    uint32_t hi = __umulhi(n, f.m);
+#else
+    uint32_t hi = (uint32_t)(((uint64_t)n * f.m) >> 32);
+#endif
+    return (uint32_t)(((uint64_t)hi + n) >> f.s);
+}
+
+// ---------------------------------------------------------------------------
+// Lattice geometry.  Site index i = s + V * tau with the spatial index
+// s = x + Nx (y + Nx z) (d = 3) or s = x (d = 1); x runs fastest.
+// ---------------------------------------------------------------------------
+struct Geo {
+    int d, nx, ntau, V;
+    int N;               // V * ntau
+    FastDiv f_nx, f_V;
+};
+
+inline Geo make_geo(int d, int nx, int ntau)
+{
+    Geo g;
+    g.d = d;
+    g.nx = nx;
+    g.ntau = ntau;
+    g.V = (d == 1) ? nx : nx * nx * nx;
+    g.N = g.V * ntau;
+    g.f_nx = make_fastdiv((uint32_t)nx);
+    g.f_V = make_fastdiv((uint32_t)g.V);
+    return g;
+}
+
+// Neighbour indices of site i: 2d spatial neighbours (periodic) and the
+// previous / next time slice (the antiperiodic sign lives in the links).
+struct Nbr {
+    int sp[6];
+    int prev, next;
+};
+
+__device__ __forceinline__ void neighbours(const Geo &g, int i, Nbr &nb)
+{
+    uint32_t tau = fd_div((uint32_t)i, g.f_V);
+    int s = i - (int)tau * g.V;
+    uint32_t yz = fd_div((uint32_t)s, g.f_nx);
+    int x = s - (int)yz * g.nx;
+    nb.sp[0] = (x == g.nx - 1) ? i - (g.nx - 1) : i + 1;
+    nb.sp[1] = (x == 0) ? i + (g.nx - 1) : i - 1;
+    if (g.d == 3) {
+        uint32_t z = fd_div(yz, g.f_nx);
+        int y = (int)yz - (int)z * g.nx;
+        int sy = g.nx, sz = g.nx * g.nx;
+        nb.sp[2] = (y == g.nx - 1) ? i - (g.nx - 1) * sy : i + sy;
+        nb.sp[3] = (y == 0) ? i + (g.nx - 1) * sy : i - sy;
+        nb.sp[4] = ((int)z == g.nx - 1) ? i - (g.nx - 1) * sz : i + sz;
+        nb.sp[5] = (z == 0) ? i + (g.nx - 1) * sz : i - sz;
+    }
+    nb.prev = (tau == 0) ? i + (g.ntau - 1) * g.V : i - g.V;
+    nb.next = ((int)tau == g.ntau - 1) ? i - (g.ntau - 1) * g.V : i + g.V;
+}
+
+// Sum of the 2d spatial neighbours in a fixed order.
+template <typename T>
+__device__ __forceinline__ T hop_sum(const Geo &g, const T *v, const Nbr &nb)
+{
+    T s = v[nb.sp[0]] + v[nb.sp[1]];
+    if (g.d == 3) s += (v[nb.sp[2]] + v[nb.sp[3]]) + (v[nb.sp[4]] + v[nb.sp[5]]);
+    return s;
+}
+
+// (M v)_i = v_i - h sum_nbr v + L(prev) v(prev)        (Eq. (10))
+template <typename T>
+__device__ __forceinline__ T stencil_M(const Geo &g, T h, const T *__restrict__ L, const T *v, int i,
+                                       const Nbr &nb)
+{
+    T acc = fma(-h, hop_sum(g, v, nb), v[i]);
+    return fma(__ldg(L + nb.prev), v[nb.prev], acc);
+}
+
+// (M^T v)_i = v_i - h sum_nbr v + L(i) v(next)
+template <typename T>
+__device__ __forceinline__ T stencil_MT(const Geo &g, T h, const T *__restrict__ L, const T *v, int i,
+                                        const Nbr &nb)
+{
+    T acc = fma(-h, hop_sum(g, v, nb), v[i]);
+    return fma(__ldg(L + i), v[nb.next], acc);
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Counter layout of the
+// library: (block, tag | a << 8, trajectory, chain), key (seed, 0).
+// ---------------------------------------------------------------------------
+struct U64x4 {
+    uint64_t v[4];
+};
+
+__device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                               uint64_t k0, uint64_t k1)
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    U64x4 o;
+    o.v[0] = c0;
+    o.v[1] = c1;
+    o.v[2] = c2;
+    o.v[3] = c3;
+    return o;
+}
+
+__device__ __forceinline__ double u53(uint64_t w)
+{
+    return (double)(w >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions: a fixed tree inside the warp, then warps in order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;  // valid in lane 0
+}
+
+// Block-wide sum; every thread must call it; the result is valid in thread 0.
+// 'red' must hold blockDim.x / 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        int nw = blockDim.x >> 5;
+        for (int j = 0; j < nw; ++j) s += red[j];
+    }
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// Grid barrier for cooperative (co-resident) launches.  Sense by generation
+// counter; every wait is bounded by a wall-clock budget read from the global
+// timer, after which the barrier records an error and returns false.
+// ---------------------------------------------------------------------------
+struct BarrierCtl {
+    unsigned int count;
+    unsigned int gen;
+    int error;          // 0, or a negative library error code
+    int active;         // systems still running (engine bookkeeping)
+    long long k;        // engine iteration counter, persists across launches
+    long long timeout_ns;
+    int pad[2];
+};
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int *p)
+{
+    return *(const volatile int *)p;
+}
+
+// Returns false if the barrier timed out or another block recorded an error.
+__device__ __forceinline__ bool grid_barrier(BarrierCtl *ctl, unsigned nblocks, unsigned &gen_local,
+                                             int *s_flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned g = gen_local;
+        int ok = 1;
+        __threadfence();
+        unsigned old = atomicAdd(&ctl->count, 1u);
+        if (old == nblocks - 1) {
+            ctl->count = 0;
+            __threadfence();
+            atomicExch(&ctl->gen, g + 1);
+        } else {
+            uint64_t t0 = global_ns();
+            unsigned spins = 0;
+            while (ld_acquire_u32(&ctl->gen) == g) {
+                if ((++spins & 255u) == 0) {
+                    if (ld_volatile_i32(&ctl->error) != 0) {
+                        ok = 0;
+                        break;
+                    }
+                    if ((long long)(global_ns() - t0) > ctl->timeout_ns) {
+                        atomicCAS(&ctl->error, 0, -6);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        if (ld_volatile_i32(&ctl->error) != 0) ok = 0;
+        gen_local = g + 1;
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+}  // namespace hh

@@ -1,0 +1,255 @@
+// Non-persistent kernels of the HMC path (Sec. 4.1): links, stencil applies,
+// Philox draws, the pseudofermion force with the fused momentum update, the
+// sigma step, energy reductions and the Metropolis test.
+#include "hh_kernels.cuh"
+
+namespace hh {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+inline int grid_for(long long n, int per_thread = 1)
+{
+    long long b = (n + (long long)kBlock * per_thread - 1) / ((long long)kBlock * per_thread);
+    if (b < 1) b = 1;
+    if (b > 65535LL * 16) b = 65535LL * 16;
+    return (int)b;
+}
+
+__device__ __forceinline__ double link_value(const Geo &g, double A, double sigma, int i)
+{
+    uint32_t tau = fd_div((uint32_t)i, g.f_V);
+    double c = 1.0 + A * sin(sigma);
+    return ((int)tau == g.ntau - 1) ? c : -c;
+}
+
+__global__ void k_links(Geo g, double A, const double *__restrict__ sigma, double *__restrict__ L64,
+                        float *__restrict__ L32)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += gridDim.x * blockDim.x) {
+        double l = link_value(g, A, sigma[i], i);
+        L64[i] = l;
+        L32[i] = (float)l;
+    }
+}
+
+__global__ void k_sigma_step(Geo g, double A, double dt, double *__restrict__ sigma,
+                             const double *__restrict__ pi, double *__restrict__ L64,
+                             float *__restrict__ L32)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += gridDim.x * blockDim.x) {
+        double s = fma(dt, pi[i], sigma[i]);
+        sigma[i] = s;
+        double l = link_value(g, A, s, i);
+        L64[i] = l;
+        L32[i] = (float)l;
+    }
+}
+
+template <typename T>
+__global__ void k_apply(Geo g, int op, T h, const T *__restrict__ L, const T *__restrict__ x,
+                        T *__restrict__ y)
+{
+    Nbr nb;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += gridDim.x * blockDim.x) {
+        neighbours(g, i, nb);
+        y[i] = (op == 0) ? stencil_M<T>(g, h, L, x, i, nb) : stencil_MT<T>(g, h, L, x, i, nb);
+    }
+}
+
+// One thread per Philox block of four elements.
+__global__ void k_gaussian(double *__restrict__ out, int n, uint64_t seed, uint64_t ctr1,
+                           uint64_t traj, uint64_t chain)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    int nblk = (n + 3) >> 2;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+        U64x4 w = philox4x64_10((uint64_t)b, ctr1, traj, chain, seed, 0);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            double u1 = u53(w.v[2 * j]), u2 = u53(w.v[2 * j + 1]);
+            double rad = sqrt(-2.0 * log(1.0 - u1));
+            double th = two_pi * u2;
+            int i0 = 4 * b + 2 * j;
+            if (i0 < n) out[i0] = rad * cos(th);
+            if (i0 + 1 < n) out[i0 + 1] = rad * sin(th);
+        }
+    }
+}
+
+__global__ void k_init_field(double *__restrict__ sigma, int n, uint64_t seed, uint64_t chain)
+{
+    const double pi = 3.14159265358979323846264338328;
+    int nblk = (n + 3) >> 2;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+        U64x4 w = philox4x64_10((uint64_t)b, 0, 0, chain, seed, 0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int i = 4 * b + j;
+            // Explicit roundings: (-pi) + (2 pi) u with no fused multiply-add.
+            if (i < n) sigma[i] = __dadd_rn(-pi, __dmul_rn(2.0 * pi, u53(w.v[j])));
+        }
+    }
+}
+
+// F_i = -sum_a (M x_a)(next(i)) s(tau_i) A cos(sigma_i) x_a(i).
+__global__ void k_force(Geo g, double h, double A, const double *__restrict__ sigma,
+                        const double *__restrict__ L64, const double *__restrict__ x, int n_rhs,
+                        double *__restrict__ pi, double eps, double *__restrict__ F_out)
+{
+    Nbr nb, nn;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += gridDim.x * blockDim.x) {
+        neighbours(g, i, nb);
+        const int j = nb.next;
+        neighbours(g, j, nn);
+        uint32_t tau = fd_div((uint32_t)i, g.f_V);
+        double s = ((int)tau == g.ntau - 1) ? 1.0 : -1.0;
+        double coef = s * A * cos(sigma[i]);
+        double F = 0.0;
+        for (int a = 0; a < n_rhs; ++a) {
+            const double *xa = x + (size_t)a * g.N;
+            double y = stencil_M<double>(g, h, L64, xa, j, nn);
+            F -= y * coef * xa[i];
+        }
+        if (F_out) F_out[i] = F;
+        if (pi) pi[i] = fma(-eps, F, pi[i]);
+    }
+}
+
+constexpr int kEnergyMaxBlocks = 1024;
+
+__global__ void k_energy(int n, const double *__restrict__ pi, const double *__restrict__ chi,
+                         const double *__restrict__ x, int n_rhs, double *__restrict__ part)
+{
+    __shared__ double red[kBlock / 32];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double e = 0.0;
+        if (pi) e = pi[i] * pi[i];
+        for (int a = 0; a < n_rhs; ++a) e = fma(chi[(size_t)a * n + i], x[(size_t)a * n + i], e);
+        acc += 0.5 * e;
+    }
+    double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void k_sum_partials(const double *__restrict__ part, int nb, double *__restrict__ out)
+{
+    double v = 0.0;
+    for (int j = threadIdx.x; j < nb; j += 32) v += part[j];
+    v = warp_sum(v);
+    if (threadIdx.x == 0) *out = v;
+}
+
+__global__ void k_metropolis(HmcScalars *sc, uint64_t seed, uint64_t traj, uint64_t chain)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double dH = sc->H1 - sc->H0;
+    U64x4 w = philox4x64_10(0, 3, traj, chain, seed, 0);
+    double u = u53(w.v[0]);
+    sc->dH = dH;
+    sc->u = u;
+    sc->accepted = (u < exp(-dH)) ? 1 : 0;
+}
+
+__global__ void k_restore(Geo g, double A, const HmcScalars *__restrict__ sc, double *__restrict__ sigma,
+                          const double *__restrict__ sigma0, double *__restrict__ L64,
+                          float *__restrict__ L32)
+{
+    if (sc->accepted) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += gridDim.x * blockDim.x) {
+        double s = sigma0[i];
+        sigma[i] = s;
+        double l = link_value(g, A, s, i);
+        L64[i] = l;
+        L32[i] = (float)l;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_links(const Geo &g, double A, const double *sigma, double *L64, float *L32,
+                         cudaStream_t st)
+{
+    k_links<<<grid_for(g.N), kBlock, 0, st>>>(g, A, sigma, L64, L32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sigma_step(const Geo &g, double A, double dt, double *sigma, const double *pi,
+                              double *L64, float *L32, cudaStream_t st)
+{
+    k_sigma_step<<<grid_for(g.N), kBlock, 0, st>>>(g, A, dt, sigma, pi, L64, L32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_f64(const Geo &g, int op, double h, const double *L, const double *x,
+                             double *y, cudaStream_t st)
+{
+    k_apply<double><<<grid_for(g.N), kBlock, 0, st>>>(g, op, h, L, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_f32(const Geo &g, int op, float h, const float *L, const float *x, float *y,
+                             cudaStream_t st)
+{
+    k_apply<float><<<grid_for(g.N), kBlock, 0, st>>>(g, op, h, L, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gaussian(double *out, int n, uint64_t seed, int tag, int a, uint64_t traj,
+                            uint64_t chain, cudaStream_t st)
+{
+    uint64_t ctr1 = (uint64_t)tag | ((uint64_t)a << 8);
+    k_gaussian<<<grid_for((n + 3) / 4), kBlock, 0, st>>>(out, n, seed, ctr1, traj, chain);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_field(double *sigma, int n, uint64_t seed, uint64_t chain, cudaStream_t st)
+{
+    k_init_field<<<grid_for((n + 3) / 4), kBlock, 0, st>>>(sigma, n, seed, chain);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force(const Geo &g, double h, double A, const double *sigma, const double *L64,
+                         const double *x, int n_rhs, double *pi, double eps, double *F_out,
+                         cudaStream_t st)
+{
+    k_force<<<grid_for(g.N), kBlock, 0, st>>>(g, h, A, sigma, L64, x, n_rhs, pi, eps, F_out);
+    return cudaGetLastError();
+}
+
+int energy_blocks(int n)
+{
+    int b = (n + kBlock - 1) / kBlock;
+    if (b > kEnergyMaxBlocks) b = kEnergyMaxBlocks;
+    if (b < 1) b = 1;
+    return b;
+}
+
+cudaError_t launch_energy(int n, const double *pi, const double *chi, const double *x, int n_rhs,
+                          double *part, double *out, cudaStream_t st)
+{
+    int nb = energy_blocks(n);
+    k_energy<<<nb, kBlock, 0, st>>>(n, pi, chi, x, n_rhs, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sum_partials<<<1, 32, 0, st>>>(part, nb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_metropolis(HmcScalars *sc, uint64_t seed, uint64_t traj, uint64_t chain,
+                              cudaStream_t st)
+{
+    k_metropolis<<<1, 32, 0, st>>>(sc, seed, traj, chain);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restore(const Geo &g, double A, const HmcScalars *sc, double *sigma,
+                           const double *sigma0, double *L64, float *L32, cudaStream_t st)
+{
+    k_restore<<<grid_for(g.N), kBlock, 0, st>>>(g, A, sc, sigma, sigma0, L64, L32);
+    return cudaGetLastError();
+}
+
+}  // namespace hh

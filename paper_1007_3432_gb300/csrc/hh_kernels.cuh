@@ -1,0 +1,61 @@
+// Launchers of the non-persistent kernels of the library (links, stencil
+// applies, random draws, HMC updates).  All launch on the given stream and
+// return the launch's cudaError_t.
+#pragma once
+
+#include "hh_device.cuh"
+
+namespace hh {
+
+// Device scalars of one HMC context (one slot each, written by kernels).
+struct HmcScalars {
+    double H0, H1, dH, u;
+    double S_pf;            // last action evaluated
+    int accepted;
+    int pad;
+    double part_scratch;    // unused padding to keep doubles aligned
+};
+
+// L64(i) = s(tau) (1 + A sin sigma_i), s = -1 except +1 at tau = N_tau - 1;
+// L32 = (float)L64.
+cudaError_t launch_links(const Geo &g, double A, const double *sigma, double *L64, float *L32,
+                         cudaStream_t st);
+
+// sigma += dt * pi, then the links.
+cudaError_t launch_sigma_step(const Geo &g, double A, double dt, double *sigma, const double *pi,
+                              double *L64, float *L32, cudaStream_t st);
+
+// y = M x or y = M^T x (op 0 / 1), FP64 or FP32.
+cudaError_t launch_apply_f64(const Geo &g, int op, double h, const double *L, const double *x,
+                             double *y, cudaStream_t st);
+cudaError_t launch_apply_f32(const Geo &g, int op, float h, const float *L, const float *x, float *y,
+                             cudaStream_t st);
+
+// out[i] = N(0,1) Philox/Box-Muller draw for element i (tag, a, traj, chain).
+cudaError_t launch_gaussian(double *out, int n, uint64_t seed, int tag, int a, uint64_t traj,
+                            uint64_t chain, cudaStream_t st);
+// sigma[i] = -pi + 2 pi u_i (tag 0).
+cudaError_t launch_init_field(double *sigma, int n, uint64_t seed, uint64_t chain, cudaStream_t st);
+
+// Force F = dS/dsigma from solutions x_a (n_rhs of them, at x + a*N); if pi is
+// non-null, pi -= eps * F; if F_out is non-null, F is stored.
+cudaError_t launch_force(const Geo &g, double h, double A, const double *sigma, const double *L64,
+                         const double *x, int n_rhs, double *pi, double eps, double *F_out,
+                         cudaStream_t st);
+
+// Energy partials: block b writes part[b] = sum over its sites of
+// 1/2 pi^2 (if pi) + 1/2 sum_a chi_a x_a.  'nblocks' is returned by
+// energy_blocks(N).  Then energy_finish sums part[0..nblocks) in order into
+// *out (device double).
+int energy_blocks(int n);
+cudaError_t launch_energy(int n, const double *pi, const double *chi, const double *x, int n_rhs,
+                          double *part, double *out, cudaStream_t st);
+
+// dH = H1 - H0, u = Philox uniform (tag 3, index 0), accepted = u < exp(-dH).
+cudaError_t launch_metropolis(HmcScalars *sc, uint64_t seed, uint64_t traj, uint64_t chain,
+                              cudaStream_t st);
+// If !sc->accepted: sigma = sigma0 and the links are recomputed.
+cudaError_t launch_restore(const Geo &g, double A, const HmcScalars *sc, double *sigma,
+                           const double *sigma0, double *L64, float *L32, cudaStream_t st);
+
+}  // namespace hh

@@ -1,0 +1,239 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+the same seeded inputs.
+
+Tolerances:
+  * FP64 stencil applies: |y_gpu - y_ref|_i <= 1e-12 * (|M| |x|)_i, where
+    (|M| |x|)_i is the sum of the magnitudes of the terms of row i (obtained
+    from the oracle with h -> -h, L -> |L|, x -> |x|).  Rounding differences
+    of FP64 sums of a handful of terms are ~1e-16 of that bound's scale.
+  * FP32 applies: the same form with 2e-6 (a few FP32 ulps of each term).
+  * CG: true relative residual ||b - Q x|| / ||b|| <= 1e-10, recomputed by the
+    oracle in FP64 from the GPU's x.
+  * Trajectories: identical accept/reject decisions (except a decision within
+    the estimated dH error of the threshold), dH within 1e-6 absolute.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import workloads  # noqa: E402
+
+H = workloads.T_HOP * workloads.DTAU
+A = workloads.A_HS
+
+
+@pytest.fixture(scope="module")
+def hh():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1007_3432_gb300 as pkg
+    from paper_1007_3432_gb300 import build
+    build.build()
+    pkg.load()
+    return pkg
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def magnitude(lat, which, L, x):
+    """Row-wise sum of |terms| of op(x)."""
+    La, xa = np.abs(L), np.abs(x)
+    if which == "M":
+        return oracle.apply_M(lat, -H, La, xa)
+    if which == "MT":
+        return oracle.apply_MT(lat, -H, La, xa)
+    return oracle.apply_MT(lat, -H, La, oracle.apply_M(lat, -H, La, xa))
+
+
+SHAPES = [(1, 32, 64), (1, 37, 13), (1, 2, 6), (1, 1024, 8), (3, 5, 7), (3, 8, 12), (3, 2, 4),
+          (3, 3, 2), (3, 10, 9)]
+
+
+@pytest.mark.parametrize("d,nx,ntau", SHAPES)
+@pytest.mark.parametrize("op", ["M", "MT", "MTM"])
+def test_apply_fp64_per_element(hh, d, nx, ntau, op):
+    lat = oracle.lattice(d, nx, ntau)
+    n = oracle.nsites(lat)
+    sigma = workloads.sigma_field(n, seed=100 + nx + ntau)
+    x = workloads.source(n, seed=200 + nx)
+    L = oracle.links(lat, A, sigma)
+    ref = {"M": oracle.apply_M, "MT": oracle.apply_MT, "MTM": oracle.apply_MTM}[op](lat, H, L, x)
+    bound = 1e-12 * magnitude(lat, op, L, x)
+    code = {"M": hh.HH_OP_M, "MT": hh.HH_OP_MT, "MTM": hh.HH_OP_MTM}[op]
+    with hh.Context(d, nx, ntau) as ctx:
+        ctx.set_field(dev(sigma))
+        y = torch.empty(n, dtype=torch.float64, device="cuda")
+        ctx.apply(code, dev(x), y)
+        got = y.cpu().numpy()
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
+
+
+@pytest.mark.parametrize("d,nx,ntau", [(1, 32, 64), (3, 8, 12), (3, 5, 7)])
+@pytest.mark.parametrize("op", ["M", "MT", "MTM"])
+def test_apply_fp32_per_element(hh, d, nx, ntau, op):
+    lat = oracle.lattice(d, nx, ntau)
+    n = oracle.nsites(lat)
+    sigma = workloads.sigma_field(n, seed=300 + nx)
+    x = workloads.source(n, seed=400 + nx).astype(np.float32)
+    L = oracle.links(lat, A, sigma)
+    x64 = x.astype(np.float64)
+    ref = {"M": oracle.apply_M, "MT": oracle.apply_MT, "MTM": oracle.apply_MTM}[op](lat, H, L, x64)
+    bound = 2e-6 * magnitude(lat, op, L, x64)
+    code = {"M": hh.HH_OP_M, "MT": hh.HH_OP_MT, "MTM": hh.HH_OP_MTM}[op]
+    with hh.Context(d, nx, ntau) as ctx:
+        ctx.set_field(dev(sigma))
+        y = torch.empty(n, dtype=torch.float32, device="cuda")
+        ctx.apply(code, dev(x), y)
+        got = y.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
+
+
+def test_field_roundtrip_and_random_init(hh):
+    d, nx, ntau = 3, 6, 5
+    n = nx ** 3 * ntau
+    with hh.Context(d, nx, ntau, chain_id=3) as ctx:
+        s = workloads.sigma_field(n, seed=5)
+        ctx.set_field(s)                      # host pointer path
+        back = np.empty(n)
+        ctx.get_field(back)
+        assert np.array_equal(back, s)
+        ctx.init_field_random(77)
+        got = torch.empty(n, dtype=torch.float64, device="cuda")
+        ctx.get_field(got)
+        assert np.array_equal(got.cpu().numpy(), oracle.init_field(77, 3, n))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("d,nx,ntau,n_rhs", [(1, 32, 64, 2), (1, 19, 11, 1), (3, 6, 8, 2), (3, 4, 16, 3)])
+def test_solve_true_residual_and_solution(hh, precision, d, nx, ntau, n_rhs):
+    lat = oracle.lattice(d, nx, ntau)
+    n = oracle.nsites(lat)
+    sigma = workloads.sigma_field(n, seed=500 + nx)
+    L = oracle.links(lat, A, sigma)
+    b = np.stack([workloads.source(n, seed=600, rhs=a) for a in range(n_rhs)])
+    with hh.Context(d, nx, ntau, precision=precision) as ctx:
+        ctx.set_field(dev(sigma))
+        x = torch.zeros(n_rhs, n, dtype=torch.float64, device="cuda")
+        rc, info = ctx.solve(dev(b), x, n_rhs)
+        xg = x.cpu().numpy()
+    assert rc == 0 and info["converged"] == 1
+    assert info["true_relres"] <= 1e-10
+    for a in range(n_rhs):
+        res = b[a] - oracle.apply_MTM(lat, H, L, xg[a])
+        assert np.linalg.norm(res) <= 1.0001e-10 * np.linalg.norm(b[a])
+        x_ref, st, it, rr = oracle.cg(lat, H, L, b[a])
+        assert st == 0
+        # Both solutions meet 1e-10; they differ by at most kappa * 2e-10.
+        assert np.linalg.norm(xg[a] - x_ref) <= 1e-4 * np.linalg.norm(x_ref)
+
+
+def test_solve_zero_rhs_and_iteration_cap(hh):
+    d, nx, ntau = 1, 16, 32
+    n = nx * ntau
+    with hh.Context(d, nx, ntau, cg_maxit=5) as ctx:
+        ctx.set_field(dev(workloads.sigma_field(n, seed=9)))
+        x = torch.full((1, n), 7.0, dtype=torch.float64, device="cuda")
+        rc, info = ctx.solve(torch.zeros(1, n, dtype=torch.float64, device="cuda"), x, 1)
+        assert rc == 0 and info["converged"] == 1 and not torch.any(x)
+        b = dev(workloads.source(n, seed=1))
+        rc, info = ctx.solve(b, x, 1, allow=(hh.binding.HH_ENOCONV,))
+        assert rc == hh.binding.HH_ENOCONV and info["converged"] == 0
+        assert info["iterations"] == 5 and info["true_relres"] > 1e-10
+
+
+@pytest.mark.parametrize("d,nx,ntau", [(1, 16, 24), (3, 4, 6)])
+def test_force_matches_oracle(hh, d, nx, ntau):
+    lat = oracle.lattice(d, nx, ntau)
+    n = oracle.nsites(lat)
+    sigma = workloads.sigma_field(n, seed=700)
+    chi = np.stack([workloads.source(n, seed=800, rhs=a) for a in range(2)])
+    prm = oracle.params(cg_tol=1e-12)
+    F_ref, *_ = oracle.force(lat, prm, sigma, chi)
+    with hh.Context(d, nx, ntau, cg_tol=1e-12) as ctx:
+        ctx.set_field(dev(sigma))
+        F = torch.empty(n, dtype=torch.float64, device="cuda")
+        ctx.force(dev(chi), 2, F)
+        got = F.cpu().numpy()
+    assert np.max(np.abs(got - F_ref)) <= 1e-7 * np.max(np.abs(F_ref))
+
+
+def test_action_heatbath_identity(hh):
+    d, nx, ntau = 1, 16, 24
+    n = nx * ntau
+    lat = oracle.lattice(d, nx, ntau)
+    sigma = workloads.sigma_field(n, seed=900)
+    prm = oracle.params(seed=31, chain=0)
+    chi = oracle.heatbath(lat, prm, sigma, traj=2)
+    S_ref, *_ = oracle.action(lat, prm, sigma, chi)
+    with hh.Context(d, nx, ntau) as ctx:
+        ctx.set_field(dev(sigma))
+        S, info = ctx.action(dev(chi), 2)
+    assert abs(S - S_ref) <= 1e-9 * S_ref
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_trajectories_match_oracle(hh, precision):
+    """Several trajectories of the d=1, 32 x 64 lattice from the same seed:
+    identical accept/reject sequences and matching energies."""
+    wl = workloads.C0
+    lat = oracle.lattice(wl.d, wl.nx, wl.ntau)
+    n = wl.nsites
+    sigma = workloads.sigma_field(n, seed=wl.seed)
+    prm = oracle.params(seed=wl.seed, n_pf=2)
+    n_md, dt = 5, 0.04
+    s_ref = sigma.copy()
+    with hh.Context(wl.d, wl.nx, wl.ntau, seed=wl.seed, n_pf=2, precision=precision) as ctx:
+        ctx.set_field(dev(sigma))
+        for traj in range(3):
+            info = ctx.trajectory(n_md, dt, traj)
+            s_ref, oinfo = oracle.trajectory(lat, prm, s_ref, n_md, dt, traj)
+            assert info["n_solves"] == 2 * (n_md + 1)
+            assert info["max_true_relres"] <= 1e-10
+            assert info["u"] == oinfo["u"]
+            assert abs(info["H0"] - oinfo["H0"]) <= 1e-8 * abs(oinfo["H0"])
+            assert abs(info["dH"] - oinfo["dH"]) <= 1e-6, (info, oinfo)
+            margin = abs(oinfo["dH"] + np.log(oinfo["u"]))
+            if margin > 1e-5:
+                assert info["accepted"] == oinfo["accepted"]
+            if info["accepted"] != oinfo["accepted"]:
+                break
+            got = torch.empty(n, dtype=torch.float64, device="cuda")
+            ctx.get_field(got)
+            assert np.max(np.abs(got.cpu().numpy() - s_ref)) <= 1e-6
+
+
+def test_leapfrog_reversible_on_gpu(hh):
+    d, nx, ntau = 1, 16, 16
+    n = nx * ntau
+    lat = oracle.lattice(d, nx, ntau)
+    sigma = workloads.sigma_field(n, seed=41)
+    pi0 = workloads.unit_normal(n, seed=41, stream=1)
+    chi = np.stack([workloads.source(n, seed=42, rhs=a) for a in range(2)])
+    with hh.Context(d, nx, ntau, cg_tol=1e-12) as ctx:
+        ctx.set_field(dev(sigma))
+        pi = dev(pi0)
+        ctx.leapfrog(pi, dev(chi), 2, 8, 0.05)
+        pi.neg_()
+        ctx.leapfrog(pi, dev(chi), 2, 8, 0.05)
+        back = torch.empty(n, dtype=torch.float64, device="cuda")
+        ctx.get_field(back)
+    assert np.max(np.abs(back.cpu().numpy() - sigma)) < 1e-8
+    assert np.max(np.abs(pi.cpu().numpy() + pi0)) < 1e-8
+
+
+def test_invalid_arguments(hh):
+    with hh.Context(1, 8, 8) as ctx:
+        x = torch.zeros(64, dtype=torch.float64, device="cuda")
+        with pytest.raises(hh.HHError):
+            ctx.apply(7, x, torch.empty_like(x))
+        with pytest.raises(hh.HHError):
+            ctx.apply(hh.HH_OP_M, x, x)
+        with pytest.raises(hh.HHError):
+            ctx.solve(x, torch.empty_like(x), 0)
+        with pytest.raises(hh.HHError):
+            ctx.trajectory(0, 0.1, 0)

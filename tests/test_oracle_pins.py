@@ -375,11 +375,16 @@ def test_trajectory_draws_and_metropolis(orc):
     assert info["n_solves"] == 2 * (6 + 3)
     if not info["accepted"]:
         assert np.array_equal(s1, sigma)
-    # A huge step must be rejected and leave sigma untouched.
-    s2, info2 = orc.trajectory(lat, prm, sigma, 2, 2.0, 10)
-    if not info2["accepted"]:
-        assert np.array_equal(s2, sigma)
-        assert info2["u"] >= np.exp(-info2["dH"])
+    # Several trajectories, one with a step so large that dH >> 1: the decision
+    # must follow u < exp(-dH) in every case, and a rejection restores sigma.
+    seen_reject = False
+    for traj, (n_md, dt) in enumerate([(2, 2.0), (4, 0.25), (4, 0.5), (3, 1.0)], start=10):
+        s2, info2 = orc.trajectory(lat, prm, sigma, n_md, dt, traj)
+        assert info2["accepted"] == (info2["u"] < np.exp(-info2["dH"]))
+        if not info2["accepted"]:
+            seen_reject = True
+            assert np.array_equal(s2, sigma)
+    assert seen_reject
 
 
 @pytest.mark.slow
