@@ -199,6 +199,37 @@ int hh_counters_reset(hh_ctx *ctx, int profile_engine);
 /* Read the counters; synchronises the context stream. */
 int hh_counters_get(hh_ctx *ctx, hh_counters *out);
 
+/* ---- Allocation-free solve ------------------------------------------------
+ * The paper has no counterpart of this entry point; it exists for callers
+ * that cannot allocate memory when they need a solve: code running while its
+ * stream is captured into a CUDA graph (cudaMalloc is not allowed there),
+ * plug-ins inside applications that own the device allocator, and loops that
+ * must not take allocator locks.  Everything the FP64 CG needs beyond the
+ * caller's sigma, b and x lives in one file-scope device array of
+ * HH_NOALLOC_SCRATCH_MB (about 9 MiB), which every device that loads the
+ * library keeps until the process exits.
+ *
+ * hh_solve_noalloc solves Q x = b (Sec. 4.1; Q = M^T M of Eq. (10) built from
+ * sigma with the parameters t, dtau, A of p) by FP64 CG with x0 = 0, one
+ * right-hand side, the same algorithm and stopping test as hh_solve.
+ *   lat, p:  lattice and parameters; p->precision must be HH_FP64, and
+ *            N = Nx^d * Ntau must not exceed HH_NOALLOC_MAX_SITES, else the
+ *            call returns HH_ESIZE without touching the device.
+ *   sigma, b, x: device pointers to N doubles owned by the caller.
+ *   cuda_stream: the cudaStream_t to run on (NULL: legacy default stream).
+ *   info: if non-NULL the call synchronises the stream and fills it.
+ * The first call on a device looks up the array's device address and the
+ * kernel's occupancy; make that first call before any stream capture.
+ * The call allocates no device or host memory.  All calls share the array and
+ * overwrite it (the call clears what must start at zero); calls whose GPU work
+ * overlaps in time race on it and must be serialised by the caller.
+ * Returns the same codes as hh_solve, plus HH_ESIZE. */
+#define HH_ESIZE (-8) /* problem larger than the static scratch of hh_solve_noalloc */
+#define HH_NOALLOC_MAX_SITES 262144
+#define HH_NOALLOC_SCRATCH_MB 9
+int hh_solve_noalloc(const hh_lattice *lat, const hh_params *p, const double *sigma,
+                     const double *b, double *x, void *cuda_stream, hh_solve_info *info);
+
 /* Text for an error code. */
 const char *hh_strerror(int code);
 

@@ -14,7 +14,8 @@ LIB_PATH = os.path.join(HERE, "lib", "libhubhmc.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "hubhmc.h")
 
 HH_OK, HH_EINVAL, HH_ENOMEM, HH_ECUDA = 0, -1, -2, -3
-HH_ENOCONV, HH_ENUMERIC, HH_ETIMEOUT, HH_EBUSY = -4, -5, -6, -7
+HH_ENOCONV, HH_ENUMERIC, HH_ETIMEOUT, HH_EBUSY, HH_ESIZE = -4, -5, -6, -7, -8
+HH_NOALLOC_MAX_SITES = 262144
 HH_FP64, HH_MIXED = 0, 1
 HH_OP_M, HH_OP_MT, HH_OP_MTM = 0, 1, 2
 HH_DTYPE_F64, HH_DTYPE_F32 = 0, 1
@@ -93,6 +94,8 @@ def load(path: str = LIB_PATH):
         "hh_leapfrog": (i, [vp, vp, vp, i, i, d, ctypes.POINTER(hh_solve_info)]),
         "hh_counters_reset": (i, [vp, i]),
         "hh_counters_get": (i, [vp, ctypes.POINTER(hh_counters)]),
+        "hh_solve_noalloc": (i, [ctypes.POINTER(hh_lattice), ctypes.POINTER(hh_params), vp, vp, vp, vp,
+                                 ctypes.POINTER(hh_solve_info)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -240,3 +243,18 @@ class Context:
         c = hh_counters()
         check(self._lib.hh_counters_get(self._h, ctypes.byref(c)), "hh_counters_get")
         return c.as_dict()
+
+
+def solve_noalloc(d, nx, ntau, sigma, b, x, t=1.0, dtau=0.05, A=0.5, cg_tol=1e-10, cg_maxit=1000000,
+                  stream=None, info=True):
+    """hh_solve_noalloc: FP64 CG for Q x = b with no allocation by the library.
+    sigma, b, x: device tensors of N doubles.  Returns (rc, info dict)."""
+    L = load()
+    lat = hh_lattice(d, nx, ntau)
+    p = hh_params()
+    L.hh_default_params(ctypes.byref(p))
+    p.t, p.dtau, p.A, p.cg_tol, p.cg_maxit = t, dtau, A, cg_tol, cg_maxit
+    inf = hh_solve_info()
+    rc = L.hh_solve_noalloc(ctypes.byref(lat), ctypes.byref(p), _ptr(sigma), _ptr(b), _ptr(x),
+                            _stream_handle(stream), ctypes.byref(inf) if info else None)
+    return rc, (inf.as_dict() if info else None)
