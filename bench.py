@@ -13,8 +13,15 @@ Q = M^T M once per right-hand side), with sigma resident on the device when a
 step's timed region starts.  e2e: the same count over wall time of the public
 calls hh_set_field(host) -> hh_trajectory -> hh_get_field(host) per step.
 
+Two further modes measure parts of the path (they print the same JSON line):
+  --mode solve : a step is one CG solve of Q x = b for two right-hand sides
+                 (value in solves/s), to compare FP64 with mixed precision;
+  --mode apply : a step is one M^T M apply with L2 flushed before it (value in
+                 applies/s), the HBM roofline of the stencil.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                        [--workload c0|c1|c2] [--precision fp64|mixed]
+                       [--mode trajectory|solve|apply] [--cg-maxit M]
 """
 import argparse
 import json
@@ -219,6 +226,104 @@ def config_of(args, wl):
             "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas%d" % args.gpus}
 
 
+def run_part(args, wl, world, rank, local, dev, stream):
+    """--mode solve / --mode apply: one CG solve (2 right-hand sides) or one
+    M^T M apply per step, each bracketed by CUDA events on the context stream,
+    L2 flushed before every step."""
+    import torch
+    from paper_1007_3432_gb300 import HH_OP_MTM, Context
+    from paper_1007_3432_gb300.binding import HH_ENOCONV
+    n = wl.nsites
+    ctx = Context(wl.d, wl.nx, wl.ntau, seed=wl.seed, chain_id=rank, precision=args.precision,
+                  cg_maxit=args.cg_maxit, stream=stream)
+    ctx.set_field(torch.from_numpy(workloads.sigma_field(n, seed=wl.seed, chain=rank)).to(dev))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    if args.mode == "solve":
+        b_h = np.stack([workloads.source(n, seed=wl.seed, chain=rank, rhs=a) for a in range(2)])
+        b = torch.from_numpy(b_h).to(dev)
+        x = torch.zeros_like(b)
+        x_h = torch.empty(b.shape, dtype=torch.float64).pin_memory()
+        b_pin = torch.from_numpy(b_h).pin_memory()
+    else:
+        dt = torch.float32 if args.precision == "mixed" else torch.float64
+        xs = torch.from_numpy(workloads.source(n, seed=wl.seed, chain=rank)).to(dev).to(dt)
+        ys = torch.empty_like(xs)
+
+    def one(timed):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0 = time.perf_counter()
+        if args.mode == "solve":
+            b.copy_(b_pin, non_blocking=True)      # host -> device input
+            e0.record(stream)
+            ctx.solve(b, x, 2, info=False)
+            e1.record(stream)
+            x_h.copy_(x, non_blocking=True)        # device -> host result
+        else:
+            e0.record(stream)
+            ctx.apply(HH_OP_MTM, xs, ys)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1), (time.perf_counter() - w0) * 1000.0
+
+    for _ in range(args.warmup):
+        one(False)
+    ctx.counters_reset(profile_engine=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    dev_ms, wall_ms = [], []
+    for _ in range(args.steps):
+        a, w = one(True)
+        dev_ms.append(a)
+        wall_ms.append(w)
+    clk = clocks.stop()
+    cnt = ctx.counters()
+    peaks, src = measured_peaks()
+    t_dev = max_over_ranks(world, sum(dev_ms) / 1000.0)
+    t_wall = max_over_ranks(world, sum(wall_ms) / 1000.0)
+    if args.mode == "solve":
+        units = sum_over_ranks(world, float(cnt["solves"]))
+        unit = "CG solves/s"
+        eng_s = cnt["engine_ms"] / 1000.0
+        if args.precision == "fp64":
+            flops = n * (cnt["cg_steps"] * flops_per_site(wl.d, "cg", "fp64") + cnt["ru_steps"] * flops_per_site(wl.d, "ru", "fp64"))
+            ach = flops / eng_s / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak_tflops(), "unit": "TFLOP/s",
+                    "frac": ach / fp64_peak_tflops(), "traffic": None, "kernel": "engine_kernel (FP64 CG)"}
+        else:
+            byts = n * (cnt["cg_steps"] * bytes_per_site("cg", "mixed") + cnt["ru_steps"] * bytes_per_site("ru", "mixed"))
+            ach = byts / eng_s / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "engine_kernel (FP32-inner CG)"}
+        extra = {"cg_steps_per_solve": cnt["cg_steps"] / max(1, cnt["solves"]),
+                 "ru_steps": cnt["ru_steps"], "fp64_steps": cnt["fp64_steps"]}
+        e2e_bytes = (n * 16, n * 16)
+    else:
+        units = float(world * args.steps)
+        unit = "MTM applies/s"
+        bps = 12 if args.precision == "mixed" else 24
+        ach = units / world * n * bps / t_dev / 1e9 * world
+        roof = {"bound": "hbm", "achieved": ach / world, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / world / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "M^T M apply (%s)" % ("FP32" if args.precision == "mixed" else "FP64"),
+                "algorithmic_bytes_per_site": bps}
+        extra = {"median_apply_us": 1000.0 * float(np.median(dev_ms))}
+        e2e_bytes = (0, 0)
+    line = {"metric": METRIC, "value": units / t_dev, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t_dev / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else ("f32" if args.mode == "apply" else "f32+f64"),
+            "data": "synthetic", "config": dict(config_of(args, wl), mode=args.mode),
+            "e2e": {"value": units / t_wall, "unit": unit, "h2d_bytes_per_step": e2e_bytes[0],
+                    "d2h_bytes_per_step": e2e_bytes[1]},
+            "gpu_launches": int(cnt["kernel_launches"]), "clocks": clk, "roofline": roof}
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -230,6 +335,8 @@ def main():
     ap.add_argument("--n-md", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--mode", default="trajectory", choices=["trajectory", "solve", "apply"])
+    ap.add_argument("--cg-maxit", type=int, default=1000000)
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.n_md is None:
@@ -249,10 +356,12 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    if args.mode != "trajectory":
+        return run_part(args, wl, world, rank, local, dev, stream)
     n = wl.nsites
     sigma_h = workloads.sigma_field(n, seed=wl.seed, chain=rank)
     ctx = Context(wl.d, wl.nx, wl.ntau, seed=wl.seed, n_pf=2, chain_id=rank, precision=args.precision,
-                  stream=stream)
+                  cg_maxit=args.cg_maxit, stream=stream)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     dt = 1.0 / args.n_md
 

@@ -21,7 +21,9 @@
  *     elements; n_rhs vectors are stored back to back (vector a at a*N).
  *   - Pointers documented as device pointers must point to CUDA device memory
  *     of the current device; the caller owns them and keeps them alive until
- *     the call's work on the context stream has finished.
+ *     the call's work on the context stream has finished.  Vector arguments
+ *     (b, x, chi) must be 16-byte aligned (they are accessed with 16-byte
+ *     loads and stores); a misaligned one is refused with HH_EINVAL.
  *   - All GPU work of a context is ordered on the stream given at creation.
  *     Calls that return results in host structures (an info argument, host
  *     output pointers) synchronise that stream before they return; the other
@@ -189,6 +191,9 @@ typedef struct {
     long long ru_steps;        /* FP64 true-residual recomputations (checks and
                                   reliable updates), summed over right-hand sides */
     long long solves;          /* right-hand sides solved */
+    long long fp64_steps;      /* CG steps run in FP64 (all of them in HH_FP64;
+                                  in HH_MIXED, the steps after a stalled system
+                                  switched to FP64) */
     long long sites;           /* N of the context's lattice */
 } hh_counters;
 

@@ -59,7 +59,7 @@ class hh_counters(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_longlong), ("engine_launches", ctypes.c_longlong),
                 ("engine_ms", ctypes.c_double), ("cg_steps", ctypes.c_longlong),
                 ("ru_steps", ctypes.c_longlong), ("solves", ctypes.c_longlong),
-                ("sites", ctypes.c_longlong)]
+                ("fp64_steps", ctypes.c_longlong), ("sites", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1,6 +1,7 @@
 // C ABI of the library: contexts, solves and the HMC trajectory driver.
 // Every step of the path runs in the kernels of hh_kernels.cu and
 // hh_engine.cu; this file only allocates, validates, plans and enqueues.
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -55,7 +56,7 @@ __device__ int severity(int st)
 
 // Running totals across solves (not cleared by k_zero_stats).
 struct EngTotals {
-    long long cg_steps, ru_steps, solves;
+    long long cg_steps, ru_steps, solves, fp64_steps;
 };
 
 __global__ void k_engine_fold(EngState *s0, EngState *s1, int nsys, const BarrierCtl *ctl,
@@ -74,6 +75,7 @@ __global__ void k_engine_fold(EngState *s0, EngState *s1, int nsys, const Barrie
         tot->cg_steps += S.cg_steps;
         tot->ru_steps += S.n_ru;
         tot->solves += 1;
+        tot->fp64_steps += S.fp64_steps;
         if (S.cg_steps > stats->max_iters) stats->max_iters = S.cg_steps;
         stats->n_solves += 1;
         stats->n_ru += S.n_ru;
@@ -169,29 +171,19 @@ void free_ctx(hh_ctx *c)
     }
 }
 
-int engine_tiles_per_system(const hh_ctx *c, int nsys)
-{
-    // Enough tiles to give every block of the grid work, at least 256 sites each.
-    int by_size = (c->N + 255) / 256;
-    int want = (c->max_grid + nsys - 1) / nsys;
-    if (want < 1) want = 1;
-    return by_size < want ? by_size : want;
-}
-
 // Build (or reuse) the engine plan for n_rhs systems b_a -> x_a.
 int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
 {
     Plan &P = c->plan;
     if (P.nsys == n_rhs && P.b == b && P.x == x && P.precision == c->prm.precision) return HH_OK;
-    int tps = engine_tiles_per_system(c, n_rhs);
-    int ntiles = tps * n_rhs;
+    Tiling tl = engine_tiling(c->N, n_rhs, c->max_grid);
+    int ntiles = tl.tiles * n_rhs;
     if (ntiles > c->max_tiles) return HH_EINVAL;
     int grid = ntiles < c->max_grid ? ntiles : c->max_grid;
     std::vector<EngSystem> sys(n_rhs);
     std::vector<EngTile> tiles;
     tiles.reserve(ntiles);
-    int chunk = (c->N + tps - 1) / tps;
-    chunk = (chunk + 31) / 32 * 32;
+    const int chunk = tl.chunk;
     for (int a = 0; a < n_rhs; ++a) {
         EngSystem &Y = sys[a];
         memset(&Y, 0, sizeof(Y));
@@ -223,6 +215,8 @@ int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
         Y.tol2 = c->prm.cg_tol * c->prm.cg_tol;
         Y.delta2 = c->prm.reliable_delta * c->prm.reliable_delta;
         Y.maxit = c->prm.cg_maxit;
+        Y.w = engine_group_width(c->lat.nx);
+        Y.stall_window = ENGINE_STALL_WINDOW;
     }
     ntiles = (int)tiles.size();
     grid = ntiles < c->max_grid ? ntiles : c->max_grid;
@@ -305,6 +299,12 @@ int ensure_rhs(hh_ctx *c, int n_rhs)
     return n_rhs >= 1 && n_rhs <= c->cap_rhs ? HH_OK : HH_EINVAL;
 }
 
+// Vector arguments are read and written with 16-byte accesses.
+bool aligned16(const void *p)
+{
+    return ((uintptr_t)p & 15u) == 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -362,18 +362,11 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
     c->N = (int)N;
     c->cap_rhs = p->n_pf > 4 ? p->n_pf : 4;
     c->timeout_ns = 5LL * 1000 * 1000 * 1000;
-    const char *bps = getenv("HH_ENGINE_BLOCKS_PER_SM");
-    int max_grid = engine_max_grid(ENGINE_BLOCK);
+    int max_grid = engine_default_grid();
     if (max_grid <= 0) {
         delete c;
         return HH_ECUDA;
     }
-    int dev = 0, nsm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int per = bps ? atoi(bps) : 2;
-    if (per < 1) per = 1;
-    if (per * nsm < max_grid) max_grid = per * nsm;
     c->max_grid = max_grid;
     c->max_tiles = c->cap_rhs * (max_grid + 1) + 64;
 
@@ -513,7 +506,7 @@ int hh_apply(hh_ctx *c, int op, const void *x, void *y, int dtype)
 
 int hh_solve(hh_ctx *c, const double *b, double *x, int n_rhs, hh_solve_info *info)
 {
-    if (!c || !b || !x) return HH_EINVAL;
+    if (!c || !b || !x || !aligned16(b) || !aligned16(x)) return HH_EINVAL;
     int rc = ensure_rhs(c, n_rhs);
     if (rc) return rc;
     rc = make_plan(c, b, x, n_rhs);
@@ -533,7 +526,7 @@ int hh_solve(hh_ctx *c, const double *b, double *x, int n_rhs, hh_solve_info *in
 
 int hh_force(hh_ctx *c, const double *chi, int n_rhs, double *F, hh_solve_info *info)
 {
-    if (!c || !chi || !F) return HH_EINVAL;
+    if (!c || !chi || !F || !aligned16(chi)) return HH_EINVAL;
     int rc = ensure_rhs(c, n_rhs);
     if (rc) return rc;
     rc = make_plan(c, chi, c->xsol, n_rhs);
@@ -556,7 +549,7 @@ int hh_force(hh_ctx *c, const double *chi, int n_rhs, double *F, hh_solve_info *
 
 int hh_action(hh_ctx *c, const double *chi, int n_rhs, double *S, hh_solve_info *info)
 {
-    if (!c || !chi || !S) return HH_EINVAL;
+    if (!c || !chi || !S || !aligned16(chi)) return HH_EINVAL;
     int rc = ensure_rhs(c, n_rhs);
     if (rc) return rc;
     rc = make_plan(c, chi, c->xsol, n_rhs);
@@ -615,7 +608,7 @@ extern "C" {
 int hh_leapfrog(hh_ctx *c, double *pi, const double *chi, int n_rhs, int n_md, double dt,
                 hh_solve_info *info)
 {
-    if (!c || !pi || !chi || n_md < 1) return HH_EINVAL;
+    if (!c || !pi || !chi || n_md < 1 || !aligned16(chi)) return HH_EINVAL;
     int rc = ensure_rhs(c, n_rhs);
     if (rc) return rc;
     k_zero_stats<<<1, 32, 0, c->stream>>>(c->d_stats);
@@ -713,6 +706,7 @@ int hh_counters_get(hh_ctx *c, hh_counters *out)
     out->cg_steps = t.cg_steps;
     out->ru_steps = t.ru_steps;
     out->solves = t.solves;
+    out->fp64_steps = t.fp64_steps;
     out->sites = c->N;
     return HH_OK;
 }

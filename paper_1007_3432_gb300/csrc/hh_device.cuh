@@ -122,6 +122,136 @@ __device__ __forceinline__ T stencil_MT(const Geo &g, T h, const T *__restrict__
 }
 
 // ---------------------------------------------------------------------------
+// Short vectors of W consecutive elements (W = 1, 2, 4), loaded and stored
+// with 8- or 16-byte accesses.  The address must be aligned to the access.
+// 'vld' uses the coherent path (data written earlier in the same kernel);
+// 'vldg' the read-only path (links, right-hand sides).
+// ---------------------------------------------------------------------------
+template <typename T, int W>
+struct Vec {
+    T a[W];
+};
+
+template <typename T, int W>
+__device__ __forceinline__ Vec<T, W> vld(const T *p)
+{
+    Vec<T, W> r;
+    if constexpr (sizeof(T) == 8 && W >= 2) {
+#pragma unroll
+        for (int j = 0; j < W; j += 2) {
+            double2 q = *reinterpret_cast<const double2 *>(p + j);
+            r.a[j] = q.x;
+            r.a[j + 1] = q.y;
+        }
+    } else if constexpr (sizeof(T) == 4 && W == 4) {
+        float4 q = *reinterpret_cast<const float4 *>(p);
+        r.a[0] = q.x; r.a[1] = q.y; r.a[2] = q.z; r.a[3] = q.w;
+    } else if constexpr (sizeof(T) == 4 && W == 2) {
+        float2 q = *reinterpret_cast<const float2 *>(p);
+        r.a[0] = q.x; r.a[1] = q.y;
+    } else {
+#pragma unroll
+        for (int j = 0; j < W; ++j) r.a[j] = p[j];
+    }
+    return r;
+}
+
+template <typename T, int W>
+__device__ __forceinline__ Vec<T, W> vldg(const T *p)
+{
+    Vec<T, W> r;
+    if constexpr (sizeof(T) == 8 && W >= 2) {
+#pragma unroll
+        for (int j = 0; j < W; j += 2) {
+            double2 q = __ldg(reinterpret_cast<const double2 *>(p + j));
+            r.a[j] = q.x;
+            r.a[j + 1] = q.y;
+        }
+    } else if constexpr (sizeof(T) == 4 && W == 4) {
+        float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+        r.a[0] = q.x; r.a[1] = q.y; r.a[2] = q.z; r.a[3] = q.w;
+    } else if constexpr (sizeof(T) == 4 && W == 2) {
+        float2 q = __ldg(reinterpret_cast<const float2 *>(p));
+        r.a[0] = q.x; r.a[1] = q.y;
+    } else {
+#pragma unroll
+        for (int j = 0; j < W; ++j) r.a[j] = __ldg(p + j);
+    }
+    return r;
+}
+
+template <typename T, int W>
+__device__ __forceinline__ void vst(T *p, const Vec<T, W> &v)
+{
+    if constexpr (sizeof(T) == 8 && W >= 2) {
+#pragma unroll
+        for (int j = 0; j < W; j += 2) *reinterpret_cast<double2 *>(p + j) = make_double2(v.a[j], v.a[j + 1]);
+    } else if constexpr (sizeof(T) == 4 && W == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v.a[0], v.a[1], v.a[2], v.a[3]);
+    } else if constexpr (sizeof(T) == 4 && W == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(v.a[0], v.a[1]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < W; ++j) p[j] = v.a[j];
+    }
+}
+
+// Neighbour rows of a group of W consecutive x sites starting at site i
+// (x0 = i mod Nx, W divides Nx, so the group stays inside one x row).
+struct GroupNbr {
+    int left, right;     // site before the group / after it along x (periodic)
+    int yp, ym, zp, zm;  // the group's start shifted by +-1 in y and z (periodic)
+    int prev, next;      // the group's start one slice earlier / later (cyclic)
+};
+
+template <int D, int W>
+__device__ __forceinline__ void group_nbrs(const Geo &g, int i, GroupNbr &nb)
+{
+    uint32_t tau = fd_div((uint32_t)i, g.f_V);
+    int s = i - (int)tau * g.V;
+    uint32_t yz = fd_div((uint32_t)s, g.f_nx);
+    int x0 = s - (int)yz * g.nx;
+    nb.left = (x0 == 0) ? i + (g.nx - 1) : i - 1;
+    nb.right = (x0 + W == g.nx) ? i + W - g.nx : i + W;
+    if (D == 3) {
+        uint32_t z = fd_div(yz, g.f_nx);
+        int y = (int)yz - (int)z * g.nx;
+        int sy = g.nx, sz = g.nx * g.nx;
+        nb.yp = (y == g.nx - 1) ? i - (g.nx - 1) * sy : i + sy;
+        nb.ym = (y == 0) ? i + (g.nx - 1) * sy : i - sy;
+        nb.zp = ((int)z == g.nx - 1) ? i - (g.nx - 1) * sz : i + sz;
+        nb.zm = (z == 0) ? i + (g.nx - 1) * sz : i - sz;
+    }
+    nb.prev = (tau == 0) ? i + (g.ntau - 1) * g.V : i - g.V;
+    nb.next = ((int)tau == g.ntau - 1) ? i - (g.ntau - 1) * g.V : i + g.V;
+}
+
+// Spatial hopping sums of a group: for site u the x neighbours are the
+// group's own elements except at the two ends.
+template <int D, typename T, int W>
+__device__ __forceinline__ Vec<T, W> group_hop(const T *v, const GroupNbr &nb, const Vec<T, W> &self)
+{
+    T vl = v[nb.left], vr = v[nb.right];
+    Vec<T, W> out;
+    Vec<T, W> yp, ym, zp, zm;
+    if (D == 3) {
+        yp = vld<T, W>(v + nb.yp);
+        ym = vld<T, W>(v + nb.ym);
+        zp = vld<T, W>(v + nb.zp);
+        zm = vld<T, W>(v + nb.zm);
+    }
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+        T xr = (u == W - 1) ? vr : self.a[u + 1 < W ? u + 1 : u];
+        T xl = (u == 0) ? vl : self.a[u > 0 ? u - 1 : 0];
+        T hsum = xr + xl;
+        if (D == 3) hsum += (yp.a[u] + ym.a[u]) + (zp.a[u] + zm.a[u]);
+        out.a[u] = hsum;
+    }
+    return out;
+}
+
+// ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Counter layout of the
 // library: (block, tag | a << 8, trajectory, chain), key (seed, 0).
 // ---------------------------------------------------------------------------
@@ -187,13 +317,15 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 }
 
 // ---------------------------------------------------------------------------
-// Grid barrier for cooperative (co-resident) launches.  Sense by generation
-// counter; every wait is bounded by a wall-clock budget read from the global
-// timer, after which the barrier records an error and returns false.
+// Grid barrier for cooperative (co-resident) launches.  Each block adds one to
+// a monotonic arrival counter (zeroed before every launch) and waits until the
+// counter reaches the next multiple of the grid size.  Every wait is bounded by
+// a wall-clock budget read from the global timer, after which the barrier
+// records an error and returns false.
 // ---------------------------------------------------------------------------
 struct BarrierCtl {
-    unsigned int count;
-    unsigned int gen;
+    unsigned int count; // arrivals since the launch began; zeroed before each launch
+    unsigned int gen;   // unused padding kept for layout stability
     int error;          // 0, or a negative library error code
     int active;         // systems still running (engine bookkeeping)
     long long k;        // engine iteration counter, persists across launches
@@ -220,39 +352,34 @@ __device__ __forceinline__ int ld_volatile_i32(const int *p)
     return *(const volatile int *)p;
 }
 
-// Returns false if the barrier timed out or another block recorded an error.
-__device__ __forceinline__ bool grid_barrier(BarrierCtl *ctl, unsigned nblocks, unsigned &gen_local,
+// 'target' is block-private and starts at 0.  Returns false if the barrier
+// timed out or another block recorded an error.
+__device__ __forceinline__ bool grid_barrier(BarrierCtl *ctl, unsigned nblocks, unsigned &target,
                                              int *s_flag)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned g = gen_local;
+        target += nblocks;
         int ok = 1;
         __threadfence();
-        unsigned old = atomicAdd(&ctl->count, 1u);
-        if (old == nblocks - 1) {
-            ctl->count = 0;
-            __threadfence();
-            atomicExch(&ctl->gen, g + 1);
-        } else {
-            uint64_t t0 = global_ns();
-            unsigned spins = 0;
-            while (ld_acquire_u32(&ctl->gen) == g) {
-                if ((++spins & 255u) == 0) {
-                    if (ld_volatile_i32(&ctl->error) != 0) {
-                        ok = 0;
-                        break;
-                    }
-                    if ((long long)(global_ns() - t0) > ctl->timeout_ns) {
-                        atomicCAS(&ctl->error, 0, -6);
-                        ok = 0;
-                        break;
-                    }
+        atomicAdd(&ctl->count, 1u);
+        unsigned spins = 0;
+        uint64_t t0 = 0;
+        while ((int)(ld_acquire_u32(&ctl->count) - target) < 0) {
+            if ((++spins & 127u) == 0) {
+                if (t0 == 0) t0 = global_ns();
+                if (ld_volatile_i32(&ctl->error) != 0) {
+                    ok = 0;
+                    break;
+                }
+                if ((long long)(global_ns() - t0) > ctl->timeout_ns) {
+                    atomicCAS(&ctl->error, 0, -6);
+                    ok = 0;
+                    break;
                 }
             }
         }
-        if (ld_volatile_i32(&ctl->error) != 0) ok = 0;
-        gen_local = g + 1;
+        if (ok && ld_volatile_i32(&ctl->error) != 0) ok = 0;
         *s_flag = ok;
     }
     __syncthreads();

@@ -1,5 +1,14 @@
 // Persistent conjugate-gradient engine (Sec. 4.1: CG on Q = M^T M).
 // The slot/mode structure is described in hh_engine.cuh.
+//
+// GB300 layout of the work: one 512-thread block per SM, every block owning
+// fixed tiles of contiguous sites; a thread handles kUnroll sites of a tile
+// per step, issuing all their loads (the site, its 2d spatial neighbours, the
+// time neighbour and the link) before any arithmetic, so that each thread has
+// several independent L2/HBM requests in flight.  The lattice dimension is a
+// compile-time parameter of the site loops.
+#include <cstdlib>
+
 #include "hh_engine.cuh"
 
 namespace hh {
@@ -9,10 +18,134 @@ namespace {
 constexpr int kNumericErr = -5;
 constexpr int kNoConv = -4;
 
+// ---------------------------------------------------------------------------
+// Site loops over [b, e) of one system, in groups of W consecutive x sites per
+// thread (b and e are multiples of W).  Each returns this thread's partial
+// sum (|t|^2 or |r|^2), accumulated in T.
+// ---------------------------------------------------------------------------
+
+// t = M v; acc += t^2.                                      (Eq. (10))
+template <int D, typename T, int W>
+__device__ double gloop_M(const Geo g, const T h, const T *__restrict__ L, const T *v, T *t, int b,
+                          int e)
+{
+    T acc = T(0);
+    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+        GroupNbr nb;
+        group_nbrs<D, W>(g, i, nb);
+        Vec<T, W> self = vld<T, W>(v + i);
+        Vec<T, W> hs = group_hop<D, T, W>(v, nb, self);
+        Vec<T, W> lk = vldg<T, W>(L + nb.prev);
+        Vec<T, W> pv = vld<T, W>(v + nb.prev);
+        Vec<T, W> out;
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            out.a[u] = fma(lk.a[u], pv.a[u], fma(-h, hs.a[u], self.a[u]));
+            acc = fma(out.a[u], out.a[u], acc);
+        }
+        vst<T, W>(t + i, out);
+    }
+    return (double)acc;
+}
+
+// CG slot 3: q = M^T t, x += alpha p, r -= alpha q; acc += r^2.
+template <int D, typename T, int W>
+__device__ double gloop_update(const Geo g, const T h, const T *__restrict__ L, const T *t, T *x,
+                               const T *p, T *r, const T alpha, int b, int e)
+{
+    T acc = T(0);
+    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+        GroupNbr nb;
+        group_nbrs<D, W>(g, i, nb);
+        Vec<T, W> self = vld<T, W>(t + i);
+        Vec<T, W> hs = group_hop<D, T, W>(t, nb, self);
+        Vec<T, W> lk = vldg<T, W>(L + i);
+        Vec<T, W> nv = vld<T, W>(t + nb.next);
+        Vec<T, W> xv = vld<T, W>(x + i);
+        Vec<T, W> pv = vld<T, W>(p + i);
+        Vec<T, W> rv = vld<T, W>(r + i);
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            T q = fma(lk.a[u], nv.a[u], fma(-h, hs.a[u], self.a[u]));
+            xv.a[u] = fma(alpha, pv.a[u], xv.a[u]);
+            rv.a[u] = fma(-alpha, q, rv.a[u]);
+            acc = fma(rv.a[u], rv.a[u], acc);
+        }
+        vst<T, W>(x + i, xv);
+        vst<T, W>(r + i, rv);
+    }
+    return (double)acc;
+}
+
+// RU slot 3 (FP64): res = b - M^T t64; r64 = res and, for a mixed system,
+// r32 = (float)res; acc += res^2.
+template <int D, int W>
+__device__ double gloop_residual(const Geo g, const double h, const double *__restrict__ L,
+                                 const double *t, const double *__restrict__ bvec, double *r, float *r32,
+                                 int b, int e)
+{
+    double acc = 0.0;
+    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+        GroupNbr nb;
+        group_nbrs<D, W>(g, i, nb);
+        Vec<double, W> self = vld<double, W>(t + i);
+        Vec<double, W> hs = group_hop<D, double, W>(t, nb, self);
+        Vec<double, W> lk = vldg<double, W>(L + i);
+        Vec<double, W> nv = vld<double, W>(t + nb.next);
+        Vec<double, W> bv = vldg<double, W>(bvec + i);
+        Vec<float, W> r32v;
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            double q = fma(lk.a[u], nv.a[u], fma(-h, hs.a[u], self.a[u]));
+            bv.a[u] = bv.a[u] - q;
+            r32v.a[u] = (float)bv.a[u];
+            acc = fma(bv.a[u], bv.a[u], acc);
+        }
+        vst<double, W>(r + i, bv);
+        if (r32) vst<float, W>(r32 + i, r32v);
+    }
+    return acc;
+}
+
+// p = r + beta p (restart: p = r).
+template <typename T, int W>
+__device__ void gloop_direction(const T *r, T *p, const T beta, bool restart, int b, int e)
+{
+    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+        Vec<T, W> rv = vld<T, W>(r + i);
+        if (!restart) {
+            Vec<T, W> pv = vld<T, W>(p + i);
+#pragma unroll
+            for (int u = 0; u < W; ++u) rv.a[u] = fma(beta, pv.a[u], rv.a[u]);
+        }
+        vst<T, W>(p + i, rv);
+    }
+}
+
+// x64 += x32, x32 = 0 (reliable update of a mixed system).
+template <int W>
+__device__ void gloop_accumulate(double *x, float *x32, int b, int e)
+{
+    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+        Vec<double, W> xv = vld<double, W>(x + i);
+        Vec<float, W> yv = vld<float, W>(x32 + i), z;
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            xv.a[u] += (double)yv.a[u];
+            z.a[u] = 0.0f;
+        }
+        vst<double, W>(x + i, xv);
+        vst<float, W>(x32 + i, z);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-system decisions.
+// ---------------------------------------------------------------------------
+
 // Fixed-order sum of per-tile partials [t0, t0 + n): lane-strided sequential
-// sums in warp 0 followed by a fixed shuffle tree; the value is broadcast to
-// the whole block.  Every block that calls it on the same data gets the same
-// bits.
+// sums in warp 0 followed by a fixed shuffle tree, broadcast to the block.
+// Every block that calls it on the same data gets the same bits.
 __device__ double sum_partials(const double *part, int t0, int n, double *s_val)
 {
     __syncthreads();
@@ -26,11 +159,6 @@ __device__ double sum_partials(const double *part, int t0, int n, double *s_val)
     double r = *s_val;
     __syncthreads();
     return r;
-}
-
-__device__ __forceinline__ bool finite(double v)
-{
-    return isfinite(v);
 }
 
 // Next mode of a system from its previous state and the |r|^2 reduced from the
@@ -48,11 +176,16 @@ __device__ EngState decide(const EngSystem &Y, const EngState &P, double rr)
         S.status = 0;
         S.final_ru = 0;
         S.true_relres = 1.0;
+        S.prec = Y.precision;
+        S.stall = 0;
+        S.fp64_steps = 0;
+        S.since_ru = 0;
         return S;
     case MODE_INIT:
         S.bb = rr;
         S.rr_last = rr;
-        if (!finite(rr)) {
+        S.rr_ru = rr;
+        if (!isfinite(rr)) {
             S.mode = MODE_DONE;
             S.status = kNumericErr;
             return S;
@@ -69,14 +202,17 @@ __device__ EngState decide(const EngSystem &Y, const EngState &P, double rr)
         return S;
     case MODE_CG: {
         S.cg_steps = P.cg_steps + 1;
+        if (P.prec == PREC_FP64) S.fp64_steps = P.fp64_steps + 1;
         S.rr_last = rr;
-        if (!finite(rr)) {
+        if (!isfinite(rr)) {
             S.mode = MODE_DONE;
             S.status = kNumericErr;
             return S;
         }
+        S.since_ru = P.since_ru + 1;
         bool need = rr <= Y.tol2 * P.bb;
-        if (Y.precision == PREC_MIXED && rr < Y.delta2 * P.maxr2) need = true;
+        if (P.prec == PREC_MIXED && rr < Y.delta2 * P.maxr2) need = true;
+        if (P.prec == PREC_MIXED && S.since_ru >= Y.stall_window) need = true;
         if (S.cg_steps >= Y.maxit) {
             need = true;
             S.final_ru = 1;
@@ -96,7 +232,7 @@ __device__ EngState decide(const EngSystem &Y, const EngState &P, double rr)
         S.n_ru = P.n_ru + 1;
         S.rr_last = rr;
         S.true_relres = sqrt(rr / P.bb);
-        if (!finite(rr)) {
+        if (!isfinite(rr)) {
             S.mode = MODE_DONE;
             S.status = kNumericErr;
             return S;
@@ -115,131 +251,83 @@ __device__ EngState decide(const EngSystem &Y, const EngState &P, double rr)
         S.beta = rr / P.rr_alpha;
         S.rr_alpha = rr;
         S.maxr2 = rr;
+        S.since_ru = 0;
+        if (P.prec == PREC_MIXED) {
+            // A reliable update that did not halve the true residual norm
+            // since the previous one (whether the FP32 residual fell below
+            // delta or the stall window ran out) means the FP32 steps have
+            // stopped making progress (eps_32 * cond(Q) >~ 1).  After two in a
+            // row the system continues with FP64 CG steps from a restart at
+            // the FP64 residual.
+            S.stall = (rr > 0.25 * P.rr_ru) ? P.stall + 1 : 0;
+            if (S.stall >= 2) {
+                S.prec = PREC_FP64;
+                S.beta = 0.0;
+            }
+        }
+        S.rr_ru = rr;
         return S;
     }
     }
 }
 
-// ---- slot 1 -----------------------------------------------------------------
-__device__ void slot1_work(const EngSystem &Y, const EngState &S, const EngTile &T)
+// ---------------------------------------------------------------------------
+// Slot bodies for one tile (D and W fixed; mode and precision from the state).
+// ---------------------------------------------------------------------------
+struct TileCtl {
+    int mode, prec;
+    double beta, alpha;
+};
+
+template <int D, int W>
+__device__ void slot1(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 {
-    if (S.mode == MODE_CG) {
-        if (Y.precision == PREC_FP64) {
-            const double beta = S.beta;
-            if (beta == 0.0) {
-                for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) Y.p[i] = Y.r[i];
-            } else {
-                for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x)
-                    Y.p[i] = fma(beta, Y.p[i], Y.r[i]);
-            }
-        } else {
-            const float beta = (float)S.beta;
-            if (S.beta == 0.0) {
-                for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) Y.p32[i] = Y.r32[i];
-            } else {
-                for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x)
-                    Y.p32[i] = fmaf(beta, Y.p32[i], Y.r32[i]);
-            }
-        }
-    } else if (S.mode == MODE_RU) {
-        if (Y.precision == PREC_MIXED) {
-            for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
-                Y.x[i] += (double)Y.x32[i];
-                Y.x32[i] = 0.0f;
-            }
-        }
-    } else if (S.mode == MODE_INIT) {
+    if (c.mode == MODE_CG) {
+        bool restart = (c.beta == 0.0);
+        if (c.prec == PREC_FP64)
+            gloop_direction<double, W>(Y.r, Y.p, c.beta, restart, T.begin, T.end);
+        else
+            gloop_direction<float, W>(Y.r32, Y.p32, (float)c.beta, restart, T.begin, T.end);
+    } else if (c.mode == MODE_RU) {
+        if (c.prec == PREC_MIXED) gloop_accumulate<W>(Y.x, Y.x32, T.begin, T.end);
+    } else if (c.mode == MODE_INIT) {
         for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) Y.x[i] = 0.0;
         if (Y.precision == PREC_MIXED)
             for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) Y.x32[i] = 0.0f;
     }
 }
 
-// ---- slot 2: t = M p (CG) or t64 = M x64 (RU); returns this thread's |t|^2 --
-__device__ double slot2_work(const EngSystem &Y, const EngState &S, const EngTile &T)
+template <int D, int W>
+__device__ double slot2(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 {
-    const Geo &g = Y.g;
-    Nbr nb;
-    if (S.mode == MODE_CG) {
-        if (Y.precision == PREC_FP64) {
-            double acc = 0.0;
-            for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
-                neighbours(g, i, nb);
-                double v = stencil_M<double>(g, Y.h, Y.L64, Y.p, i, nb);
-                Y.t[i] = v;
-                acc = fma(v, v, acc);
-            }
-            return acc;
-        } else {
-            float acc = 0.0f;
-            const float h = (float)Y.h;
-            for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
-                neighbours(g, i, nb);
-                float v = stencil_M<float>(g, h, Y.L32, Y.p32, i, nb);
-                Y.t32[i] = v;
-                acc = fmaf(v, v, acc);
-            }
-            return (double)acc;
-        }
-    } else if (S.mode == MODE_RU) {
-        for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
-            neighbours(g, i, nb);
-            Y.t[i] = stencil_M<double>(g, Y.h, Y.L64, Y.x, i, nb);
-        }
+    if (c.mode == MODE_CG) {
+        if (c.prec == PREC_FP64)
+            return gloop_M<D, double, W>(Y.g, Y.h, Y.L64, Y.p, Y.t, T.begin, T.end);
+        return gloop_M<D, float, W>(Y.g, (float)Y.h, Y.L32, Y.p32, Y.t32, T.begin, T.end);
     }
+    if (c.mode == MODE_RU) gloop_M<D, double, W>(Y.g, Y.h, Y.L64, Y.x, Y.t, T.begin, T.end);
     return 0.0;
 }
 
-// ---- slot 3: returns this thread's |r|^2 -------------------------------------
-__device__ double slot3_work(const EngSystem &Y, const EngState &S, const EngTile &T, double alpha)
+template <int D, int W>
+__device__ double slot3(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 {
-    const Geo &g = Y.g;
-    Nbr nb;
-    if (S.mode == MODE_CG) {
-        if (Y.precision == PREC_FP64) {
-            double acc = 0.0;
-            for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
-                neighbours(g, i, nb);
-                double q = stencil_MT<double>(g, Y.h, Y.L64, Y.t, i, nb);
-                Y.x[i] = fma(alpha, Y.p[i], Y.x[i]);
-                double r = fma(-alpha, q, Y.r[i]);
-                Y.r[i] = r;
-                acc = fma(r, r, acc);
-            }
-            return acc;
-        } else {
-            float acc = 0.0f;
-            const float a = (float)alpha, h = (float)Y.h;
-            for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
-                neighbours(g, i, nb);
-                float q = stencil_MT<float>(g, h, Y.L32, Y.t32, i, nb);
-                Y.x32[i] = fmaf(a, Y.p32[i], Y.x32[i]);
-                float r = fmaf(-a, q, Y.r32[i]);
-                Y.r32[i] = r;
-                acc = fmaf(r, r, acc);
-            }
-            return (double)acc;
-        }
-    } else if (S.mode == MODE_RU) {
+    if (c.mode == MODE_CG) {
+        if (c.prec == PREC_FP64)
+            return gloop_update<D, double, W>(Y.g, Y.h, Y.L64, Y.t, Y.x, Y.p, Y.r, c.alpha, T.begin,
+                                              T.end);
+        return gloop_update<D, float, W>(Y.g, (float)Y.h, Y.L32, Y.t32, Y.x32, Y.p32, Y.r32,
+                                         (float)c.alpha, T.begin, T.end);
+    }
+    if (c.mode == MODE_RU)
+        return gloop_residual<D, W>(Y.g, Y.h, Y.L64, Y.t, Y.b, Y.r,
+                                    Y.precision == PREC_MIXED ? Y.r32 : nullptr, T.begin, T.end);
+    if (c.mode == MODE_INIT) {
         double acc = 0.0;
         for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
-            neighbours(g, i, nb);
-            double res = Y.b[i] - stencil_MT<double>(g, Y.h, Y.L64, Y.t, i, nb);
-            if (Y.precision == PREC_FP64)
-                Y.r[i] = res;
-            else
-                Y.r32[i] = (float)res;
-            acc = fma(res, res, acc);
-        }
-        return acc;
-    } else if (S.mode == MODE_INIT) {
-        double acc = 0.0;
-        for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
-            double bi = Y.b[i];
-            if (Y.precision == PREC_FP64)
-                Y.r[i] = bi;
-            else
-                Y.r32[i] = (float)bi;
+            double bi = __ldg(Y.b + i);
+            Y.r[i] = bi;
+            if (Y.precision == PREC_MIXED) Y.r32[i] = (float)bi;
             acc = fma(bi, bi, acc);
         }
         return acc;
@@ -247,86 +335,148 @@ __device__ double slot3_work(const EngSystem &Y, const EngState &S, const EngTil
     return 0.0;
 }
 
-__global__ void __launch_bounds__(ENGINE_BLOCK) engine_kernel(EngLaunch L)
+// Dispatch on the lattice dimension and the group width of the system.
+template <int SLOT>
+__device__ double run_slot(const EngSystem &Y, const TileCtl &c, const EngTile &T)
+{
+#define HH_SLOT_CALL(D, W)                                   \
+    if (SLOT == 1) {                                         \
+        slot1<D, W>(Y, c, T);                                \
+        return 0.0;                                          \
+    } else if (SLOT == 2) {                                  \
+        return slot2<D, W>(Y, c, T);                         \
+    } else {                                                 \
+        return slot3<D, W>(Y, c, T);                         \
+    }
+    const int w = Y.w;
+    if (Y.g.d == 3) {
+        if (w == 4) { HH_SLOT_CALL(3, 4) }
+        if (w == 2) { HH_SLOT_CALL(3, 2) }
+        HH_SLOT_CALL(3, 1)
+    } else {
+        if (w == 4) { HH_SLOT_CALL(1, 4) }
+        if (w == 2) { HH_SLOT_CALL(1, 2) }
+        HH_SLOT_CALL(1, 1)
+    }
+#undef HH_SLOT_CALL
+}
+
+__global__ void __launch_bounds__(ENGINE_BLOCK, 1) engine_kernel(EngLaunch L)
 {
     __shared__ double s_red[ENGINE_BLOCK / 32];
     __shared__ double s_val;
     __shared__ int s_flag;
-    __shared__ unsigned s_gen;
+    __shared__ EngState s_state;
+    __shared__ TileCtl s_ctl;
 
     BarrierCtl *ctl = L.ctl;
     const unsigned G = gridDim.x;
-    if (threadIdx.x == 0) s_gen = *(volatile unsigned *)&ctl->gen;
-    __syncthreads();
-    unsigned gen = s_gen;
+    unsigned target = 0;
     long long k = *(volatile long long *)&ctl->k;
 
     for (long long it = 0; it < L.max_iters; ++it, ++k) {
-        EngState *cur = L.state[k & 1];
-        EngState *nxt = L.state[(k + 1) & 1];
+        EngState *cur = (k & 1) ? L.state[1] : L.state[0];
+        EngState *nxt = (k & 1) ? L.state[0] : L.state[1];
 
-        // ---- slot 1: decide, then p update / reliable-update accumulate ----
+        // ---- slot 1: decide, then direction update / reliable-update accumulate ----
         {
             int last = -1;
-            EngState S;
             for (int tile = blockIdx.x; tile < L.ntiles; tile += G) {
                 const EngTile T = L.tiles[tile];
                 const EngSystem &Y = L.sys[T.sys];
                 if (T.sys != last) {
-                    const EngState P = cur[T.sys];
+                    __syncthreads();
+                    if (threadIdx.x == 0) s_state = cur[T.sys];
+                    __syncthreads();
+                    const int pm = s_state.mode;
                     double rr = 0.0;
-                    if (P.mode == MODE_INIT || P.mode == MODE_CG || P.mode == MODE_RU)
+                    if (pm == MODE_INIT || pm == MODE_CG || pm == MODE_RU)
                         rr = sum_partials(L.part_rr, Y.tile0, Y.ntiles, &s_val);
-                    S = decide(Y, P, rr);
-                    last = T.sys;
-                    if ((int)blockIdx.x == Y.owner && threadIdx.x == 0) {
-                        nxt[T.sys] = S;
-                        if (S.mode == MODE_DONE && P.mode != MODE_DONE) atomicSub(&ctl->active, 1);
+                    if (threadIdx.x == 0) {
+                        const EngState P = s_state;
+                        const EngState S = decide(Y, P, rr);
+                        if ((int)blockIdx.x == Y.owner) {
+                            nxt[T.sys] = S;
+                            if (S.mode == MODE_DONE && P.mode != MODE_DONE) atomicSub(&ctl->active, 1);
+                        }
+                        s_ctl.mode = S.mode;
+                        s_ctl.prec = S.prec;
+                        s_ctl.beta = S.beta;
+                        s_ctl.alpha = 0.0;
                     }
+                    __syncthreads();
+                    last = T.sys;
                 }
-                slot1_work(Y, S, T);
+                const TileCtl c = s_ctl;
+                run_slot<1>(Y, c, T);
             }
         }
-        if (!grid_barrier(ctl, G, gen, &s_flag)) return;
+        if (!grid_barrier(ctl, G, target, &s_flag)) return;
         if (ld_volatile_i32(&ctl->active) <= 0) {
             if (blockIdx.x == 0 && threadIdx.x == 0) ctl->k = k + 1;
             return;
         }
 
         // ---- slot 2 ----
-        for (int tile = blockIdx.x; tile < L.ntiles; tile += G) {
-            const EngTile T = L.tiles[tile];
-            const EngSystem &Y = L.sys[T.sys];
-            const EngState S = nxt[T.sys];
-            double v = slot2_work(Y, S, T);
-            if (S.mode == MODE_CG) {
-                double tot = block_sum(v, s_red);
-                if (threadIdx.x == 0) L.part_tt[tile] = tot;
+        {
+            int last = -1;
+            for (int tile = blockIdx.x; tile < L.ntiles; tile += G) {
+                const EngTile T = L.tiles[tile];
+                const EngSystem &Y = L.sys[T.sys];
+                if (T.sys != last) {
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        const EngState S = nxt[T.sys];
+                        s_ctl.mode = S.mode;
+                        s_ctl.prec = S.prec;
+                        s_ctl.beta = S.beta;
+                        s_ctl.alpha = 0.0;
+                    }
+                    __syncthreads();
+                    last = T.sys;
+                }
+                const TileCtl c = s_ctl;
+                double v = run_slot<2>(Y, c, T);
+                if (c.mode == MODE_CG) {
+                    double tot = block_sum(v, s_red);
+                    if (threadIdx.x == 0) L.part_tt[tile] = tot;
+                }
             }
         }
-        if (!grid_barrier(ctl, G, gen, &s_flag)) return;
+        if (!grid_barrier(ctl, G, target, &s_flag)) return;
 
         // ---- slot 3 ----
         {
             int last = -1;
-            double alpha = 0.0;
             for (int tile = blockIdx.x; tile < L.ntiles; tile += G) {
                 const EngTile T = L.tiles[tile];
                 const EngSystem &Y = L.sys[T.sys];
-                const EngState S = nxt[T.sys];
-                if (S.mode == MODE_CG && T.sys != last) {
-                    double tt = sum_partials(L.part_tt, Y.tile0, Y.ntiles, &s_val);
-                    alpha = S.rr_alpha / tt;
+                if (T.sys != last) {
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        const EngState S = nxt[T.sys];
+                        s_state = S;
+                        s_ctl.mode = S.mode;
+                        s_ctl.prec = S.prec;
+                        s_ctl.beta = S.beta;
+                    }
+                    __syncthreads();
+                    if (s_ctl.mode == MODE_CG) {
+                        double tt = sum_partials(L.part_tt, Y.tile0, Y.ntiles, &s_val);
+                        if (threadIdx.x == 0) s_ctl.alpha = s_state.rr_alpha / tt;
+                    }
+                    __syncthreads();
                     last = T.sys;
                 }
-                double v = slot3_work(Y, S, T, alpha);
-                if (S.mode == MODE_CG || S.mode == MODE_RU || S.mode == MODE_INIT) {
+                const TileCtl c = s_ctl;
+                double v = run_slot<3>(Y, c, T);
+                if (c.mode == MODE_CG || c.mode == MODE_RU || c.mode == MODE_INIT) {
                     double tot = block_sum(v, s_red);
                     if (threadIdx.x == 0) L.part_rr[tile] = tot;
                 }
             }
         }
-        if (!grid_barrier(ctl, G, gen, &s_flag)) return;
+        if (!grid_barrier(ctl, G, target, &s_flag)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->k = k;
 }
@@ -349,6 +499,19 @@ int engine_max_grid(int block)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, engine_kernel, block, 0) != cudaSuccess)
         return 0;
     return per * nsm;
+}
+
+int engine_default_grid()
+{
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    int mx = engine_max_grid(ENGINE_BLOCK);
+    const char *env = getenv("HH_ENGINE_BLOCKS_PER_SM");
+    int per = env ? atoi(env) : 1;
+    if (per < 1) per = 1;
+    int g = per * nsm;
+    return g < mx ? g : mx;
 }
 
 }  // namespace hh

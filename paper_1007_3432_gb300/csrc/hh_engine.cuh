@@ -46,8 +46,21 @@ struct EngSystem {
     double tol2;                      // cg_tol^2
     double delta2;                    // reliable_delta^2 (mixed)
     int maxit;
+    int w;                            // x sites per thread group: 4, 2 or 1 (divides Nx)
+    int stall_window;                 // mixed: forced RU after this many FP32 steps without one
     int pad;
 };
+
+// FP32 steps after which a mixed system takes a reliable update even if its
+// FP32 residual has not dropped by reliable_delta (a plateau of the FP32
+// iteration when eps_32 * cond(Q) >~ 1).
+constexpr int ENGINE_STALL_WINDOW = 2000;
+
+// Group width for a lattice: the largest of 4, 2, 1 that divides Nx.
+__host__ __device__ inline int engine_group_width(int nx)
+{
+    return (nx % 4 == 0) ? 4 : (nx % 2 == 0) ? 2 : 1;
+}
 
 struct EngState {
     double bb;          // |b|^2
@@ -56,11 +69,18 @@ struct EngState {
     double maxr2;       // max |r|^2 since the last reliable update (mixed)
     double beta;
     double true_relres; // last true relative residual (RU)
+    double rr_ru;       // true |r|^2 at the last RU (stall detection)
     int mode;           // mode executed in the iteration that wrote this state
     int cg_steps;
     int n_ru;
     int status;         // 0, or HH_ENOCONV / HH_ENUMERIC
     int final_ru;       // RU forced by the iteration cap
+    int prec;           // precision of the CG steps now running (a mixed system
+                        // switches to PREC_FP64 when FP32 steps stop reducing
+                        // the true residual)
+    int stall;          // consecutive reliable updates without progress
+    int fp64_steps;     // CG steps run in FP64
+    int since_ru;       // CG steps since the last RU
     int pad;
 };
 
@@ -81,12 +101,40 @@ struct EngLaunch {
 };
 
 // Host launcher: runs the engine with a cooperative launch of 'grid' blocks.
+// The barrier counter ctl->count must be zero when the launch starts.
 // Returns a cudaError_t from the launch.
 cudaError_t engine_launch(const EngLaunch &L, int grid, int block, cudaStream_t stream);
 
 // Largest co-resident grid for the engine kernel at 'block' threads.
 int engine_max_grid(int block);
 
-constexpr int ENGINE_BLOCK = 256;
+constexpr int ENGINE_BLOCK = 512;
+constexpr int ENGINE_MIN_TILE = 512;   // sites per tile, at least one per thread
+
+// Default grid: one block per SM (fewer arrivals per grid barrier), capped by
+// co-residency.  HH_ENGINE_BLOCKS_PER_SM overrides the blocks per SM.
+int engine_default_grid();
+
+// Tiles of one system: 'tiles' contiguous ranges of 'chunk' sites (the last
+// one shorter), enough to give every block of the grid a tile when 'nsys'
+// systems share the launch.
+struct Tiling {
+    int tiles, chunk;
+};
+
+inline Tiling engine_tiling(int N, int nsys, int max_grid)
+{
+    int by_size = (N + ENGINE_MIN_TILE - 1) / ENGINE_MIN_TILE;
+    int want = (max_grid + nsys - 1) / (nsys > 0 ? nsys : 1);
+    if (want < 1) want = 1;
+    int tps = by_size < want ? by_size : want;
+    if (tps < 1) tps = 1;
+    int chunk = (N + tps - 1) / tps;
+    chunk = (chunk + 31) / 32 * 32;
+    Tiling t;
+    t.chunk = chunk;
+    t.tiles = (N + chunk - 1) / chunk;
+    return t;
+}
 
 }  // namespace hh

@@ -16,6 +16,7 @@
 // call itself.  Calls whose GPU work overlaps (two host threads, or two
 // streams running at once) race on the array and give wrong results; callers
 // must serialise them.
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 
@@ -66,12 +67,8 @@ int setup_device(int dev, unsigned char **base, int *max_grid)
     if (!g_scratch_addr[dev]) {
         void *addr = nullptr;
         if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) return HH_ECUDA;
-        int nsm = 0;
-        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            return HH_ECUDA;
-        int g = engine_max_grid(ENGINE_BLOCK);
+        int g = engine_default_grid();
         if (g <= 0) return HH_ECUDA;
-        if (2 * nsm < g) g = 2 * nsm;
         g_max_grid[dev] = g;
         g_scratch_addr[dev] = (unsigned char *)addr;
     }
@@ -113,6 +110,8 @@ __global__ void k_noalloc_plan(unsigned char *base, Geo g, double h, const doubl
         Y.tol2 = tol * tol;
         Y.delta2 = 0.0;
         Y.maxit = maxit;
+        Y.w = engine_group_width(g.nx);
+        Y.stall_window = ENGINE_STALL_WINDOW;
         *(EngSystem *)(base + kOffSys) = Y;
         EngState z;
         memset(&z, 0, sizeof(z));
@@ -135,6 +134,7 @@ extern "C" int hh_solve_noalloc(const hh_lattice *lat, const hh_params *p, const
                                 const double *b, double *x, void *cuda_stream, hh_solve_info *info)
 {
     if (!lat || !p || !sigma || !b || !x) return HH_EINVAL;
+    if (((uintptr_t)b & 15u) || ((uintptr_t)x & 15u)) return HH_EINVAL;
     if (lat->d != 1 && lat->d != 3) return HH_EINVAL;
     if (lat->nx < 2 || lat->ntau < 2) return HH_EINVAL;
     if (p->precision != HH_FP64 || !(p->cg_tol > 0.0) || p->cg_maxit < 1) return HH_EINVAL;
@@ -151,13 +151,9 @@ extern "C" int hh_solve_noalloc(const hh_lattice *lat, const hh_params *p, const
     if (rc) return rc;
 
     Geo g = make_geo(lat->d, lat->nx, lat->ntau);
-    // The same tiling rule as the context solver: one tile per block of the
-    // grid, at least 256 sites per tile, tile length a multiple of 32.
-    int by_size = (g.N + 255) / 256;
-    int tps = by_size < max_grid ? by_size : max_grid;
-    int chunk = (g.N + tps - 1) / tps;
-    chunk = (chunk + 31) / 32 * 32;
-    int ntiles = (g.N + chunk - 1) / chunk;
+    // The same grid and tiling rule as the context solver.
+    Tiling tl = engine_tiling(g.N, 1, max_grid);
+    int chunk = tl.chunk, ntiles = tl.tiles;
     if (ntiles > kMaxTiles) return HH_ESIZE;
     int grid = ntiles < max_grid ? ntiles : max_grid;
 
