@@ -204,6 +204,103 @@ int hh_counters_reset(hh_ctx *ctx, int profile_engine);
 /* Read the counters; synchronises the context stream. */
 int hh_counters_get(hh_ctx *ctx, hh_counters *out);
 
+/* ---- Batched multi-chain engine and serving loop ---------------------------
+ * Many independent Markov chains and solves, of different lattices, share one
+ * persistent CG launch (the a12/a13 patterns of the build: not in the paper,
+ * whose Sec. 5 runs one lattice at a time).  Requests are admitted into slots
+ * while the HBM budget and the active-site window allow, each slot's state
+ * stays resident on the device, and the engine advances every active system
+ * by 'chunk_iters' CG iterations per launch (a CUDA-graph replay).  Between
+ * launches the host retires finished solves, advances trajectories through
+ * their leapfrog stages (force, sigma step, next solve, Metropolis) and admits
+ * queued requests, so work that arrives while others run joins at the next
+ * chunk (continuous batching).  Every system is tiled by its own size only and
+ * reduced in a fixed order, so its bits do not depend on the other requests
+ * in the mix. */
+#define HH_REQ_SOLVE 0
+#define HH_REQ_TRAJECTORY 1
+
+typedef struct hh_batch hh_batch;
+
+typedef struct {
+    int kind;            /* HH_REQ_SOLVE or HH_REQ_TRAJECTORY */
+    hh_lattice lat;
+    hh_params prm;       /* as for hh_create; for a solve, n_pf is the number of
+                            right-hand sides (1..4) */
+    const double *sigma; /* host, N doubles, copied at submit; NULL: sigma from
+                            Philox tag 0 with prm.seed (as hh_init_field_random) */
+    const double *b;     /* solve: host, n_pf*N doubles copied at submit; NULL:
+                            N(0,1) sources (Philox tag 2, trajectory word traj_index) */
+    double *out;         /* host, written on completion (x for a solve, n_pf*N
+                            doubles; sigma after Metropolis for a trajectory, N
+                            doubles); NULL: not written.  Owned by the caller and
+                            kept alive until the result has been polled. */
+    int n_md;            /* trajectory: leapfrog steps */
+    double dt;           /* trajectory: step size */
+    uint64_t traj_index; /* trajectory number (Philox counter word) */
+} hh_request;
+
+typedef struct {
+    uint64_t ticket;
+    int kind;
+    int status;             /* HH_OK or an error code of the request */
+    int cg_iterations;      /* summed over the request's solves and right-hand sides */
+    int reliable_updates;
+    int n_solves;
+    double max_true_relres;
+    double H0, H1, dH, u;   /* trajectory only */
+    int accepted;
+    double queue_ms;        /* submit -> admitted into a slot */
+    double latency_ms;      /* submit -> result ready */
+} hh_result;
+
+typedef struct {
+    int max_slots;           /* concurrent requests on the device (<= 256) */
+    size_t hbm_budget_bytes; /* device memory for slots (arena allocated at create) */
+    int chunk_iters;         /* CG iterations per engine launch */
+    int tile_sites;          /* sites per tile (multiple of 32) */
+    long long max_active_sites; /* admission window on summed active sites (0: none) */
+} hh_batch_config;
+
+/* Defaults: 64 slots, 4 GiB, 32 iterations per chunk, 4096-site tiles, no window. */
+void hh_batch_default_config(hh_batch_config *cfg);
+
+/* Create a batch engine on the current device and stream.  Allocates the
+ * slot arena (hbm_budget_bytes) and the engine tables.  Errors: HH_EINVAL,
+ * HH_ENOMEM, HH_ECUDA. */
+int hh_batch_create(hh_batch **out, const hh_batch_config *cfg, void *cuda_stream);
+
+/* Stop the worker (if running), free everything.  NULL is accepted. */
+int hh_batch_destroy(hh_batch *b);
+
+/* Queue a request (thread safe, non-blocking); host arrays are copied now.
+ * Returns HH_EBUSY if the request alone needs more than the whole budget,
+ * HH_EINVAL for bad shapes. */
+int hh_batch_submit(hh_batch *b, const hh_request *req, uint64_t *ticket);
+
+/* One scheduling round on the calling thread: admit, run one engine chunk,
+ * advance or retire requests.  *n_busy (may be NULL) receives queued + active
+ * requests.  Must not be called while the worker thread runs. */
+int hh_batch_step(hh_batch *b, int *n_busy);
+
+/* Run scheduling rounds on a background thread until hh_batch_stop. */
+int hh_batch_start(hh_batch *b);
+int hh_batch_stop(hh_batch *b);
+
+/* Move up to max finished results into out (thread safe). */
+int hh_batch_poll(hh_batch *b, hh_result *out, int max, int *n_done);
+
+/* Requests waiting for a slot and requests on the device. */
+int hh_batch_pending(hh_batch *b, int *queued, int *active);
+
+/* Autotuner: time each candidate configuration (tile size, chunk length,
+ * active-site window) on copies of the given solve requests for 'rounds'
+ * scheduling rounds, return the fastest in *best (CG site-iterations per
+ * second), and, if cache_path is not NULL, record it as a JSON line keyed by
+ * the request mix.  Uses a scratch batch of the given budget. */
+int hh_batch_autotune(const hh_request *sample, int n, size_t hbm_budget_bytes, int rounds,
+                      const char *cache_path, void *cuda_stream, hh_batch_config *best);
+
 /* ---- Allocation-free solve ------------------------------------------------
  * The paper has no counterpart of this entry point; it exists for callers
  * that cannot allocate memory when they need a solve: code running while its

@@ -65,6 +65,35 @@ class hh_counters(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class hh_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("lat", hh_lattice), ("prm", hh_params),
+                ("sigma", ctypes.c_void_p), ("b", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("n_md", ctypes.c_int), ("dt", ctypes.c_double), ("traj_index", ctypes.c_uint64)]
+
+
+class hh_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("kind", ctypes.c_int), ("status", ctypes.c_int),
+                ("cg_iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("n_solves", ctypes.c_int), ("max_true_relres", ctypes.c_double),
+                ("H0", ctypes.c_double), ("H1", ctypes.c_double), ("dH", ctypes.c_double),
+                ("u", ctypes.c_double), ("accepted", ctypes.c_int), ("queue_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hh_batch_config(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
+                ("chunk_iters", ctypes.c_int), ("tile_sites", ctypes.c_int),
+                ("max_active_sites", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+HH_REQ_SOLVE, HH_REQ_TRAJECTORY = 0, 1
+
 _lib = None
 
 
@@ -96,6 +125,17 @@ def load(path: str = LIB_PATH):
         "hh_counters_get": (i, [vp, ctypes.POINTER(hh_counters)]),
         "hh_solve_noalloc": (i, [ctypes.POINTER(hh_lattice), ctypes.POINTER(hh_params), vp, vp, vp, vp,
                                  ctypes.POINTER(hh_solve_info)]),
+        "hh_batch_default_config": (None, [ctypes.POINTER(hh_batch_config)]),
+        "hh_batch_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(hh_batch_config), vp]),
+        "hh_batch_destroy": (i, [vp]),
+        "hh_batch_submit": (i, [vp, ctypes.POINTER(hh_request), ctypes.POINTER(u64)]),
+        "hh_batch_step": (i, [vp, ctypes.POINTER(i)]),
+        "hh_batch_start": (i, [vp]),
+        "hh_batch_stop": (i, [vp]),
+        "hh_batch_poll": (i, [vp, ctypes.POINTER(hh_result), i, ctypes.POINTER(i)]),
+        "hh_batch_pending": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "hh_batch_autotune": (i, [ctypes.POINTER(hh_request), i, ctypes.c_size_t, i, ctypes.c_char_p, vp,
+                                  ctypes.POINTER(hh_batch_config)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -258,3 +298,119 @@ def solve_noalloc(d, nx, ntau, sigma, b, x, t=1.0, dtau=0.05, A=0.5, cg_tol=1e-1
     rc = L.hh_solve_noalloc(ctypes.byref(lat), ctypes.byref(p), _ptr(sigma), _ptr(b), _ptr(x),
                             _stream_handle(stream), ctypes.byref(inf) if info else None)
     return rc, (inf.as_dict() if info else None)
+
+
+def make_params(t=1.0, dtau=0.05, A=0.5, precision=HH_FP64, cg_tol=1e-10, cg_maxit=1000000,
+                reliable_delta=0.1, seed=0, n_pf=2, chain_id=0):
+    L = load()
+    p = hh_params()
+    L.hh_default_params(ctypes.byref(p))
+    p.t, p.dtau, p.A = t, dtau, A
+    p.precision = {"fp64": HH_FP64, "mixed": HH_MIXED}.get(precision, precision)
+    p.cg_tol, p.cg_maxit, p.reliable_delta = cg_tol, cg_maxit, reliable_delta
+    p.seed, p.n_pf, p.chain_id = seed, n_pf, chain_id
+    return p
+
+
+def make_request(kind, d, nx, ntau, sigma=None, b=None, out=None, n_md=0, dt=0.0, traj_index=0, **prm):
+    """An hh_request.  sigma, b: host float64 NumPy arrays (copied at submit);
+    out: host float64 NumPy array written on completion (kept alive by the caller)."""
+    r = hh_request()
+    r.kind = kind
+    r.lat = hh_lattice(d, nx, ntau)
+    r.prm = make_params(**prm)
+    r.sigma = sigma.ctypes.data if sigma is not None else None
+    r.b = b.ctypes.data if b is not None else None
+    r.out = out.ctypes.data if out is not None else None
+    r.n_md, r.dt, r.traj_index = n_md, dt, traj_index
+    return r
+
+
+class Batch:
+    """Batched multi-chain engine / serving loop (hh_batch_*)."""
+
+    def __init__(self, max_slots=64, hbm_budget_bytes=4 << 30, chunk_iters=32, tile_sites=4096,
+                 max_active_sites=0, stream=None):
+        L = load()
+        self._lib = L
+        cfg = hh_batch_config()
+        L.hh_batch_default_config(ctypes.byref(cfg))
+        cfg.max_slots, cfg.hbm_budget_bytes = max_slots, hbm_budget_bytes
+        cfg.chunk_iters, cfg.tile_sites, cfg.max_active_sites = chunk_iters, tile_sites, max_active_sites
+        self.config = cfg
+        h = ctypes.c_void_p()
+        check(L.hh_batch_create(ctypes.byref(h), ctypes.byref(cfg), _stream_handle(stream)), "hh_batch_create")
+        self._h = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hh_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, req, keep=None, allow=()):
+        t = ctypes.c_uint64()
+        rc = self._lib.hh_batch_submit(self._h, ctypes.byref(req), ctypes.byref(t))
+        check(rc, "hh_batch_submit", allow)
+        if rc == HH_OK and keep is not None:
+            self._keep[t.value] = keep
+        return rc, t.value
+
+    def step(self):
+        n = ctypes.c_int()
+        rc = self._lib.hh_batch_step(self._h, ctypes.byref(n))
+        check(rc, "hh_batch_step")
+        return n.value
+
+    def start(self):
+        check(self._lib.hh_batch_start(self._h), "hh_batch_start")
+
+    def stop(self):
+        check(self._lib.hh_batch_stop(self._h), "hh_batch_stop")
+
+    def poll(self, max_results=256):
+        arr = (hh_result * max_results)()
+        n = ctypes.c_int()
+        check(self._lib.hh_batch_poll(self._h, arr, max_results, ctypes.byref(n)), "hh_batch_poll")
+        out = [arr[j].as_dict() for j in range(n.value)]
+        for r in out:
+            self._keep.pop(r["ticket"], None)
+        return out
+
+    def pending(self):
+        q, a = ctypes.c_int(), ctypes.c_int()
+        check(self._lib.hh_batch_pending(self._h, ctypes.byref(q), ctypes.byref(a)), "hh_batch_pending")
+        return q.value, a.value
+
+    def run_until_idle(self, max_steps=10 ** 7):
+        results = []
+        for _ in range(max_steps):
+            busy = self.step()
+            results += self.poll()
+            if busy == 0:
+                break
+        return results + self.poll()
+
+
+def autotune(requests, hbm_budget_bytes=4 << 30, rounds=8, cache_path=None, stream=None):
+    """hh_batch_autotune on copies of the given solve requests; returns the
+    chosen configuration as a dict."""
+    L = load()
+    arr = (hh_request * len(requests))(*requests)
+    best = hh_batch_config()
+    check(L.hh_batch_autotune(arr, len(requests), hbm_budget_bytes, rounds,
+                              cache_path.encode() if cache_path else None, _stream_handle(stream),
+                              ctypes.byref(best)), "hh_batch_autotune")
+    return best.as_dict()

@@ -207,9 +207,11 @@ int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
             T.sys = a;
             T.begin = s0;
             T.end = s0 + chunk < c->N ? s0 + chunk : c->N;
+            T.part = (int)tiles.size();
             tiles.push_back(T);
         }
         Y.ntiles = (int)tiles.size() - Y.tile0;
+        Y.part0 = Y.tile0;
         Y.owner = Y.tile0 % grid;
         Y.precision = c->prm.precision;
         Y.tol2 = c->prm.cg_tol * c->prm.cg_tol;

@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, 1) engine_kernel(EngLaunch L)
                     const int pm = s_state.mode;
                     double rr = 0.0;
                     if (pm == MODE_INIT || pm == MODE_CG || pm == MODE_RU)
-                        rr = sum_partials(L.part_rr, Y.tile0, Y.ntiles, &s_val);
+                        rr = sum_partials(L.part_rr, Y.part0, Y.ntiles, &s_val);
                     if (threadIdx.x == 0) {
                         const EngState P = s_state;
                         const EngState S = decide(Y, P, rr);
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, 1) engine_kernel(EngLaunch L)
                 double v = run_slot<2>(Y, c, T);
                 if (c.mode == MODE_CG) {
                     double tot = block_sum(v, s_red);
-                    if (threadIdx.x == 0) L.part_tt[tile] = tot;
+                    if (threadIdx.x == 0) L.part_tt[T.part] = tot;
                 }
             }
         }
@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, 1) engine_kernel(EngLaunch L)
                     }
                     __syncthreads();
                     if (s_ctl.mode == MODE_CG) {
-                        double tt = sum_partials(L.part_tt, Y.tile0, Y.ntiles, &s_val);
+                        double tt = sum_partials(L.part_tt, Y.part0, Y.ntiles, &s_val);
                         if (threadIdx.x == 0) s_ctl.alpha = s_state.rr_alpha / tt;
                     }
                     __syncthreads();
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, 1) engine_kernel(EngLaunch L)
                 double v = run_slot<3>(Y, c, T);
                 if (c.mode == MODE_CG || c.mode == MODE_RU || c.mode == MODE_INIT) {
                     double tot = block_sum(v, s_red);
-                    if (threadIdx.x == 0) L.part_rr[tile] = tot;
+                    if (threadIdx.x == 0) L.part_rr[T.part] = tot;
                 }
             }
         }
@@ -489,6 +489,11 @@ cudaError_t engine_launch(const EngLaunch &L, int grid, int block, cudaStream_t 
     void *args[] = {(void *)&arg};
     return cudaLaunchCooperativeKernel((const void *)engine_kernel, dim3(grid), dim3(block), args, 0,
                                        stream);
+}
+
+const void *engine_kernel_fn()
+{
+    return (const void *)engine_kernel;
 }
 
 int engine_max_grid(int block)

@@ -41,6 +41,9 @@ struct EngSystem {
     double *r, *p, *t;                // FP64 CG vectors (t also FP64 scratch for RU)
     float *r32, *p32, *t32, *x32;     // FP32 inner vectors (mixed)
     int tile0, ntiles;                // tiles [tile0, tile0 + ntiles) of the global tile list
+    int part0;                        // partial sums of its tiles: [part0, part0 + ntiles),
+                                      // stable for the system's lifetime even when the
+                                      // tile list is rebuilt between launches
     int owner;                        // block that writes this system's state
     int precision;                    // PREC_FP64 or PREC_MIXED
     double tol2;                      // cg_tol^2
@@ -87,6 +90,7 @@ struct EngState {
 struct EngTile {
     int sys;
     int begin, end;     // sites [begin, end) of the system
+    int part;           // index of this tile's partial sums (part0 of its system + j)
 };
 
 struct EngLaunch {
@@ -104,6 +108,9 @@ struct EngLaunch {
 // The barrier counter ctl->count must be zero when the launch starts.
 // Returns a cudaError_t from the launch.
 cudaError_t engine_launch(const EngLaunch &L, int grid, int block, cudaStream_t stream);
+
+// The engine kernel, for CUDA-graph kernel nodes.
+const void *engine_kernel_fn();
 
 // Largest co-resident grid for the engine kernel at 'block' threads.
 int engine_max_grid(int block);

@@ -89,6 +89,7 @@ __global__ void k_noalloc_plan(unsigned char *base, Geo g, double h, const doubl
         T.sys = 0;
         T.begin = j * chunk;
         T.end = (j + 1) * chunk < g.N ? (j + 1) * chunk : g.N;
+        T.part = j;
         tiles[j] = T;
     }
     if (threadIdx.x == 0) {
@@ -105,6 +106,7 @@ __global__ void k_noalloc_plan(unsigned char *base, Geo g, double h, const doubl
         Y.t = (double *)(base + kOffT);
         Y.tile0 = 0;
         Y.ntiles = ntiles;
+        Y.part0 = 0;
         Y.owner = 0;
         Y.precision = PREC_FP64;
         Y.tol2 = tol * tol;
