@@ -13,15 +13,20 @@ Q = M^T M once per right-hand side), with sigma resident on the device when a
 step's timed region starts.  e2e: the same count over wall time of the public
 calls hh_set_field(host) -> hh_trajectory -> hh_get_field(host) per step.
 
-Two further modes measure parts of the path (they print the same JSON line):
+Further modes measure parts of the path (they print the same JSON line):
   --mode solve : a step is one CG solve of Q x = b for two right-hand sides
                  (value in solves/s), to compare FP64 with mixed precision;
   --mode apply : a step is one M^T M apply with L2 flushed before it (value in
-                 applies/s), the HBM roofline of the stencil.
+                 applies/s), the HBM roofline of the stencil;
+  --mode batch : a step solves two right-hand sides for each of 64 d=3 chains of
+                 uneven volume in the batched engine (autotuned), in solves/s;
+  --mode serve : a Poisson stream of solve and trajectory requests at each rate
+                 of --rates, served by the continuous-batching worker; reports
+                 p50/p99 latency and solves/s per rate.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                        [--workload c0|c1|c2] [--precision fp64|mixed]
-                       [--mode trajectory|solve|apply] [--cg-maxit M]
+                       [--mode trajectory|solve|apply|batch|serve] [--cg-maxit M]
 """
 import argparse
 import json
@@ -324,6 +329,142 @@ def run_part(args, wl, world, rank, local, dev, stream):
     ctx.close()
 
 
+def _batch_requests(B, chains, precision, rank, keep):
+    from paper_1007_3432_gb300.binding import HH_REQ_SOLVE
+    reqs = []
+    for c in chains:
+        n = c.nsites
+        sigma = workloads.sigma_field(n, seed=workloads.BATCH_SEED, chain=c.chain + 1000 * rank)
+        b = np.stack([workloads.source(n, seed=workloads.BATCH_SEED, chain=c.chain, rhs=a) for a in range(2)])
+        keep.append((sigma, b))
+        reqs.append(B.make_request(HH_REQ_SOLVE, 3, c.nx, c.ntau, sigma=sigma, b=b, out=None,
+                                   precision=precision, n_pf=2))
+    return reqs
+
+
+def run_batch(args, world, rank, local, dev, stream):
+    """64 independent d=3 chains of uneven volume; one step solves both
+    right-hand sides of every chain in the batched engine.  The engine
+    configuration comes from the library's autotuner on this request mix."""
+    import torch
+    from paper_1007_3432_gb300 import binding as B
+    chains = workloads.batch_chains(64)
+    sites = sum(c.nsites for c in chains)
+    keep = []
+    reqs = _batch_requests(B, chains, args.precision, rank, keep)
+    budget = int(min(args.budget_gb, 120.0) * (1 << 30))
+    tuned = B.autotune(reqs, hbm_budget_bytes=budget, rounds=6,
+                       cache_path=os.path.join(ROOT, "paper_1007_3432_gb300", "lib", "autotune.jsonl"),
+                       stream=stream)
+    batch = B.Batch(max_slots=64, hbm_budget_bytes=budget, chunk_iters=tuned["chunk_iters"],
+                    tile_sites=tuned["tile_sites"], max_active_sites=tuned["max_active_sites"], stream=stream)
+
+    def one():
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for r in reqs:
+            batch.submit(r)
+        res = batch.run_until_idle()
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t0, res
+
+    for _ in range(args.warmup):
+        one()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, allres = [], []
+    for _ in range(args.steps):
+        t, res = one()
+        times.append(t)
+        allres += res
+    clk = clocks.stop()
+    batch.close()
+    t_tot = max_over_ranks(world, sum(times))
+    solves = sum_over_ranks(world, float(sum(r["n_solves"] for r in allres)))
+    its = sum(r["cg_iterations"] for r in allres)
+    bad = sum(1 for r in allres if r["status"] != 0 or r["max_true_relres"] > 1e-10)
+    peaks, src = measured_peaks()
+    per_site = bytes_per_site("cg", args.precision)
+    size_of = {j: c.nsites for j, c in enumerate(chains)}
+    site_its = sum(r["cg_iterations"] * size_of[(r["ticket"] - 1) % len(chains)] for r in allres)
+    ach = site_its * per_site / sum(times) / 1e9
+    line = {"metric": METRIC, "value": solves / t_tot, "unit": "CG solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": "batch64_d3", "chains": len(chains), "sites_total": sites,
+                       "nx_choices": list(workloads.BATCH_NX), "ntau_choices": list(workloads.BATCH_NTAU),
+                       "seed": workloads.BATCH_SEED, "precision": args.precision, "n_rhs": 2,
+                       "autotuned": tuned, "mode": "batch", "parallelism": "replicas%d" % world},
+            "cg_iterations_per_solve": its / max(1, solves), "failed_solves": bad,
+            "e2e": {"value": solves / t_tot, "unit": "CG solves/s",
+                    "h2d_bytes_per_step": int(sum(3 * 8 * c.nsites for c in chains)), "d2h_bytes_per_step": 0},
+            "gpu_launches": None, "clocks": clk,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                         "kernel": "engine_kernel (batched, %s)" % args.precision,
+                         "note": "algorithmic CG bytes over the whole step wall time"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serve(args, world, rank, local, dev, stream):
+    """Poisson arrivals of solve and trajectory requests, served by the
+    continuous-batching worker thread; p50/p99 latency and solves/s per rate."""
+    import torch
+    from paper_1007_3432_gb300 import binding as B
+    from paper_1007_3432_gb300.binding import HH_REQ_SOLVE, HH_REQ_TRAJECTORY
+    budget = int(args.budget_gb * (1 << 30))
+    per_rate = []
+    for rate in [float(x) for x in args.rates.split(",")]:
+        reqs = workloads.poisson_requests(rate, args.requests, seed=workloads.SERVE_SEED + 17 * rank)
+        batch = B.Batch(max_slots=64, hbm_budget_bytes=budget, chunk_iters=32, tile_sites=4096, stream=stream)
+        batch.start()
+        keep, got = [], []
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for r in reqs:
+            while time.perf_counter() - t0 < r.arrival_s:
+                time.sleep(0.0002)
+            sigma = workloads.sigma_field(r.nsites, seed=r.seed)
+            if r.kind == "solve":
+                req = B.make_request(HH_REQ_SOLVE, r.d, r.nx, r.ntau, sigma=sigma, precision="mixed",
+                                     seed=r.seed, n_pf=2, traj_index=r.rid)
+            else:
+                req = B.make_request(HH_REQ_TRAJECTORY, r.d, r.nx, r.ntau, sigma=sigma, precision="mixed",
+                                     seed=r.seed, n_pf=2, n_md=args.serve_n_md, dt=1.0 / args.serve_n_md,
+                                     traj_index=r.rid)
+            keep.append(sigma)
+            batch.submit(req)
+            got += batch.poll()
+        deadline = time.perf_counter() + 600
+        while len(got) < len(reqs) and time.perf_counter() < deadline:
+            got += batch.poll()
+            time.sleep(0.001)
+        wall = time.perf_counter() - t0
+        batch.stop()
+        batch.close()
+        lat = np.array([g["latency_ms"] for g in got]) if got else np.array([np.nan])
+        per_rate.append({"rate_hz": rate, "requests": len(reqs), "completed": len(got),
+                         "failed": sum(1 for g in got if g["status"] != 0),
+                         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                         "solves_per_s": sum(g["n_solves"] for g in got) / wall,
+                         "requests_per_s": len(got) / wall, "wall_s": wall,
+                         "mean_queue_ms": float(np.mean([g["queue_ms"] for g in got])) if got else None})
+    best = max(per_rate, key=lambda d: d["solves_per_s"])
+    line = {"metric": METRIC, "value": best["solves_per_s"], "unit": "CG solves/s", "n_gpus": world,
+            "steps": len(per_rate), "warmup": 0, "ms_per_step": 1000.0 * sum(d["wall_s"] for d in per_rate) / len(per_rate),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "serve_poisson", "seed": workloads.SERVE_SEED, "requests_per_rate": args.requests,
+                       "d1": {"nx": [64, 2048], "ntau": [64, 512]}, "d3": {"nx": [8, 24], "ntau": [40, 256]},
+                       "trajectory_n_md": args.serve_n_md, "hbm_budget_gb": args.budget_gb, "precision": "mixed",
+                       "mode": "serve", "parallelism": "replicas%d" % world},
+            "per_rate": per_rate, "e2e": None, "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,8 +476,12 @@ def main():
     ap.add_argument("--n-md", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--mode", default="trajectory", choices=["trajectory", "solve", "apply"])
+    ap.add_argument("--mode", default="trajectory", choices=["trajectory", "solve", "apply", "batch", "serve"])
     ap.add_argument("--cg-maxit", type=int, default=1000000)
+    ap.add_argument("--rates", default="10,100,1000")
+    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--serve-n-md", type=int, default=4)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.n_md is None:
@@ -356,6 +501,10 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    if args.mode == "batch":
+        return run_batch(args, world, rank, local, dev, stream)
+    if args.mode == "serve":
+        return run_serve(args, world, rank, local, dev, stream)
     if args.mode != "trajectory":
         return run_part(args, wl, world, rank, local, dev, stream)
     n = wl.nsites

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/hubhmc.h"
+#include "hh_apply.cuh"
 #include "hh_engine.cuh"
 #include "hh_kernels.cuh"
 
@@ -135,6 +136,8 @@ struct hh_ctx {
     double *d_energy_part;
     double *d_energy_out;   // [0] S or H scratch
     void *h_pinned;         // host readback buffer
+    int *d_apply_err;       // set by a fused apply whose bounded wait ran out
+    int nsm;
 };
 
 namespace {
@@ -164,6 +167,7 @@ void free_ctx(hh_ctx *c)
         if (p) cudaFree(p);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->d_totals) cudaFree(c->d_totals);
+    if (c->d_apply_err) cudaFree(c->d_apply_err);
     if (c->ev) {
         for (int i = 0; i < c->ev_cap; ++i)
             if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -402,6 +406,7 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
     if (e == cudaSuccess) e = dalloc(&c->d_stats, 1);
     if (e == cudaSuccess) e = dalloc(&c->d_sc, 1);
     if (e == cudaSuccess) e = dalloc(&c->d_totals, 1);
+    if (e == cudaSuccess) e = dalloc(&c->d_apply_err, 1);
     if (e == cudaSuccess) e = dalloc(&c->d_energy_part, (size_t)energy_blocks(c->N));
     if (e == cudaSuccess) e = dalloc(&c->d_energy_out, 4);
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_pinned, 4096);
@@ -414,6 +419,12 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_ctl, 0, sizeof(BarrierCtl), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_sc, 0, sizeof(HmcScalars), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_totals, 0, sizeof(EngTotals), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_apply_err, 0, sizeof(int), c->stream);
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
     if (e == cudaSuccess) e = launch_links(c->geo, p->A, c->sigma, c->L64, c->L32, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -481,28 +492,55 @@ int hh_apply(hh_ctx *c, int op, const void *x, void *y, int dtype)
     if (!c || !x || !y || x == y) return HH_EINVAL;
     if (op != HH_OP_M && op != HH_OP_MT && op != HH_OP_MTM) return HH_EINVAL;
     const double h = c->prm.t * c->prm.dtau;
+    // Vector sweeps need 16-byte aligned x and y; the scalar kernels take any.
+    const bool vec = aligned16(x) && aligned16(y);
+    int launches = 0;
     if (dtype == HH_DTYPE_F64) {
         const double *xd = (const double *)x;
         double *yd = (double *)y;
         if (op == HH_OP_MTM) {
-            HH_TRY(launch_apply_f64(c->geo, 0, h, c->L64, xd, c->tmp, c->stream));
-            HH_TRY(launch_apply_f64(c->geo, 1, h, c->L64, c->tmp, yd, c->stream));
+            if (vec) {
+                HH_TRY(launch_sweep_f64(c->geo, false, h, c->L64, xd, c->tmp, c->stream));
+                HH_TRY(launch_sweep_f64(c->geo, true, h, c->L64, c->tmp, yd, c->stream));
+            } else {
+                HH_TRY(launch_apply_f64(c->geo, 0, h, c->L64, xd, c->tmp, c->stream));
+                HH_TRY(launch_apply_f64(c->geo, 1, h, c->L64, c->tmp, yd, c->stream));
+            }
+            launches = 2;
         } else {
-            HH_TRY(launch_apply_f64(c->geo, op, h, c->L64, xd, yd, c->stream));
+            if (vec)
+                HH_TRY(launch_sweep_f64(c->geo, op == HH_OP_MT, h, c->L64, xd, yd, c->stream));
+            else
+                HH_TRY(launch_apply_f64(c->geo, op, h, c->L64, xd, yd, c->stream));
+            launches = 1;
         }
     } else if (dtype == HH_DTYPE_F32) {
         const float *xf = (const float *)x;
         float *yf = (float *)y;
         if (op == HH_OP_MTM) {
-            HH_TRY(launch_apply_f32(c->geo, 0, (float)h, c->L32, xf, c->tmp32a, c->stream));
-            HH_TRY(launch_apply_f32(c->geo, 1, (float)h, c->L32, c->tmp32a, yf, c->stream));
+            if (vec && fused_mtm_ok(c->geo, c->L32, xf, yf)) {
+                HH_TRY(launch_mtm_fused_f32(c->geo, (float)h, c->L32, xf, yf, c->d_apply_err, c->nsm, c->stream));
+                launches = 1;
+            } else if (vec) {
+                HH_TRY(launch_sweep_f32(c->geo, false, (float)h, c->L32, xf, c->tmp32a, c->stream));
+                HH_TRY(launch_sweep_f32(c->geo, true, (float)h, c->L32, c->tmp32a, yf, c->stream));
+                launches = 2;
+            } else {
+                HH_TRY(launch_apply_f32(c->geo, 0, (float)h, c->L32, xf, c->tmp32a, c->stream));
+                HH_TRY(launch_apply_f32(c->geo, 1, (float)h, c->L32, c->tmp32a, yf, c->stream));
+                launches = 2;
+            }
         } else {
-            HH_TRY(launch_apply_f32(c->geo, op, (float)h, c->L32, xf, yf, c->stream));
+            if (vec)
+                HH_TRY(launch_sweep_f32(c->geo, op == HH_OP_MT, (float)h, c->L32, xf, yf, c->stream));
+            else
+                HH_TRY(launch_apply_f32(c->geo, op, (float)h, c->L32, xf, yf, c->stream));
+            launches = 1;
         }
     } else {
         return HH_EINVAL;
     }
-    c->n_launch += (op == HH_OP_MTM) ? 2 : 1;
+    c->n_launch += launches;
     return HH_OK;
 }
 
@@ -702,6 +740,8 @@ int hh_counters_get(hh_ctx *c, hh_counters *out)
         HH_TRY(cudaEventElapsedTime(&m, c->ev[i], c->ev[i + 1]));
         ms += m;
     }
+    int aerr = 0;
+    HH_TRY(cudaMemcpy(&aerr, c->d_apply_err, sizeof(int), cudaMemcpyDeviceToHost));
     out->kernel_launches = c->n_launch;
     out->engine_launches = c->n_engine;
     out->engine_ms = ms;
@@ -710,7 +750,7 @@ int hh_counters_get(hh_ctx *c, hh_counters *out)
     out->solves = t.solves;
     out->fp64_steps = t.fp64_steps;
     out->sites = c->N;
-    return HH_OK;
+    return aerr ? aerr : HH_OK;
 }
 
 }  // extern "C"

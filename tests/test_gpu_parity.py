@@ -73,7 +73,11 @@ def test_apply_fp64_per_element(hh, d, nx, ntau, op):
     assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
 
 
-@pytest.mark.parametrize("d,nx,ntau", [(1, 32, 64), (3, 8, 12), (3, 5, 7)])
+FP32_SHAPES = [(1, 32, 64), (3, 8, 12), (3, 5, 7), (3, 4, 3), (3, 6, 5), (3, 12, 9), (3, 32, 10),
+               (3, 10, 40)]
+
+
+@pytest.mark.parametrize("d,nx,ntau", FP32_SHAPES)
 @pytest.mark.parametrize("op", ["M", "MT", "MTM"])
 def test_apply_fp32_per_element(hh, d, nx, ntau, op):
     lat = oracle.lattice(d, nx, ntau)
@@ -90,6 +94,27 @@ def test_apply_fp32_per_element(hh, d, nx, ntau, op):
         y = torch.empty(n, dtype=torch.float32, device="cuda")
         ctx.apply(code, dev(x), y)
         got = y.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
+
+
+def test_fused_mtm_fp32_full_size_lattice(hh):
+    """Q x on the d=3, 32^3 x 128 lattice (4.2M sites) in the launch
+    configuration the benchmark times, every element against the oracle."""
+    wl = workloads.C2
+    lat = oracle.lattice(wl.d, wl.nx, wl.ntau)
+    n = wl.nsites
+    sigma = workloads.sigma_field(n, seed=wl.seed)
+    x = workloads.source(n, seed=wl.seed).astype(np.float32)
+    L = oracle.links(lat, A, sigma)
+    x64 = x.astype(np.float64)
+    ref = oracle.apply_MTM(lat, H, L, x64)
+    bound = 2e-6 * magnitude(lat, "MTM", L, x64)
+    with hh.Context(wl.d, wl.nx, wl.ntau) as ctx:
+        ctx.set_field(dev(sigma))
+        y = torch.empty(n, dtype=torch.float32, device="cuda")
+        ctx.apply(hh.HH_OP_MTM, dev(x), y)
+        got = y.cpu().numpy().astype(np.float64)
+        assert ctx.counters()["sites"] == n      # also checks the fused kernel's wait flag
     assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
 
 
