@@ -228,7 +228,22 @@ def config_of(args, wl):
             "t": workloads.T_HOP, "dtau": workloads.DTAU, "A": workloads.A_HS, "seed": wl.seed,
             "n_md": args.n_md, "dt": 1.0 / args.n_md, "n_pf": 2, "cg_tol": 1e-10,
             "precision": args.precision, "step": "one HMC trajectory",
-            "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas%d" % args.gpus}
+            "l2": "flushed between steps (512 MiB write, then 512 MiB read)", "parallelism": "replicas%d" % args.gpus}
+
+
+class L2Flush:
+    """Evicts L2 between timed steps: writes a buffer larger than L2 (129 MB on
+    GB300), then reads another one, so that the lines left in L2 are clean and
+    the next step does not pay the write-back of the flush."""
+
+    def __init__(self, dev, mbytes=512):
+        import torch
+        self.w = torch.empty(mbytes * (1 << 20) // 4, dtype=torch.float32, device=dev)
+        self.r = torch.ones(mbytes * (1 << 20) // 4, dtype=torch.float32, device=dev)
+
+    def __call__(self, v=1.0):
+        self.w.fill_(v)
+        self.r.sum()
 
 
 def run_part(args, wl, world, rank, local, dev, stream):
@@ -242,7 +257,7 @@ def run_part(args, wl, world, rank, local, dev, stream):
     ctx = Context(wl.d, wl.nx, wl.ntau, seed=wl.seed, chain_id=rank, precision=args.precision,
                   cg_maxit=args.cg_maxit, stream=stream)
     ctx.set_field(torch.from_numpy(workloads.sigma_field(n, seed=wl.seed, chain=rank)).to(dev))
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     if args.mode == "solve":
         b_h = np.stack([workloads.source(n, seed=wl.seed, chain=rank, rhs=a) for a in range(2)])
         b = torch.from_numpy(b_h).to(dev)
@@ -255,7 +270,7 @@ def run_part(args, wl, world, rank, local, dev, stream):
         ys = torch.empty_like(xs)
 
     def one(timed):
-        flush.fill_(1.0)
+        flush()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         w0 = time.perf_counter()
@@ -450,7 +465,12 @@ def run_serve(args, world, rank, local, dev, stream):
                          "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                          "solves_per_s": sum(g["n_solves"] for g in got) / wall,
                          "requests_per_s": len(got) / wall, "wall_s": wall,
-                         "mean_queue_ms": float(np.mean([g["queue_ms"] for g in got])) if got else None})
+                         "mean_queue_ms": float(np.mean([g["queue_ms"] for g in got])) if got else None,
+                         "status_counts": {str(k): int(v) for k, v in zip(*np.unique([g["status"] for g in got],
+                                                                                  return_counts=True))} if got else {},
+                         "requests_detail": [[reqs[g["ticket"] - 1].kind[0], reqs[g["ticket"] - 1].d,
+                                              reqs[g["ticket"] - 1].nx, reqs[g["ticket"] - 1].ntau, g["status"],
+                                              round(g["latency_ms"], 1), g["cg_iterations"]] for g in got]})
     best = max(per_rate, key=lambda d: d["solves_per_s"])
     line = {"metric": METRIC, "value": best["solves_per_s"], "unit": "CG solves/s", "n_gpus": world,
             "steps": len(per_rate), "warmup": 0, "ms_per_step": 1000.0 * sum(d["wall_s"] for d in per_rate) / len(per_rate),
@@ -511,11 +531,11 @@ def main():
     sigma_h = workloads.sigma_field(n, seed=wl.seed, chain=rank)
     ctx = Context(wl.d, wl.nx, wl.ntau, seed=wl.seed, n_pf=2, chain_id=rank, precision=args.precision,
                   cg_maxit=args.cg_maxit, stream=stream)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     dt = 1.0 / args.n_md
 
     def step(traj, timed):
-        flush.fill_(float(traj))
+        flush(float(traj))
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)

@@ -104,6 +104,12 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
         : "memory");
 }
 
+// Bulk prefetch of [src, src + bytes) into L2 (16-byte aligned, multiple of 16).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 struct FusedCfg {
     Geo g;
     float h;
@@ -135,6 +141,22 @@ __device__ __forceinline__ unsigned load_planes(const FusedCfg &c, const float *
     return bytes;
 }
 
+// Planes [z_first, z_first + count) of slice tau into L2, one request per run.
+__device__ __forceinline__ void prefetch_planes(const FusedCfg &c, const float *src, int tau, int z_first,
+                                                int count)
+{
+    const int nx = c.g.nx;
+    int z = ((z_first % nx) + nx) % nx;
+    int done = 0;
+    while (done < count) {
+        int run = count - done;
+        if (z + run > nx) run = nx - z;
+        bulk_prefetch_l2(src + (size_t)tau * c.g.V + (size_t)z * c.P, (unsigned)(run * c.P * sizeof(float)));
+        done += run;
+        z = 0;
+    }
+}
+
 constexpr long long kSpinLimit = 1LL << 26;
 
 // Bounded wait on an mbarrier phase; on timeout sets *err and returns false.
@@ -150,31 +172,101 @@ __device__ __forceinline__ bool wait_phase(uint64_t *bar, unsigned parity, int *
     return true;
 }
 
-__global__ void __launch_bounds__(512, 1) k_mtm_fused_d3(const FusedCfg c, const float *__restrict__ L,
+// In-plane geometry of one thread's float4 group: 4 consecutive x sites at
+// in-plane offset s (x0 = s mod Nx is a multiple of 4), the single sites just
+// before and after the group along x, and the groups one row up / down in y.
+struct PlaneGroup {
+    int s, xm, xp, yp, ym;
+};
+
+__device__ __forceinline__ PlaneGroup plane_group(int g, int nx)
+{
+    PlaneGroup q;
+    const int s = 4 * g;
+    const int yy = s / nx, x0 = s - yy * nx;
+    q.s = s;
+    q.xm = yy * nx + (x0 == 0 ? nx - 1 : x0 - 1);
+    q.xp = yy * nx + (x0 + 4 == nx ? 0 : x0 + 4);
+    q.yp = (yy + 1 == nx ? 0 : yy + 1) * nx + x0;
+    q.ym = (yy == 0 ? nx - 1 : yy - 1) * nx + x0;
+    return q;
+}
+
+__device__ __forceinline__ float4 ld4(const float *p)
+{
+    return *reinterpret_cast<const float4 *>(p);
+}
+
+// One plane of the stencil for a float4 group: out = c - h hop(c) + l * o,
+// with the z neighbours 'below' and 'above' already loaded.
+// The x neighbours outside the group come from the adjacent lanes' groups
+// when a row of groups lies inside one warp (shfl), else from shared memory.
+__device__ __forceinline__ void x_halo(const float *c, const PlaneGroup &q, const float4 &self, bool shfl,
+                                       int src_m, int src_p, float &xm, float &xp)
+{
+    if (shfl) {
+        xm = __shfl_sync(0xffffffffu, self.w, src_m);
+        xp = __shfl_sync(0xffffffffu, self.x, src_p);
+    } else {
+        xm = c[q.xm];
+        xp = c[q.xp];
+    }
+}
+
+__device__ __forceinline__ float4 plane_stencil(const float *c, const PlaneGroup &q, float4 self, float4 below,
+                                                float4 above, float4 l, float4 o, float h, float xm, float xp)
+{
+    const float4 yp = ld4(c + q.yp), ym = ld4(c + q.ym);
+    float4 r;
+    r.x = fmaf(l.x, o.x, fmaf(-h, (xm + self.y) + (yp.x + ym.x) + (above.x + below.x), self.x));
+    r.y = fmaf(l.y, o.y, fmaf(-h, (self.x + self.z) + (yp.y + ym.y) + (above.y + below.y), self.y));
+    r.z = fmaf(l.z, o.z, fmaf(-h, (self.y + self.w) + (yp.z + ym.z) + (above.z + below.z), self.z));
+    r.w = fmaf(l.w, o.w, fmaf(-h, (self.z + xp) + (yp.w + ym.w) + (above.w + below.w), self.w));
+    return r;
+}
+
+constexpr int kFusedThreads = 512;
+
+template <int TZ>
+__global__ void __launch_bounds__(kFusedThreads, 1) k_mtm_fused_d3(const FusedCfg c, const float *__restrict__ L,
                                                          const float *__restrict__ x, float *__restrict__ y,
                                                          int *err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bars[2];
-    const int P = c.P, tz = c.tz, nx = c.g.nx, ntau = c.g.ntau;
-    const int xpl = tz + 4, tpl = tz + 2;  // planes held for x and for t / L
+    constexpr int XPL = TZ + 4, TPL = TZ + 2;  // planes held for x and for t / L
+    const int P = c.P, nx = c.g.nx, ntau = c.g.ntau, V = c.g.V;
     float *XB = (float *)smem_raw;                     // 3 slices of x
-    float *LB = XB + 3 * (size_t)xpl * P;              // 2 slices of L
-    float *TB = LB + 2 * (size_t)tpl * P;              // 2 slices of t
+    float *LB = XB + 3 * XPL * P;                      // 2 slices of L
+    float *TB = LB + 2 * TPL * P;                      // 2 slices of t
 
     const int slab = blockIdx.x % c.nslab;
     const int chunk = blockIdx.x / c.nslab;
-    const int z0 = slab * tz;
+    const int z0 = slab * TZ;
     const int tau0 = chunk * c.tc;
     int tau1 = tau0 + c.tc;
     if (tau1 > ntau) tau1 = ntau;
     if (tau0 >= tau1) return;
     const float h = c.h;
 
-    // x slices live in XB slot (tau - tau0 + 1) % 3; L and t slices in slot tau % 2.
-    auto xslot = [&](int tau) { return XB + (size_t)(((tau - tau0 + 1) % 3 + 3) % 3) * xpl * P; };
-    auto lslot = [&](int tau) { return LB + (size_t)(((tau % 2) + 2) % 2) * tpl * P; };
-    auto tslot = [&](int tau) { return TB + (size_t)(((tau % 2) + 2) % 2) * tpl * P; };
+    // Thread -> (float4 group in the plane, range of planes).
+    const int G = P / 4;
+    const int R = (int)blockDim.x / G > 0 ? (int)blockDim.x / G : 1;
+    const int g = threadIdx.x % G, r = threadIdx.x / G;
+    const bool worker = r < R && (int)threadIdx.x < R * G;
+    const PlaneGroup q = plane_group(g, nx);
+    const int t_per = (TPL + R - 1) / R, t_lo = r * t_per, t_hi = min(TPL, t_lo + t_per);
+    const int c_per = (TZ + R - 1) / R, c_lo = r * c_per, c_hi = min(TZ, c_lo + c_per);
+    // Shuffles for the x halo when the groups of a row are consecutive lanes
+    // of one warp and every lane of the warp is a worker on the same planes.
+    const int gpr = nx / 4, lane = threadIdx.x & 31, j = lane % gpr;
+    const bool shfl = (32 % gpr == 0) && (G % 32 == 0) && (R * G == (int)blockDim.x);
+    const int src_m = (j == 0) ? lane + gpr - 1 : lane - 1;
+    const int src_p = (j == gpr - 1) ? lane - gpr + 1 : lane + 1;
+
+    auto xslot = [&](int tau) { return XB + (((tau - tau0 + 1) % 3 + 3) % 3) * XPL * P; };
+    auto lslot = [&](int tau) { return LB + (((tau % 2) + 2) % 2) * TPL * P; };
+    auto tslot = [&](int tau) { return TB + (((tau % 2) + 2) % 2) * TPL * P; };
     auto wrap_tau = [&](int tau) { return ((tau % ntau) + ntau) % ntau; };
 
     if (threadIdx.x == 0) {
@@ -187,42 +279,39 @@ __global__ void __launch_bounds__(512, 1) k_mtm_fused_d3(const FusedCfg c, const
 
     // Stage 0: x(tau0-1), x(tau0), L(tau0-1).  Stage 1: x(tau0+1), L(tau0).
     if (threadIdx.x == 0) {
-        unsigned bytes = (unsigned)(2 * xpl + tpl) * P * sizeof(float);
+        unsigned bytes = (unsigned)(2 * XPL + TPL) * P * sizeof(float);
         mbar_expect_tx(&bars[0], bytes);
-        load_planes(c, x, wrap_tau(tau0 - 1), z0 - 2, xpl, xslot(tau0 - 1), &bars[0]);
-        load_planes(c, x, wrap_tau(tau0), z0 - 2, xpl, xslot(tau0), &bars[0]);
-        load_planes(c, L, wrap_tau(tau0 - 1), z0 - 1, tpl, lslot(tau0 - 1), &bars[0]);
-        bytes = (unsigned)(xpl + tpl) * P * sizeof(float);
+        load_planes(c, x, wrap_tau(tau0 - 1), z0 - 2, XPL, xslot(tau0 - 1), &bars[0]);
+        load_planes(c, x, wrap_tau(tau0), z0 - 2, XPL, xslot(tau0), &bars[0]);
+        load_planes(c, L, wrap_tau(tau0 - 1), z0 - 1, TPL, lslot(tau0 - 1), &bars[0]);
+        bytes = (unsigned)(XPL + TPL) * P * sizeof(float);
         mbar_expect_tx(&bars[1], bytes);
-        load_planes(c, x, wrap_tau(tau0 + 1), z0 - 2, xpl, xslot(tau0 + 1), &bars[1]);
-        load_planes(c, L, wrap_tau(tau0), z0 - 1, tpl, lslot(tau0), &bars[1]);
+        load_planes(c, x, wrap_tau(tau0 + 1), z0 - 2, XPL, xslot(tau0 + 1), &bars[1]);
+        load_planes(c, L, wrap_tau(tau0), z0 - 1, TPL, lslot(tau0), &bars[1]);
+        // Keep HBM streaming ahead of the shared-memory stages.
+        for (int a = 2; a <= 4 && tau0 + a - 1 < tau1; ++a) {
+            prefetch_planes(c, x, wrap_tau(tau0 + a), z0 - 2, XPL);
+            prefetch_planes(c, L, wrap_tau(tau0 + a - 1), z0 - 1, TPL);
+        }
     }
 
-    // t(tau) on the slab plus one halo plane from x(tau) (xs) and x(tau-1)
-    // (xp, site term) with L(tau-1) (ls).  A thread owns in-plane sites s and
-    // walks them through the planes, so the in-plane neighbour offsets are
-    // computed once per site and step.
+    // t(tau) on planes [t_lo, t_hi) of the slab plus one halo plane: x plane
+    // pz + 1 of xs is aligned with t plane pz; xp is x(tau-1), ls is L(tau-1).
     auto compute_t = [&](const float *xs, const float *xp, const float *ls, float *ts) {
-        for (int s = threadIdx.x; s < P; s += blockDim.x) {
-            const int yy = s / nx, xx = s - yy * nx;
-            const int oxp = yy * nx + (xx + 1 == nx ? 0 : xx + 1), oxm = yy * nx + (xx == 0 ? nx - 1 : xx - 1);
-            const int oyp = (yy + 1 == nx ? 0 : yy + 1) * nx + xx, oym = (yy == 0 ? nx - 1 : yy - 1) * nx + xx;
-            // x planes q = pz + 1 - 1 .. pz + 1 + 1 around t plane pz; keep a
-            // sliding window of the site value along z.
-            float below = xs[s], here = xs[(size_t)P + s];
-            for (int pz = 0; pz < tpl; ++pz) {
-                const float *xc = xs + (size_t)(pz + 1) * P;
-                const float above = xc[(size_t)P + s];
-                float hop = (xc[oxp] + xc[oxm]) + (xc[oyp] + xc[oym]) + (above + below);
-                float v = fmaf(-h, hop, here);
-                ts[(size_t)pz * P + s] = fmaf(ls[(size_t)pz * P + s], xp[(size_t)(pz + 1) * P + s], v);
-                below = here;
-                here = above;
-            }
+        if (!worker || t_lo >= t_hi) return;
+        float4 below = ld4(xs + t_lo * P + q.s), here = ld4(xs + (t_lo + 1) * P + q.s);
+        for (int pz = t_lo; pz < t_hi; ++pz) {
+            const float *xc = xs + (pz + 1) * P;
+            const float4 above = ld4(xc + P + q.s);
+            const float4 l = ld4(ls + pz * P + q.s), o = ld4(xp + (pz + 1) * P + q.s);
+            float hm, hp;
+            x_halo(xc, q, here, shfl, src_m, src_p, hm, hp);
+            *reinterpret_cast<float4 *>(ts + pz * P + q.s) = plane_stencil(xc, q, here, below, above, l, o, h, hm, hp);
+            below = here;
+            here = above;
         }
     };
 
-    int stage = 0;
     // Prologue: wait for stage 0, build t(tau0).
     if (!wait_phase(&bars[0], phase[0], err)) return;
     phase[0] ^= 1u;
@@ -230,36 +319,39 @@ __global__ void __launch_bounds__(512, 1) k_mtm_fused_d3(const FusedCfg c, const
     __syncthreads();
 
     for (int tau = tau0; tau < tau1; ++tau) {
-        stage = (tau - tau0 + 1) & 1;
+        const int stage = (tau - tau0 + 1) & 1;
         // Wait for x(tau+1) and L(tau).
         if (!wait_phase(&bars[stage], phase[stage], err)) return;
         phase[stage] ^= 1u;
         // Prefetch x(tau+2), L(tau+1) into the buffers freed by the last step.
         if (tau + 1 < tau1 && threadIdx.x == 0) {
             const int nb = stage ^ 1;
-            unsigned bytes = (unsigned)(xpl + tpl) * P * sizeof(float);
+            unsigned bytes = (unsigned)(XPL + TPL) * P * sizeof(float);
             mbar_expect_tx(&bars[nb], bytes);
-            load_planes(c, x, wrap_tau(tau + 2), z0 - 2, xpl, xslot(tau + 2), &bars[nb]);
-            load_planes(c, L, wrap_tau(tau + 1), z0 - 1, tpl, lslot(tau + 1), &bars[nb]);
+            load_planes(c, x, wrap_tau(tau + 2), z0 - 2, XPL, xslot(tau + 2), &bars[nb]);
+            load_planes(c, L, wrap_tau(tau + 1), z0 - 1, TPL, lslot(tau + 1), &bars[nb]);
+            if (tau + 4 < tau1) {
+                prefetch_planes(c, x, wrap_tau(tau + 5), z0 - 2, XPL);
+                prefetch_planes(c, L, wrap_tau(tau + 4), z0 - 1, TPL);
+            }
         }
         // t(tau+1) = (M x)(tau+1): site term x(tau) with L(tau).
         compute_t(xslot(tau + 1), xslot(tau), lslot(tau), tslot(tau + 1));
         __syncthreads();
-        // q(tau) = t(tau) - h hop(t(tau)) + L(tau) t(tau+1) on the core planes.
-        const float *t0 = tslot(tau), *t1 = tslot(tau + 1), *lc = lslot(tau);
-        float *yo = y + (size_t)wrap_tau(tau) * c.g.V + (size_t)z0 * P;
-        for (int s = threadIdx.x; s < P; s += blockDim.x) {
-            const int yy = s / nx, xx = s - yy * nx;
-            const int oxp = yy * nx + (xx + 1 == nx ? 0 : xx + 1), oxm = yy * nx + (xx == 0 ? nx - 1 : xx - 1);
-            const int oyp = (yy + 1 == nx ? 0 : yy + 1) * nx + xx, oym = (yy == 0 ? nx - 1 : yy - 1) * nx + xx;
-            float below = t0[s], here = t0[(size_t)P + s];
-            for (int pz = 0; pz < tz; ++pz) {
-                const float *tc = t0 + (size_t)(pz + 1) * P;
-                const float above = tc[(size_t)P + s];
-                float hop = (tc[oxp] + tc[oxm]) + (tc[oyp] + tc[oym]) + (above + below);
-                const size_t k = (size_t)(pz + 1) * P + s;
-                float v = fmaf(-h, hop, here);
-                yo[(size_t)pz * P + s] = fmaf(lc[k], t1[k], v);
+        // q(tau) = t(tau) - h hop(t(tau)) + L(tau) t(tau+1) on core planes [c_lo, c_hi).
+        if (worker && c_lo < c_hi) {
+            const float *t0 = tslot(tau), *t1 = tslot(tau + 1), *lc = lslot(tau);
+            float *yo = y + wrap_tau(tau) * V + z0 * P;
+            float4 below = ld4(t0 + c_lo * P + q.s), here = ld4(t0 + (c_lo + 1) * P + q.s);
+            for (int pz = c_lo; pz < c_hi; ++pz) {
+                const float *tc = t0 + (pz + 1) * P;
+                const float4 above = ld4(tc + P + q.s);
+                const int k = (pz + 1) * P + q.s;
+                const float4 l = ld4(lc + k), o = ld4(t1 + k);
+                float hm, hp;
+                x_halo(tc, q, here, shfl, src_m, src_p, hm, hp);
+                *reinterpret_cast<float4 *>(yo + pz * P + q.s) =
+                    plane_stencil(tc, q, here, below, above, l, o, h, hm, hp);
                 below = here;
                 here = above;
             }
@@ -276,15 +368,17 @@ size_t fused_mtm_smem(int nx, int tz)
     return (3 * (size_t)(tz + 4) + 2 * (size_t)(tz + 2) * 2) * P * sizeof(float);
 }
 
+static int fused_tz(int nx)
+{
+    return (nx % 4 == 0 && nx >= 8) ? 4 : 2;
+}
+
 bool fused_mtm_ok(const Geo &g, const void *L, const void *x, const void *y)
 {
-    if (g.d != 3) return false;
-    size_t P = (size_t)g.nx * g.nx;
-    if ((P * sizeof(float)) % 16) return false;
-    if (((uintptr_t)L | (uintptr_t)x) & 15u) return false;
-    if (g.nx < 4 || g.ntau < 3) return false;
-    int tz = (g.nx % 4 == 0) ? 4 : (g.nx % 2 == 0 ? 2 : 1);
-    return fused_mtm_smem(g.nx, tz) <= 200 * 1024;
+    if (g.d != 3 || g.nx % 4 != 0 || g.nx < 4 || g.ntau < 3) return false;
+    if (((uintptr_t)L | (uintptr_t)x | (uintptr_t)y) & 15u) return false;
+    if ((size_t)g.nx * g.nx / 4 > 1024) return false;   // one float4 group per thread at least
+    return fused_mtm_smem(g.nx, fused_tz(g.nx)) <= 200 * 1024;
 }
 
 cudaError_t launch_mtm_fused_f32(const Geo &g, float h, const float *L, const float *x, float *y, int *err,
@@ -293,7 +387,7 @@ cudaError_t launch_mtm_fused_f32(const Geo &g, float h, const float *L, const fl
     FusedCfg c;
     c.g = g;
     c.h = h;
-    c.tz = (g.nx % 4 == 0) ? 4 : (g.nx % 2 == 0 ? 2 : 1);
+    c.tz = fused_tz(g.nx);
     c.nslab = g.nx / c.tz;
     c.P = g.nx * g.nx;
     int chunks = (nsm + c.nslab - 1) / c.nslab;
@@ -301,10 +395,16 @@ cudaError_t launch_mtm_fused_f32(const Geo &g, float h, const float *L, const fl
     c.tc = (g.ntau + chunks - 1) / chunks;
     chunks = (g.ntau + c.tc - 1) / c.tc;
     size_t smem = fused_mtm_smem(g.nx, c.tz);
-    cudaError_t e = cudaFuncSetAttribute(k_mtm_fused_d3, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    k_mtm_fused_d3<<<c.nslab * chunks, 512, smem, st>>>(c, L, x, y, err);
+    cudaError_t e;
+    if (c.tz == 4) {
+        e = cudaFuncSetAttribute(k_mtm_fused_d3<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_mtm_fused_d3<4><<<c.nslab * chunks, kFusedThreads, smem, st>>>(c, L, x, y, err);
+    } else {
+        e = cudaFuncSetAttribute(k_mtm_fused_d3<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_mtm_fused_d3<2><<<c.nslab * chunks, kFusedThreads, smem, st>>>(c, L, x, y, err);
+    }
     return cudaGetLastError();
 }
 

@@ -212,7 +212,10 @@ struct hh_batch {
     EngTile *d_tiles = nullptr;
     double *d_tt = nullptr, *d_rr = nullptr;
     BarrierCtl *d_ctl = nullptr;
-    int max_sys = 0, grid = 0, ntiles = 0;
+    int max_sys = 0, ntiles = 0;
+    int grid_of[4] = {0, 0, 0, 0};  // engine grid per kernel kind
+    int kind = ENGINE_GENERIC;      // kernel of the current plan
+    int graph_kind = -1;
     long long k = 0;
     bool plan_dirty = true;
     std::vector<EngSystem> h_sys;
@@ -432,7 +435,13 @@ int build_plan(hh_batch *b)
     }
     b->ntiles = (int)b->h_tiles.size();
     if (b->ntiles > kMaxTiles) return HH_EINVAL;
-    int grid = b->ntiles < b->grid ? b->ntiles : b->grid;
+    // One dimension in the whole plan: the specialised kernel.
+    int dims = 0;
+    for (int s = 0; s < (int)b->slots.size(); ++s)
+        if (b->slots[s].used && b->slots[s].in_engine) dims |= (b->slots[s].geo.d == 1) ? 1 : 2;
+    b->kind = dims == 1 ? ENGINE_D1 : dims == 2 ? ENGINE_D3 : ENGINE_GENERIC;
+    const int kgrid = b->grid_of[b->kind];
+    int grid = b->ntiles < kgrid ? b->ntiles : kgrid;
     for (int s = 0; s < (int)b->slots.size(); ++s) {
         Slot &S = b->slots[s];
         if (!S.used || !S.in_engine) continue;
@@ -476,13 +485,20 @@ int launch_chunk(hh_batch *b, int grid)
         void *args[] = {(void *)&arg};
         cudaKernelNodeParams kp;
         memset(&kp, 0, sizeof(kp));
-        kp.func = (void *)engine_kernel_fn();
+        kp.func = (void *)engine_kernel_fn(b->kind);
         kp.gridDim = dim3(grid);
         kp.blockDim = dim3(ENGINE_BLOCK);
         kp.sharedMemBytes = 0;
         kp.kernelParams = args;
         bool ok = true;
+        if (b->gexec && b->graph_kind != b->kind) {
+            cudaGraphExecDestroy(b->gexec);
+            cudaGraphDestroy(b->graph);
+            b->gexec = nullptr;
+            b->graph = nullptr;
+        }
         if (!b->gexec) {
+            b->graph_kind = b->kind;
             ok = cudaGraphCreate(&b->graph, 0) == cudaSuccess &&
                  cudaGraphAddKernelNode(&b->gnode, b->graph, nullptr, 0, &kp) == cudaSuccess;
             if (ok) {
@@ -501,7 +517,7 @@ int launch_chunk(hh_batch *b, int grid)
         cudaGetLastError();
         b->use_graph = false;
     }
-    HB_TRY(engine_launch(arg, grid, ENGINE_BLOCK, b->stream));
+    HB_TRY(engine_launch(arg, grid, ENGINE_BLOCK, b->stream, b->kind));
     return HH_OK;
 }
 
@@ -603,7 +619,8 @@ int step(hh_batch *b)
         rc = build_plan(b);
         if (rc) return rc;
     }
-    int grid = b->ntiles < b->grid ? b->ntiles : b->grid;
+    const int kgrid = b->grid_of[b->kind];
+    int grid = b->ntiles < kgrid ? b->ntiles : kgrid;
     BarrierCtl c;
     memset(&c, 0, sizeof(c));
     c.active = n_running;
@@ -712,8 +729,11 @@ int hh_batch_create(hh_batch **out, const hh_batch_config *cfg, void *cuda_strea
     b->max_sys = cfg->max_slots * kMaxRhs;
     b->h_sys.resize(b->max_sys);
     memset(b->h_sys.data(), 0, sizeof(EngSystem) * b->max_sys);
-    b->grid = engine_default_grid();
-    cudaError_t e = b->grid > 0 ? cudaSuccess : cudaErrorUnknown;
+    b->grid_of[ENGINE_GENERIC] = engine_default_grid(ENGINE_GENERIC);
+    b->grid_of[ENGINE_D1] = engine_default_grid(ENGINE_D1);
+    b->grid_of[ENGINE_D3] = engine_default_grid(ENGINE_D3);
+    cudaError_t e = (b->grid_of[0] > 0 && b->grid_of[1] > 0 && b->grid_of[3] > 0) ? cudaSuccess
+                                                                                 : cudaErrorUnknown;
     if (e == cudaSuccess) e = b->arena.init(cfg->hbm_budget_bytes);
     b->parts.init(kMaxTiles);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_sys, sizeof(EngSystem) * b->max_sys);

@@ -109,6 +109,7 @@ struct hh_ctx {
     int N;
     int cap_rhs;
     int max_grid;
+    int kind;               // engine kernel for this lattice's dimension
     long long timeout_ns;
     // fields
     double *sigma, *sigma0, *L64, *pi, *chi, *xsol, *tmp, *F;
@@ -263,7 +264,7 @@ int run_engine(hh_ctx *c)
     L.max_iters = 3LL * (long long)c->prm.cg_maxit + 64;
     bool rec = c->profile && c->ev_used + 2 <= c->ev_cap;
     if (rec) HH_TRY(cudaEventRecord(c->ev[c->ev_used], c->stream));
-    HH_TRY(engine_launch(L, P.grid, ENGINE_BLOCK, c->stream));
+    HH_TRY(engine_launch(L, P.grid, ENGINE_BLOCK, c->stream, c->kind));
     if (rec) {
         HH_TRY(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
         c->ev_used += 2;
@@ -368,7 +369,8 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
     c->N = (int)N;
     c->cap_rhs = p->n_pf > 4 ? p->n_pf : 4;
     c->timeout_ns = 5LL * 1000 * 1000 * 1000;
-    int max_grid = engine_default_grid();
+    c->kind = lat->d == 1 ? ENGINE_D1 : ENGINE_D3;
+    int max_grid = engine_default_grid(c->kind);
     if (max_grid <= 0) {
         delete c;
         return HH_ECUDA;

@@ -361,8 +361,9 @@ __device__ __forceinline__ bool grid_barrier(BarrierCtl *ctl, unsigned nblocks, 
     if (threadIdx.x == 0) {
         target += nblocks;
         int ok = 1;
-        __threadfence();
-        atomicAdd(&ctl->count, 1u);
+        // Release: the block's writes (ordered before by bar.sync) become
+        // visible no later than this arrival.
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&ctl->count), "r"(1u) : "memory");
         unsigned spins = 0;
         uint64_t t0 = 0;
         while ((int)(ld_acquire_u32(&ctl->count) - target) < 0) {

@@ -256,10 +256,15 @@ __device__ EngState decide(const EngSystem &Y, const EngState &P, double rr)
             // A reliable update that did not halve the true residual norm
             // since the previous one (whether the FP32 residual fell below
             // delta or the stall window ran out) means the FP32 steps have
-            // stopped making progress (eps_32 * cond(Q) >~ 1).  After two in a
-            // row the system continues with FP64 CG steps from a restart at
-            // the FP64 residual.
-            S.stall = (rr > 0.25 * P.rr_ru) ? P.stall + 1 : 0;
+            // stopped making progress (eps_32 * cond(Q) >~ 1).  After two
+            // stalls in a row the system continues with FP64 CG steps from a
+            // restart at the FP64 residual.
+            // Also a stall: the true residual is more than 4x (in norm) the
+            // FP32 recursive residual that triggered this update, i.e. the
+            // FP32 recursion no longer tracks b - Q x.
+            const bool no_progress = rr > 0.25 * P.rr_ru;
+            const bool drifted = rr > 16.0 * P.rr_last;
+            S.stall = (no_progress || drifted) ? P.stall + 1 : 0;
             if (S.stall >= 2) {
                 S.prec = PREC_FP64;
                 S.beta = 0.0;
@@ -335,8 +340,8 @@ __device__ double slot3(const EngSystem &Y, const TileCtl &c, const EngTile &T)
     return 0.0;
 }
 
-// Dispatch on the lattice dimension and the group width of the system.
-template <int SLOT>
+// Dispatch on the lattice dimension (fixed when FD != 0) and the group width.
+template <int SLOT, int FD>
 __device__ double run_slot(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 {
 #define HH_SLOT_CALL(D, W)                                   \
@@ -349,7 +354,7 @@ __device__ double run_slot(const EngSystem &Y, const TileCtl &c, const EngTile &
         return slot3<D, W>(Y, c, T);                         \
     }
     const int w = Y.w;
-    if (Y.g.d == 3) {
+    if (FD == 3 || (FD == 0 && Y.g.d == 3)) {
         if (w == 4) { HH_SLOT_CALL(3, 4) }
         if (w == 2) { HH_SLOT_CALL(3, 2) }
         HH_SLOT_CALL(3, 1)
@@ -361,18 +366,75 @@ __device__ double run_slot(const EngSystem &Y, const TileCtl &c, const EngTile &
 #undef HH_SLOT_CALL
 }
 
-__global__ void __launch_bounds__(ENGINE_BLOCK, 1) engine_kernel(EngLaunch L)
+// Per-block cache of the systems a block touches.  Every block that owns a
+// tile of a system computes that system's state with the same pure decide(),
+// so after the first iteration of a launch the block keeps the states in
+// shared memory and reads only the per-tile partial sums from global memory;
+// the owner block still writes each state to global memory for the host and
+// for the next launch.  A block touching more systems or tiles than the cache
+// holds falls back to reading the states from global memory.
+constexpr int kCacheSys = 32;
+constexpr int kCacheTiles = 128;
+
+template <int FD, int MINB>
+__global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
 {
     __shared__ double s_red[ENGINE_BLOCK / 32];
     __shared__ double s_val;
     __shared__ int s_flag;
-    __shared__ EngState s_state;
-    __shared__ TileCtl s_ctl;
+    __shared__ EngState s_cache[kCacheSys];
+    __shared__ TileCtl s_tctl[kCacheSys];
+    __shared__ int s_sys[kCacheSys];
+    __shared__ unsigned char s_slot[kCacheTiles];
+    __shared__ int s_ok;
+    // Read-only descriptors of this block's tiles and systems, copied once:
+    // the acquire at every grid barrier invalidates L1, so re-reading them
+    // from global memory would cost two dependent L2 round trips per phase.
+    __shared__ EngTile s_tiles[kCacheTiles];
+    __shared__ EngSystem s_sysd[kCacheSys];
 
     BarrierCtl *ctl = L.ctl;
     const unsigned G = gridDim.x;
     unsigned target = 0;
     long long k = *(volatile long long *)&ctl->k;
+
+    if (threadIdx.x == 0) {
+        int n = 0, ok = 1, j = 0;
+        for (int tile = blockIdx.x; tile < L.ntiles; tile += G, ++j) {
+            if (j >= kCacheTiles) {
+                ok = 0;
+                break;
+            }
+            const int sys = L.tiles[tile].sys;
+            int slot = -1;
+            for (int q = 0; q < n; ++q)
+                if (s_sys[q] == sys) slot = q;
+            if (slot < 0) {
+                if (n == kCacheSys) {
+                    ok = 0;
+                    break;
+                }
+                slot = n;
+                s_sys[n++] = sys;
+            }
+            s_slot[j] = (unsigned char)slot;
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    const bool cached = s_ok != 0;
+    if (cached) {
+        int j = 0;
+        for (int tile = blockIdx.x; tile < L.ntiles; tile += G, ++j)
+            if ((int)threadIdx.x == (j % (int)blockDim.x)) s_tiles[j] = L.tiles[tile];
+        __syncthreads();
+        j = 0;
+        for (int tile = blockIdx.x; tile < L.ntiles; tile += G, ++j) {
+            const int slot = s_slot[j];
+            if (threadIdx.x == 0 && s_sys[slot] == s_tiles[j].sys) s_sysd[slot] = L.sys[s_tiles[j].sys];
+        }
+        __syncthreads();
+    }
 
     for (long long it = 0; it < L.max_iters; ++it, ++k) {
         EngState *cur = (k & 1) ? L.state[1] : L.state[0];
@@ -380,35 +442,39 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, 1) engine_kernel(EngLaunch L)
 
         // ---- slot 1: decide, then direction update / reliable-update accumulate ----
         {
-            int last = -1;
-            for (int tile = blockIdx.x; tile < L.ntiles; tile += G) {
-                const EngTile T = L.tiles[tile];
-                const EngSystem &Y = L.sys[T.sys];
+            int last = -1, j = 0;
+            for (int tile = blockIdx.x; tile < L.ntiles; tile += G, ++j) {
+                const int slot = cached ? s_slot[j] : 0;
+                const EngTile T = cached ? s_tiles[j] : L.tiles[tile];
+                const EngSystem &Y = cached ? s_sysd[slot] : L.sys[T.sys];
                 if (T.sys != last) {
+                    if (!cached || it == 0) {
+                        __syncthreads();
+                        if (threadIdx.x == 0) s_cache[slot] = cur[T.sys];
+                    }
                     __syncthreads();
-                    if (threadIdx.x == 0) s_state = cur[T.sys];
-                    __syncthreads();
-                    const int pm = s_state.mode;
+                    const int pm = s_cache[slot].mode;
                     double rr = 0.0;
                     if (pm == MODE_INIT || pm == MODE_CG || pm == MODE_RU)
                         rr = sum_partials(L.part_rr, Y.part0, Y.ntiles, &s_val);
                     if (threadIdx.x == 0) {
-                        const EngState P = s_state;
+                        const EngState P = s_cache[slot];
                         const EngState S = decide(Y, P, rr);
                         if ((int)blockIdx.x == Y.owner) {
                             nxt[T.sys] = S;
                             if (S.mode == MODE_DONE && P.mode != MODE_DONE) atomicSub(&ctl->active, 1);
                         }
-                        s_ctl.mode = S.mode;
-                        s_ctl.prec = S.prec;
-                        s_ctl.beta = S.beta;
-                        s_ctl.alpha = 0.0;
+                        s_cache[slot] = S;
+                        s_tctl[slot].mode = S.mode;
+                        s_tctl[slot].prec = S.prec;
+                        s_tctl[slot].beta = S.beta;
+                        s_tctl[slot].alpha = 0.0;
                     }
                     __syncthreads();
                     last = T.sys;
                 }
-                const TileCtl c = s_ctl;
-                run_slot<1>(Y, c, T);
+                const TileCtl c = s_tctl[slot];
+                run_slot<1, FD>(Y, c, T);
             }
         }
         if (!grid_barrier(ctl, G, target, &s_flag)) return;
@@ -419,24 +485,26 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, 1) engine_kernel(EngLaunch L)
 
         // ---- slot 2 ----
         {
-            int last = -1;
-            for (int tile = blockIdx.x; tile < L.ntiles; tile += G) {
-                const EngTile T = L.tiles[tile];
-                const EngSystem &Y = L.sys[T.sys];
-                if (T.sys != last) {
+            int last = -1, j = 0;
+            for (int tile = blockIdx.x; tile < L.ntiles; tile += G, ++j) {
+                const int slot = cached ? s_slot[j] : 0;
+                const EngTile T = cached ? s_tiles[j] : L.tiles[tile];
+                const EngSystem &Y = cached ? s_sysd[slot] : L.sys[T.sys];
+                if (!cached && T.sys != last) {
                     __syncthreads();
                     if (threadIdx.x == 0) {
                         const EngState S = nxt[T.sys];
-                        s_ctl.mode = S.mode;
-                        s_ctl.prec = S.prec;
-                        s_ctl.beta = S.beta;
-                        s_ctl.alpha = 0.0;
+                        s_cache[0] = S;
+                        s_tctl[0].mode = S.mode;
+                        s_tctl[0].prec = S.prec;
+                        s_tctl[0].beta = S.beta;
+                        s_tctl[0].alpha = 0.0;
                     }
                     __syncthreads();
                     last = T.sys;
                 }
-                const TileCtl c = s_ctl;
-                double v = run_slot<2>(Y, c, T);
+                const TileCtl c = s_tctl[slot];
+                double v = run_slot<2, FD>(Y, c, T);
                 if (c.mode == MODE_CG) {
                     double tot = block_sum(v, s_red);
                     if (threadIdx.x == 0) L.part_tt[T.part] = tot;
@@ -447,29 +515,30 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, 1) engine_kernel(EngLaunch L)
 
         // ---- slot 3 ----
         {
-            int last = -1;
-            for (int tile = blockIdx.x; tile < L.ntiles; tile += G) {
-                const EngTile T = L.tiles[tile];
-                const EngSystem &Y = L.sys[T.sys];
+            int last = -1, j = 0;
+            for (int tile = blockIdx.x; tile < L.ntiles; tile += G, ++j) {
+                const int slot = cached ? s_slot[j] : 0;
+                const EngTile T = cached ? s_tiles[j] : L.tiles[tile];
+                const EngSystem &Y = cached ? s_sysd[slot] : L.sys[T.sys];
                 if (T.sys != last) {
                     __syncthreads();
-                    if (threadIdx.x == 0) {
+                    if (!cached && threadIdx.x == 0) {
                         const EngState S = nxt[T.sys];
-                        s_state = S;
-                        s_ctl.mode = S.mode;
-                        s_ctl.prec = S.prec;
-                        s_ctl.beta = S.beta;
+                        s_cache[0] = S;
+                        s_tctl[0].mode = S.mode;
+                        s_tctl[0].prec = S.prec;
+                        s_tctl[0].beta = S.beta;
                     }
                     __syncthreads();
-                    if (s_ctl.mode == MODE_CG) {
+                    if (s_tctl[slot].mode == MODE_CG) {
                         double tt = sum_partials(L.part_tt, Y.part0, Y.ntiles, &s_val);
-                        if (threadIdx.x == 0) s_ctl.alpha = s_state.rr_alpha / tt;
+                        if (threadIdx.x == 0) s_tctl[slot].alpha = s_cache[slot].rr_alpha / tt;
                     }
                     __syncthreads();
                     last = T.sys;
                 }
-                const TileCtl c = s_ctl;
-                double v = run_slot<3>(Y, c, T);
+                const TileCtl c = s_tctl[slot];
+                double v = run_slot<3, FD>(Y, c, T);
                 if (c.mode == MODE_CG || c.mode == MODE_RU || c.mode == MODE_INIT) {
                     double tot = block_sum(v, s_red);
                     if (threadIdx.x == 0) L.part_rr[T.part] = tot;
@@ -483,35 +552,47 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, 1) engine_kernel(EngLaunch L)
 
 }  // namespace
 
-cudaError_t engine_launch(const EngLaunch &L, int grid, int block, cudaStream_t stream)
+// The kernels: generic (any mix of dimensions) and the dimension-specialised
+// ones.  The d = 1 kernel is compiled to fit 64 registers (two blocks could
+// share an SM); measured on GB300, one block per SM with fewer grid-barrier
+// arrivals is faster, so every kind launches one block per SM by default.
+const void *kernel_of(int kind)
+{
+    switch (kind) {
+    case ENGINE_D1: return (const void *)engine_kernel<1, 2>;
+    case ENGINE_D3: return (const void *)engine_kernel<3, 1>;
+    default: return (const void *)engine_kernel<0, 1>;
+    }
+}
+
+cudaError_t engine_launch(const EngLaunch &L, int grid, int block, cudaStream_t stream, int kind)
 {
     EngLaunch arg = L;
     void *args[] = {(void *)&arg};
-    return cudaLaunchCooperativeKernel((const void *)engine_kernel, dim3(grid), dim3(block), args, 0,
-                                       stream);
+    return cudaLaunchCooperativeKernel(kernel_of(kind), dim3(grid), dim3(block), args, 0, stream);
 }
 
-const void *engine_kernel_fn()
+const void *engine_kernel_fn(int kind)
 {
-    return (const void *)engine_kernel;
+    return kernel_of(kind);
 }
 
-int engine_max_grid(int block)
+int engine_max_grid(int block, int kind)
 {
     int dev = 0, nsm = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, engine_kernel, block, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel_of(kind), block, 0) != cudaSuccess)
         return 0;
     return per * nsm;
 }
 
-int engine_default_grid()
+int engine_default_grid(int kind)
 {
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    int mx = engine_max_grid(ENGINE_BLOCK);
+    int mx = engine_max_grid(ENGINE_BLOCK, kind);
     const char *env = getenv("HH_ENGINE_BLOCKS_PER_SM");
     int per = env ? atoi(env) : 1;
     if (per < 1) per = 1;

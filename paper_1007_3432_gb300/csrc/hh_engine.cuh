@@ -104,23 +104,29 @@ struct EngLaunch {
     long long max_iters;    // engine iterations this launch may run
 };
 
+// Engine kernels: ENGINE_GENERIC handles systems of both dimensions in one
+// launch; ENGINE_D1 / ENGINE_D3 require every system of the launch to have
+// that dimension and are compiled for it.
+enum EngKind : int { ENGINE_GENERIC = 0, ENGINE_D1 = 1, ENGINE_D3 = 3 };
+
 // Host launcher: runs the engine with a cooperative launch of 'grid' blocks.
 // The barrier counter ctl->count must be zero when the launch starts.
 // Returns a cudaError_t from the launch.
-cudaError_t engine_launch(const EngLaunch &L, int grid, int block, cudaStream_t stream);
+cudaError_t engine_launch(const EngLaunch &L, int grid, int block, cudaStream_t stream, int kind);
 
-// The engine kernel, for CUDA-graph kernel nodes.
-const void *engine_kernel_fn();
+// The engine kernel of a kind, for CUDA-graph kernel nodes.
+const void *engine_kernel_fn(int kind);
 
-// Largest co-resident grid for the engine kernel at 'block' threads.
-int engine_max_grid(int block);
+// Largest co-resident grid for the engine kernel of a kind at 'block' threads.
+int engine_max_grid(int block, int kind);
 
 constexpr int ENGINE_BLOCK = 512;
 constexpr int ENGINE_MIN_TILE = 512;   // sites per tile, at least one per thread
 
-// Default grid: one block per SM (fewer arrivals per grid barrier), capped by
-// co-residency.  HH_ENGINE_BLOCKS_PER_SM overrides the blocks per SM.
-int engine_default_grid();
+// Default grid: one block per SM (fewer arrivals per grid barrier), capped
+// by co-residency.
+// HH_ENGINE_BLOCKS_PER_SM overrides the blocks per SM.
+int engine_default_grid(int kind);
 
 // Tiles of one system: 'tiles' contiguous ranges of 'chunk' sites (the last
 // one shorter), enough to give every block of the grid a tile when 'nsys'

@@ -55,25 +55,26 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 unsigned char *g_scratch_addr[kMaxDevices];
-int g_max_grid[kMaxDevices];
+int g_max_grid[kMaxDevices][2];   // engine grid for d = 1 and d = 3
 
 // Once per device, with that device current: the device address of the
 // scratch array (the host-side symbol is only a stand-in) and the engine's
 // co-resident grid size.
-int setup_device(int dev, unsigned char **base, int *max_grid)
+int setup_device(int dev, int d, unsigned char **base, int *max_grid)
 {
     if (dev < 0 || dev >= kMaxDevices) return HH_EINVAL;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_addr[dev]) {
         void *addr = nullptr;
         if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) return HH_ECUDA;
-        int g = engine_default_grid();
-        if (g <= 0) return HH_ECUDA;
-        g_max_grid[dev] = g;
+        int g1 = engine_default_grid(ENGINE_D1), g3 = engine_default_grid(ENGINE_D3);
+        if (g1 <= 0 || g3 <= 0) return HH_ECUDA;
+        g_max_grid[dev][0] = g1;
+        g_max_grid[dev][1] = g3;
         g_scratch_addr[dev] = (unsigned char *)addr;
     }
     *base = g_scratch_addr[dev];
-    *max_grid = g_max_grid[dev];
+    *max_grid = g_max_grid[dev][d == 1 ? 0 : 1];
     return HH_OK;
 }
 
@@ -149,7 +150,7 @@ extern "C" int hh_solve_noalloc(const hh_lattice *lat, const hh_params *p, const
     if (cudaGetDevice(&dev) != cudaSuccess) return HH_ECUDA;
     unsigned char *base = nullptr;
     int max_grid = 0;
-    int rc = setup_device(dev, &base, &max_grid);
+    int rc = setup_device(dev, lat->d, &base, &max_grid);
     if (rc) return rc;
 
     Geo g = make_geo(lat->d, lat->nx, lat->ntau);
@@ -177,7 +178,8 @@ extern "C" int hh_solve_noalloc(const hh_lattice *lat, const hh_params *p, const
     L.nsys = 1;
     L.ntiles = ntiles;
     L.max_iters = 3LL * (long long)p->cg_maxit + 64;
-    if (engine_launch(L, grid, ENGINE_BLOCK, st) != cudaSuccess) return HH_ECUDA;
+    if (engine_launch(L, grid, ENGINE_BLOCK, st, lat->d == 1 ? ENGINE_D1 : ENGINE_D3) != cudaSuccess)
+        return HH_ECUDA;
     if (!info) return HH_OK;
 
     // Results into caller stack memory (pageable copies, no allocation).
