@@ -48,6 +48,8 @@ def lib():
         L.oracle_nsites.restype = ctypes.c_long
         L.oracle_uniform.restype = ctypes.c_double
         L.oracle_action.restype = ctypes.c_double
+        L.oracle_cheb_poly.restype = ctypes.c_double
+        L.oracle_cheb_poly.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
         _lib = L
     return _lib
 
@@ -106,6 +108,38 @@ def cg(lat, h, L, b, tol=1e-10, maxit=100000):
     st = lib().oracle_cg(ctypes.byref(lat), ctypes.c_double(h), _ptr(L), _ptr(b), _ptr(x),
                          ctypes.c_double(tol), ctypes.c_int(maxit), ctypes.byref(it),
                          ctypes.byref(rr))
+    return x, st, it.value, rr.value
+
+
+def gershgorin_lambda_max(d, h, A):
+    """Upper bound of the spectrum of Q = M^T M: ||Q|| <= ||M||_1 ||M||_inf,
+    each at most 1 + 2 d h + (1 + A) (unit diagonal, 2d hops, one link)."""
+    return (2.0 + 2.0 * d * h + A) ** 2
+
+
+def cheb_poly(n, eps, z):
+    return lib().oracle_cheb_poly(n, eps, z)
+
+
+def cheb_apply(lat, h, L, n, eps, lam, x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    y = np.empty(nsites(lat))
+    lib().oracle_cheb_apply(ctypes.byref(lat), ctypes.c_double(h), _ptr(L), ctypes.c_int(n),
+                            ctypes.c_double(eps), ctypes.c_double(lam), _ptr(x), _ptr(y))
+    return y
+
+
+def pcg(lat, h, L, b, n, eps, lam, tol=1e-10, maxit=100000):
+    """Chebyshev-preconditioned CG; returns (x, status, iterations, true_relres)."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    x = np.empty(nsites(lat))
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = lib().oracle_pcg(ctypes.byref(lat), ctypes.c_double(h), _ptr(L), ctypes.c_int(n),
+                          ctypes.c_double(eps), ctypes.c_double(lam), _ptr(b), _ptr(x),
+                          ctypes.c_double(tol), ctypes.c_int(maxit), ctypes.byref(it), ctypes.byref(rr))
     return x, st, it.value, rr.value
 
 

@@ -223,6 +223,134 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
+/* Chebyshev polynomial preconditioner, Sec. 4.2 Eqs. (13)-(17).            */
+/* ------------------------------------------------------------------------ */
+
+/* Root z_k of Eq. (15), as (re, im). */
+static void cheb_root(int n, double eps, int k, double *re, double *im)
+{
+    const double pi = 3.14159265358979323846264338328;
+    double m = 0.5 * (1.0 + eps);
+    double th = 2.0 * pi * (double)k / (double)(2 * n + 1);
+    *re = m * (1.0 - cos(th));
+    *im = -sqrt(eps) * sin(th);
+}
+
+/* P(z) = c_2n prod_k (z - z_k) with c_2n^{-1} = m prod_k (m - z_k) (Eqs. (13)-(14)).
+ * The roots come in conjugate pairs (k and 2n+1-k), so the product is real;
+ * it is evaluated as a complex product of the 2n factors, each divided by its
+ * value at z = m, in the order k = 1..2n. */
+double oracle_cheb_poly(int n, double eps, double z)
+{
+    double m = 0.5 * (1.0 + eps);
+    double pr = 1.0 / m, pi_ = 0.0;
+    for (int k = 1; k <= 2 * n; ++k) {
+        double re, im;
+        cheb_root(n, eps, k, &re, &im);
+        /* (z - z_k) / (m - z_k) */
+        double ar = z - re, ai = -im;
+        double br = m - re, bi = -im;
+        double den = br * br + bi * bi;
+        double qr = (ar * br + ai * bi) / den, qi = (ai * br - ar * bi) / den;
+        double nr = pr * qr - pi_ * qi, ni = pr * qi + pi_ * qr;
+        pr = nr;
+        pi_ = ni;
+    }
+    return pr;
+}
+
+/* y = P(Q/lam) x: the conjugate pair k, 2n+1-k gives the real factor
+ * ((Q/lam - a)^2 + b^2) / ((m - a)^2 + b^2) with a = Re z_k, b = Im z_k;
+ * factors applied for k = 1..n, then the overall 1/m. */
+void oracle_cheb_apply(const oracle_lattice *lat, double h, const double *L, int n, double eps,
+                       double lam, const double *x, double *y)
+{
+    long N = oracle_nsites(lat);
+    double m = 0.5 * (1.0 + eps);
+    double *v = (double *)malloc(sizeof(double) * (size_t)N);
+    double *u = (double *)malloc(sizeof(double) * (size_t)N);
+    double *w = (double *)malloc(sizeof(double) * (size_t)N);
+    for (long i = 0; i < N; ++i) v[i] = x[i];
+    for (int k = 1; k <= n; ++k) {
+        double a, b;
+        cheb_root(n, eps, k, &a, &b);
+        double qm = (m - a) * (m - a) + b * b;
+        /* u = (Q/lam - a) v */
+        oracle_apply_MTM(lat, h, L, v, w);
+        for (long i = 0; i < N; ++i) u[i] = w[i] / lam - a * v[i];
+        /* v = ((Q/lam - a) u + b^2 v) / qm */
+        oracle_apply_MTM(lat, h, L, u, w);
+        for (long i = 0; i < N; ++i) v[i] = (w[i] / lam - a * u[i] + b * b * v[i]) / qm;
+    }
+    for (long i = 0; i < N; ++i) y[i] = v[i] / m;
+    free(v);
+    free(u);
+    free(w);
+}
+
+/* Preconditioned CG (Sec. 4.2: CG on Q with the preconditioner P(Q/lam)),
+ * x0 = 0, same stopping rule as oracle_cg. */
+int oracle_pcg(const oracle_lattice *lat, double h, const double *L, int n, double eps, double lam,
+               const double *b, double *x, double tol, int maxit, int *iterations, double *true_relres)
+{
+    long N = oracle_nsites(lat);
+    double *r = (double *)malloc(sizeof(double) * (size_t)N);
+    double *z = (double *)malloc(sizeof(double) * (size_t)N);
+    double *p = (double *)malloc(sizeof(double) * (size_t)N);
+    double *q = (double *)malloc(sizeof(double) * (size_t)N);
+    int status = -4, k = 0;
+    double bnorm = sqrt(dot(N, b, b));
+    for (long i = 0; i < N; ++i) {
+        x[i] = 0.0;
+        r[i] = b[i];
+    }
+    *true_relres = 0.0;
+    if (bnorm == 0.0) {
+        status = 0;
+        goto done;
+    }
+    *true_relres = 1.0;
+    oracle_cheb_apply(lat, h, L, n, eps, lam, r, z);
+    for (long i = 0; i < N; ++i) p[i] = z[i];
+    double rz = dot(N, r, z);
+    for (k = 1; k <= maxit; ++k) {
+        oracle_apply_MTM(lat, h, L, p, q);
+        double alpha = rz / dot(N, p, q);
+        for (long i = 0; i < N; ++i) {
+            x[i] += alpha * p[i];
+            r[i] -= alpha * q[i];
+        }
+        if (sqrt(dot(N, r, r)) <= tol * bnorm) {
+            oracle_apply_MTM(lat, h, L, x, q);
+            for (long i = 0; i < N; ++i) r[i] = b[i] - q[i];
+            *true_relres = sqrt(dot(N, r, r)) / bnorm;
+            if (*true_relres <= tol) {
+                status = 0;
+                break;
+            }
+        }
+        oracle_cheb_apply(lat, h, L, n, eps, lam, r, z);
+        double rz_new = dot(N, r, z);
+        double beta = rz_new / rz;
+        rz = rz_new;
+        for (long i = 0; i < N; ++i) p[i] = z[i] + beta * p[i];
+    }
+    if (status != 0) {
+        oracle_apply_MTM(lat, h, L, x, q);
+        for (long i = 0; i < N; ++i) r[i] = b[i] - q[i];
+        *true_relres = sqrt(dot(N, r, r)) / bnorm;
+        k = maxit;
+    }
+done:
+    *iterations = k;
+    free(r);
+    free(z);
+    free(p);
+    free(q);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Philox4x64-10 counter-based generator (Salmon, Moraes, Dror, Shaw,        */
 /* "Parallel random numbers: as easy as 1, 2, 3", SC'11).                    */
 /* ------------------------------------------------------------------------ */

@@ -69,6 +69,18 @@ void oracle_apply_MTM(const oracle_lattice *lat, double h, const double *L,
 int oracle_cg(const oracle_lattice *lat, double h, const double *L, const double *b,
               double *x, double tol, int maxit, int *iterations, double *true_relres);
 
+/* Chebyshev polynomial preconditioner of Sec. 4.2, Eqs. (13)-(17).
+ * Roots z_k = m (1 - cos(2 pi k/(2n+1))) - i sqrt(eps) sin(2 pi k/(2n+1)),
+ * m = (1 + eps)/2, k = 1..2n, for Q normalised to eigenvalues in [0, 1]. */
+double oracle_cheb_poly(int n, double eps, double z);
+/* y = P(Q/lam) x (normalisation lam >= lambda_max(Q)). */
+void oracle_cheb_apply(const oracle_lattice *lat, double h, const double *L, int n, double eps,
+                       double lam, const double *x, double *y);
+/* Preconditioned CG with preconditioner P(Q/lam); x0 = 0; stop on the true
+ * residual as oracle_cg.  *iterations counts PCG steps. */
+int oracle_pcg(const oracle_lattice *lat, double h, const double *L, int n, double eps, double lam,
+               const double *b, double *x, double tol, int maxit, int *iterations, double *true_relres);
+
 /* Philox4x64-10 block cipher (Salmon et al., SC'11). */
 void oracle_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
 void oracle_gaussian(uint64_t seed, int tag, int a, uint64_t traj, uint64_t chain,

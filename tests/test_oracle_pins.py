@@ -426,3 +426,87 @@ def test_hmc_reproduces_exact_expectation_on_2x2(orc):
     blocks = obs[: len(obs) // 50 * 50].reshape(50, -1).mean(axis=1)
     err = blocks.std(ddof=1) / np.sqrt(len(blocks))
     assert abs(obs.mean() - exact) < 4 * err, (obs.mean(), exact, err)
+
+
+# --- Chebyshev polynomial preconditioner (Sec. 4.2) ---------------------------
+
+
+@pytest.mark.parametrize("n,eps", [(2, 0.1), (4, 0.01), (8, 1e-3), (16, 1e-4), (12, 0.05)])
+def test_chebyshev_error_bound(orc, n, eps):
+    """|z P(z) - 1| <= 2 ((1 - sqrt(eps)) / (1 + sqrt(eps)))^(2n+1) on [eps, 1]
+    (Eqs. (16)-(17)); P(z) > 0 on [0, 1]."""
+    bound = 2 * ((1 - np.sqrt(eps)) / (1 + np.sqrt(eps))) ** (2 * n + 1)
+    zs = np.concatenate([np.linspace(eps, 1.0, 4001), np.geomspace(eps, 1.0, 2001)])
+    worst = max(abs(z * orc.cheb_poly(n, eps, z) - 1.0) for z in zs)
+    assert worst <= bound * (1 + 1e-9), (worst, bound)
+    # the bound is nearly attained: the polynomial is the minimax one
+    assert worst >= 0.5 * bound
+    assert all(orc.cheb_poly(n, eps, z) > 0 for z in np.linspace(0.0, 1.0, 501))
+
+
+def test_chebyshev_limit_cases(orc):
+    """n = 0 gives P = 1/m (m = (1+eps)/2), and P(z) -> 1/z on [eps, 1] as n
+    grows, at the exponential rate of the bound (Eq. (16))."""
+    assert abs(orc.cheb_poly(0, 0.3, 0.7) - 1 / 0.65) < 1e-15
+    eps = 0.01
+    for n in (20, 40, 60):
+        bound = 2 * ((1 - np.sqrt(eps)) / (1 + np.sqrt(eps))) ** (2 * n + 1)
+        for z in (0.05, 0.3, 0.9):
+            assert abs(orc.cheb_poly(n, eps, z) * z - 1) <= bound
+
+
+@pytest.mark.parametrize("d,nx,ntau", [(1, 8, 6), (3, 4, 4)])
+def test_chebyshev_apply_plane_waves(orc, d, nx, ntau):
+    """Uniform field: plane waves are eigenvectors of Q with eigenvalue
+    |lambda|^2, so P(Q/lam) v = P(|lambda|^2/lam) v element by element."""
+    A, sigma0, n, eps = 0.5, 0.4, 6, 0.02
+    c = 1.0 + A * np.sin(sigma0)
+    lat = orc.lattice(d, nx, ntau)
+    nsite = orc.nsites(lat)
+    L = orc.links(lat, A, np.full(nsite, sigma0))
+    lam = orc.gershgorin_lambda_max(d, H, A)
+    V = nx ** d
+    idx = np.arange(nsite)
+    tau = idx // V
+    s = idx % V
+    coords = [(s // nx ** j) % nx for j in range(d)]
+    ms = np.array([1] * d)
+    k = 2 * np.pi * ms / nx
+    w = np.pi * 3 / ntau
+    v = np.cos(sum(k[j] * coords[j] for j in range(d)) + w * tau)
+    # a real plane wave mixes w and -w; both have the same |lambda|
+    lam_m = 1.0 - 2.0 * H * np.sum(np.cos(k)) - c * np.exp(-1j * w)
+    ev = abs(lam_m) ** 2
+    got = orc.cheb_apply(lat, H, L, n, eps, lam, v)
+    assert np.max(np.abs(got - orc.cheb_poly(n, eps, ev / lam) * v)) < 1e-12
+
+
+def test_chebyshev_operator_is_spd_and_commutes(orc):
+    lat = orc.lattice(1, 5, 4)
+    nsite = orc.nsites(lat)
+    rng = np.random.default_rng(3)
+    L = orc.links(lat, 0.5, rng.uniform(-np.pi, np.pi, nsite))
+    lam = orc.gershgorin_lambda_max(1, H, 0.5)
+    P = np.stack([orc.cheb_apply(lat, H, L, 5, 0.01, lam, e) for e in np.eye(nsite)], axis=1)
+    Q = orc.dense(lat, H, L, "MTM")
+    assert np.max(np.linalg.eigvalsh(Q)) <= lam
+    assert np.allclose(P, P.T, atol=1e-12)
+    assert np.min(np.linalg.eigvalsh(0.5 * (P + P.T))) > 0
+    assert np.allclose(P @ Q, Q @ P, atol=1e-10)
+
+
+@pytest.mark.parametrize("d,nx,ntau", [(1, 8, 12), (3, 3, 4)])
+def test_pcg_matches_dense_lu(orc, d, nx, ntau):
+    lat = orc.lattice(d, nx, ntau)
+    nsite = orc.nsites(lat)
+    rng = np.random.default_rng(12)
+    L = orc.links(lat, 0.5, rng.uniform(-np.pi, np.pi, nsite))
+    b = rng.standard_normal(nsite)
+    lam = orc.gershgorin_lambda_max(d, H, 0.5)
+    x, st, it, relres = orc.pcg(lat, H, L, b, 4, 1e-3, lam)
+    assert st == 0 and relres <= 1e-10
+    Q = orc.dense(lat, H, L, "MTM")
+    x_lu = np.linalg.solve(Q, b)
+    assert np.linalg.norm(x - x_lu) <= 2 * np.linalg.cond(Q) * 1e-10 * np.linalg.norm(x_lu)
+    x0, st0, it0, _ = orc.cg(lat, H, L, b)
+    assert it < it0   # each PCG step applies Q 2n+1 times: far fewer steps
