@@ -91,6 +91,11 @@ typedef struct {
     uint64_t seed;         /* Philox key for all random draws of the context */
     int n_pf;              /* real pseudofermion components (2: weight (det M)^2) */
     uint64_t chain_id;     /* Philox counter word identifying the Markov chain */
+    int cheb_degree;       /* n of the Chebyshev preconditioner P(Q) of Sec. 4.2
+                              (degree 2n, Eqs. (13)-(15)); 0: plain CG.  HH_FP64
+                              contexts only. */
+    double cheb_eps;       /* its interval (eps, 1] for Q scaled by the Gershgorin
+                              bound (2 + 2 d h + A)^2 of its spectrum */
 } hh_params;
 
 typedef struct {
@@ -110,7 +115,8 @@ typedef struct {
 } hh_traj_info;
 
 /* Fill p with the defaults t = 1, dtau = 0.05, A = 0.5, FP64, cg_tol = 1e-10,
- * cg_maxit = 1000000, reliable_delta = 0.1, seed = 0, n_pf = 2, chain_id = 0. */
+ * cg_maxit = 1000000, reliable_delta = 0.1, seed = 0, n_pf = 2, chain_id = 0,
+ * cheb_degree = 0 (plain CG), cheb_eps = 1e-3. */
 void hh_default_params(hh_params *p);
 
 /* Create a context for one lattice and one Markov chain.  Allocates sigma,
@@ -149,7 +155,10 @@ int hh_init_field_random(hh_ctx *ctx, uint64_t seed);
 int hh_apply(hh_ctx *ctx, int op, const void *x, void *y, int dtype);
 
 /* Solve Q x_a = b_a for a = 0..n_rhs-1 by CG with x0 = 0 (Sec. 4.1) in the
- * context's precision, all right-hand sides in one persistent launch.
+ * context's precision, all right-hand sides in one persistent launch.  With
+ * cheb_degree = n > 0 the CG is preconditioned by the Chebyshev polynomial
+ * P(Q) of Sec. 4.2, applied as n real quadratic factors (2n applications of
+ * Q per step); info->iterations then counts preconditioned steps.
  * b, x: device pointers to n_rhs * N doubles.  info may be NULL (then the call
  * does not synchronise).  Returns HH_ENOCONV if a right-hand side missed
  * cg_tol within cg_maxit (x then holds the last iterate), HH_ETIMEOUT if a

@@ -35,7 +35,8 @@ class hh_params(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("dtau", ctypes.c_double), ("A", ctypes.c_double),
                 ("precision", ctypes.c_int), ("cg_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
                 ("reliable_delta", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("n_pf", ctypes.c_int), ("chain_id", ctypes.c_uint64)]
+                ("n_pf", ctypes.c_int), ("chain_id", ctypes.c_uint64),
+                ("cheb_degree", ctypes.c_int), ("cheb_eps", ctypes.c_double)]
 
 
 class hh_solve_info(ctypes.Structure):
@@ -186,7 +187,8 @@ class Context:
     """One lattice and one Markov chain on the current CUDA device."""
 
     def __init__(self, d, nx, ntau, t=1.0, dtau=0.05, A=0.5, precision=HH_FP64, cg_tol=1e-10,
-                 cg_maxit=1000000, reliable_delta=0.1, seed=0, n_pf=2, chain_id=0, stream=None):
+                 cg_maxit=1000000, reliable_delta=0.1, seed=0, n_pf=2, chain_id=0, stream=None,
+                 cheb_degree=0, cheb_eps=1e-3):
         L = load()
         self._lib = L
         self.lat = hh_lattice(d, nx, ntau)
@@ -196,6 +198,7 @@ class Context:
         p.precision = {"fp64": HH_FP64, "mixed": HH_MIXED}.get(precision, precision)
         p.cg_tol, p.cg_maxit, p.reliable_delta = cg_tol, cg_maxit, reliable_delta
         p.seed, p.n_pf, p.chain_id = seed, n_pf, chain_id
+        p.cheb_degree, p.cheb_eps = cheb_degree, cheb_eps
         self.params = p
         self.stream = stream
         h = ctypes.c_void_p()

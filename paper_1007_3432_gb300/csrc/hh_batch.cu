@@ -260,6 +260,7 @@ int validate(const hh_request &r)
     if (r.prm.precision != HH_FP64 && r.prm.precision != HH_MIXED) return HH_EINVAL;
     if (!(r.prm.cg_tol > 0.0) || r.prm.cg_maxit < 1) return HH_EINVAL;
     if (r.kind == HH_REQ_TRAJECTORY && r.n_md < 1) return HH_EINVAL;
+    if (r.prm.cheb_degree != 0) return HH_EINVAL;  // the batch engine runs plain CG
     return HH_OK;
 }
 

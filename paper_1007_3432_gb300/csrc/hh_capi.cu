@@ -1,6 +1,7 @@
 // C ABI of the library: contexts, solves and the HMC trajectory driver.
 // Every step of the path runs in the kernels of hh_kernels.cu and
 // hh_engine.cu; this file only allocates, validates, plans and enqueues.
+#include <cmath>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -139,6 +140,8 @@ struct hh_ctx {
     void *h_pinned;         // host readback buffer
     int *d_apply_err;       // set by a fused apply whose bounded wait ran out
     int nsm;
+    double *z, *u;          // Chebyshev preconditioner vectors (cap_rhs each), or null
+    double *d_cheb;         // its coefficient table
 };
 
 namespace {
@@ -169,6 +172,9 @@ void free_ctx(hh_ctx *c)
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->d_totals) cudaFree(c->d_totals);
     if (c->d_apply_err) cudaFree(c->d_apply_err);
+    if (c->z) cudaFree(c->z);
+    if (c->u) cudaFree(c->u);
+    if (c->d_cheb) cudaFree(c->d_cheb);
     if (c->ev) {
         for (int i = 0; i < c->ev_cap; ++i)
             if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -224,6 +230,10 @@ int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
         Y.maxit = c->prm.cg_maxit;
         Y.w = engine_group_width(c->lat.nx);
         Y.stall_window = ENGINE_STALL_WINDOW;
+        Y.cheb_n = c->prm.cheb_degree;
+        Y.cheb = c->d_cheb;
+        Y.z = c->z ? c->z + off : nullptr;
+        Y.u = c->u ? c->u + off : nullptr;
     }
     ntiles = (int)tiles.size();
     grid = ntiles < c->max_grid ? ntiles : c->max_grid;
@@ -329,6 +339,8 @@ void hh_default_params(hh_params *p)
     p->seed = 0;
     p->n_pf = 2;
     p->chain_id = 0;
+    p->cheb_degree = 0;
+    p->cheb_eps = 1e-3;
 }
 
 const char *hh_strerror(int code)
@@ -355,6 +367,9 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
     if (p->n_pf < 1 || p->n_pf > 64) return HH_EINVAL;
     if (p->precision != HH_FP64 && p->precision != HH_MIXED) return HH_EINVAL;
     if (!(p->cg_tol > 0.0) || p->cg_maxit < 1) return HH_EINVAL;
+    if (p->cheb_degree < 0 || p->cheb_degree > CHEB_MAX_DEGREE) return HH_EINVAL;
+    if (p->cheb_degree > 0 && (p->precision != HH_FP64 || !(p->cheb_eps > 0.0 && p->cheb_eps < 1.0)))
+        return HH_EINVAL;
     long long V = lat->d == 1 ? lat->nx : (long long)lat->nx * lat->nx * lat->nx;
     long long N = V * lat->ntau;
     if (N >= (1LL << 31) - 1024) return HH_EINVAL;
@@ -412,6 +427,32 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
     if (e == cudaSuccess) e = dalloc(&c->d_energy_part, (size_t)energy_blocks(c->N));
     if (e == cudaSuccess) e = dalloc(&c->d_energy_out, 4);
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_pinned, 4096);
+    if (e == cudaSuccess && p->cheb_degree > 0) {
+        e = dalloc(&c->z, nr);
+        if (e == cudaSuccess) e = dalloc(&c->u, nr);
+        if (e == cudaSuccess) e = dalloc(&c->d_cheb, (size_t)(2 + 3 * CHEB_MAX_DEGREE));
+        if (e == cudaSuccess) {
+            // Sec. 4.2: roots z_k = m (1 - cos th_k) - i sqrt(eps) sin th_k,
+            // th_k = 2 pi k / (2n + 1), m = (1 + eps)/2, for Q / lam with lam the
+            // Gershgorin bound of its spectrum: each row of M has the unit
+            // diagonal, 2d hops of h and one link of size <= 1 + A.
+            const double pi = 3.14159265358979323846;
+            const double h = p->t * p->dtau, eps = p->cheb_eps, m = 0.5 * (1.0 + eps);
+            const double rowsum = 2.0 + 2.0 * lat->d * fabs(h) + fabs(p->A);
+            const double lam = rowsum * rowsum;
+            std::vector<double> tab(2 + 3 * CHEB_MAX_DEGREE, 0.0);
+            tab[0] = 1.0 / lam;
+            tab[1] = 1.0 / m;
+            for (int k = 1; k <= p->cheb_degree; ++k) {
+                double th = 2.0 * pi * k / (2.0 * p->cheb_degree + 1.0);
+                double a = m * (1.0 - cos(th)), b = sqrt(eps) * sin(th);
+                tab[2 + 3 * (k - 1)] = a;
+                tab[3 + 3 * (k - 1)] = b * b;
+                tab[4 + 3 * (k - 1)] = 1.0 / ((m - a) * (m - a) + b * b);
+            }
+            e = cudaMemcpy(c->d_cheb, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
+        }
+    }
     if (e != cudaSuccess) {
         free_ctx(c);
         delete c;

@@ -107,6 +107,60 @@ __device__ double gloop_residual(const Geo g, const double h, const double *__re
     return acc;
 }
 
+// Preconditioner sub-step of an even index: u = (Q/lam) z - a z, from t = M z.
+template <int D, int W>
+__device__ void gloop_cheb_u(const Geo g, const double h, const double *__restrict__ L, const double *t,
+                             const double *z, double *u, const double invlam, const double a, int b, int e)
+{
+    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+        GroupNbr nb;
+        group_nbrs<D, W>(g, i, nb);
+        Vec<double, W> self = vld<double, W>(t + i);
+        Vec<double, W> hs = group_hop<D, double, W>(t, nb, self);
+        Vec<double, W> lk = vldg<double, W>(L + i);
+        Vec<double, W> nv = vld<double, W>(t + nb.next);
+        Vec<double, W> zv = vld<double, W>(z + i);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            double q = fma(lk.a[k], nv.a[k], fma(-h, hs.a[k], self.a[k]));
+            zv.a[k] = fma(q, invlam, -a * zv.a[k]);
+        }
+        vst<double, W>(u + i, zv);
+    }
+}
+
+// Odd index: z = ((Q/lam) u - a u + b2 z) * invq, from t = M u; after the last
+// factor also z *= scale and acc += r . z.
+template <int D, int W>
+__device__ double gloop_cheb_z(const Geo g, const double h, const double *__restrict__ L, const double *t,
+                               const double *u, double *z, const double *r, const double invlam,
+                               const double a, const double b2, const double invq, const double scale,
+                               bool dot, int b, int e)
+{
+    double acc = 0.0;
+    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+        GroupNbr nb;
+        group_nbrs<D, W>(g, i, nb);
+        Vec<double, W> self = vld<double, W>(t + i);
+        Vec<double, W> hs = group_hop<D, double, W>(t, nb, self);
+        Vec<double, W> lk = vldg<double, W>(L + i);
+        Vec<double, W> nv = vld<double, W>(t + nb.next);
+        Vec<double, W> uv = vld<double, W>(u + i);
+        Vec<double, W> zv = vld<double, W>(z + i);
+        Vec<double, W> rv;
+        if (dot) rv = vld<double, W>(r + i);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            double q = fma(lk.a[k], nv.a[k], fma(-h, hs.a[k], self.a[k]));
+            double v = fma(q, invlam, fma(-a, uv.a[k], b2 * zv.a[k]));
+            zv.a[k] = v * invq * scale;
+            if (dot) acc = fma(rv.a[k], zv.a[k], acc);
+        }
+        vst<double, W>(z + i, zv);
+    }
+    return acc;
+}
+
 // p = r + beta p (restart: p = r).
 template <typename T, int W>
 __device__ void gloop_direction(const T *r, T *p, const T beta, bool restart, int b, int e)
@@ -180,6 +234,7 @@ __device__ EngState decide(const EngSystem &Y, const EngState &P, double rr)
         S.stall = 0;
         S.fp64_steps = 0;
         S.since_ru = 0;
+        S.pre_j = 0;
         return S;
     case MODE_INIT:
         S.bb = rr;
@@ -199,7 +254,29 @@ __device__ EngState decide(const EngSystem &Y, const EngState &P, double rr)
         S.beta = 0.0;
         S.rr_alpha = rr;
         S.maxr2 = rr;
+        if (Y.cheb_n > 0) {
+            // PCG: first precondition r = b; beta = 0 marks the first step.
+            S.mode = MODE_PRE;
+            S.pre_j = 0;
+            S.rr_alpha = 0.0;
+        }
         return S;
+    case MODE_PRE: {
+        // rr is <r, z> after the last sub-step (reduced from part_tt).
+        if (P.pre_j + 1 < 2 * Y.cheb_n) {
+            S.pre_j = P.pre_j + 1;
+            return S;
+        }
+        if (!isfinite(rr) || rr <= 0.0) {
+            S.mode = MODE_DONE;
+            S.status = kNumericErr;
+            return S;
+        }
+        S.mode = MODE_CG;
+        S.beta = (P.rr_alpha > 0.0) ? rr / P.rr_alpha : 0.0;
+        S.rr_alpha = rr;
+        return S;
+    }
     case MODE_CG: {
         S.cg_steps = P.cg_steps + 1;
         if (P.prec == PREC_FP64) S.fp64_steps = P.fp64_steps + 1;
@@ -219,6 +296,11 @@ __device__ EngState decide(const EngSystem &Y, const EngState &P, double rr)
         }
         if (need) {
             S.mode = MODE_RU;
+            return S;
+        }
+        if (Y.cheb_n > 0) {
+            S.mode = MODE_PRE;
+            S.pre_j = 0;
             return S;
         }
         S.mode = MODE_CG;
@@ -252,6 +334,15 @@ __device__ EngState decide(const EngSystem &Y, const EngState &P, double rr)
         S.rr_alpha = rr;
         S.maxr2 = rr;
         S.since_ru = 0;
+        if (Y.cheb_n > 0) {
+            // PCG after residual replacement: precondition the new r; beta
+            // comes from <r, z> at the end of the sub-steps.
+            S.mode = MODE_PRE;
+            S.pre_j = 0;
+            S.rr_alpha = P.rr_alpha;
+            S.rr_ru = rr;
+            return S;
+        }
         if (P.prec == PREC_MIXED) {
             // A reliable update that did not halve the true residual norm
             // since the previous one (whether the FP32 residual fell below
@@ -280,16 +371,20 @@ __device__ EngState decide(const EngSystem &Y, const EngState &P, double rr)
 // Slot bodies for one tile (D and W fixed; mode and precision from the state).
 // ---------------------------------------------------------------------------
 struct TileCtl {
-    int mode, prec;
+    int mode, prec, pre_j, pad;
     double beta, alpha;
 };
 
 template <int D, int W>
 __device__ void slot1(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 {
-    if (c.mode == MODE_CG) {
+    if (c.mode == MODE_PRE) {
+        if (c.pre_j == 0) gloop_direction<double, W>(Y.r, Y.z, 0.0, true, T.begin, T.end);
+    } else if (c.mode == MODE_CG) {
         bool restart = (c.beta == 0.0);
-        if (c.prec == PREC_FP64)
+        if (Y.cheb_n > 0)
+            gloop_direction<double, W>(Y.z, Y.p, c.beta, restart, T.begin, T.end);
+        else if (c.prec == PREC_FP64)
             gloop_direction<double, W>(Y.r, Y.p, c.beta, restart, T.begin, T.end);
         else
             gloop_direction<float, W>(Y.r32, Y.p32, (float)c.beta, restart, T.begin, T.end);
@@ -311,6 +406,8 @@ __device__ double slot2(const EngSystem &Y, const TileCtl &c, const EngTile &T)
         return gloop_M<D, float, W>(Y.g, (float)Y.h, Y.L32, Y.p32, Y.t32, T.begin, T.end);
     }
     if (c.mode == MODE_RU) gloop_M<D, double, W>(Y.g, Y.h, Y.L64, Y.x, Y.t, T.begin, T.end);
+    if (c.mode == MODE_PRE)
+        gloop_M<D, double, W>(Y.g, Y.h, Y.L64, (c.pre_j & 1) ? Y.u : Y.z, Y.t, T.begin, T.end);
     return 0.0;
 }
 
@@ -327,6 +424,18 @@ __device__ double slot3(const EngSystem &Y, const TileCtl &c, const EngTile &T)
     if (c.mode == MODE_RU)
         return gloop_residual<D, W>(Y.g, Y.h, Y.L64, Y.t, Y.b, Y.r,
                                     Y.precision == PREC_MIXED ? Y.r32 : nullptr, T.begin, T.end);
+    if (c.mode == MODE_PRE) {
+        const int k = c.pre_j >> 1;
+        const double invlam = __ldg(Y.cheb), a = __ldg(Y.cheb + 2 + 3 * k);
+        if ((c.pre_j & 1) == 0) {
+            gloop_cheb_u<D, W>(Y.g, Y.h, Y.L64, Y.t, Y.z, Y.u, invlam, a, T.begin, T.end);
+            return 0.0;
+        }
+        const bool last = (c.pre_j == 2 * Y.cheb_n - 1);
+        const double b2 = __ldg(Y.cheb + 3 + 3 * k), invq = __ldg(Y.cheb + 4 + 3 * k);
+        return gloop_cheb_z<D, W>(Y.g, Y.h, Y.L64, Y.t, Y.u, Y.z, Y.r, invlam, a, b2, invq,
+                                  last ? __ldg(Y.cheb + 1) : 1.0, last, T.begin, T.end);
+    }
     if (c.mode == MODE_INIT) {
         double acc = 0.0;
         for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
@@ -457,6 +566,8 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                     double rr = 0.0;
                     if (pm == MODE_INIT || pm == MODE_CG || pm == MODE_RU)
                         rr = sum_partials(L.part_rr, Y.part0, Y.ntiles, &s_val);
+                    else if (pm == MODE_PRE && s_cache[slot].pre_j == 2 * Y.cheb_n - 1)
+                        rr = sum_partials(L.part_tt, Y.part0, Y.ntiles, &s_val);
                     if (threadIdx.x == 0) {
                         const EngState P = s_cache[slot];
                         const EngState S = decide(Y, P, rr);
@@ -467,6 +578,7 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                         s_cache[slot] = S;
                         s_tctl[slot].mode = S.mode;
                         s_tctl[slot].prec = S.prec;
+                        s_tctl[slot].pre_j = S.pre_j;
                         s_tctl[slot].beta = S.beta;
                         s_tctl[slot].alpha = 0.0;
                     }
@@ -497,6 +609,7 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                         s_cache[0] = S;
                         s_tctl[0].mode = S.mode;
                         s_tctl[0].prec = S.prec;
+                        s_tctl[0].pre_j = S.pre_j;
                         s_tctl[0].beta = S.beta;
                         s_tctl[0].alpha = 0.0;
                     }
@@ -527,6 +640,7 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                         s_cache[0] = S;
                         s_tctl[0].mode = S.mode;
                         s_tctl[0].prec = S.prec;
+                        s_tctl[0].pre_j = S.pre_j;
                         s_tctl[0].beta = S.beta;
                     }
                     __syncthreads();
@@ -542,6 +656,9 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                 if (c.mode == MODE_CG || c.mode == MODE_RU || c.mode == MODE_INIT) {
                     double tot = block_sum(v, s_red);
                     if (threadIdx.x == 0) L.part_rr[T.part] = tot;
+                } else if (c.mode == MODE_PRE && c.pre_j == 2 * Y.cheb_n - 1) {
+                    double tot = block_sum(v, s_red);
+                    if (threadIdx.x == 0) L.part_tt[T.part] = tot;
                 }
             }
         }
@@ -553,13 +670,13 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
 }  // namespace
 
 // The kernels: generic (any mix of dimensions) and the dimension-specialised
-// ones.  The d = 1 kernel is compiled to fit 64 registers (two blocks could
-// share an SM); measured on GB300, one block per SM with fewer grid-barrier
-// arrivals is faster, so every kind launches one block per SM by default.
+// ones, each launched with one 512-thread block per SM (measured on GB300:
+// two blocks per SM, at 64 registers, was slower than one block with fewer
+// grid-barrier arrivals).
 const void *kernel_of(int kind)
 {
     switch (kind) {
-    case ENGINE_D1: return (const void *)engine_kernel<1, 2>;
+    case ENGINE_D1: return (const void *)engine_kernel<1, 1>;
     case ENGINE_D3: return (const void *)engine_kernel<3, 1>;
     default: return (const void *)engine_kernel<0, 1>;
     }

@@ -27,7 +27,14 @@
 
 namespace hh {
 
-enum EngMode : int { MODE_NEW = 0, MODE_INIT = 1, MODE_CG = 2, MODE_RU = 3, MODE_DONE = 4 };
+enum EngMode : int { MODE_NEW = 0, MODE_INIT = 1, MODE_CG = 2, MODE_RU = 3, MODE_DONE = 4, MODE_PRE = 5 };
+
+// Chebyshev preconditioner (Sec. 4.2): z = P(Q/lam) r is applied as n real
+// quadratic factors ((Q/lam - a_k)^2 + b_k^2) / q_k, each two applications of
+// Q, i.e. 2n engine iterations in MODE_PRE (sub-step j: t = M v in slot 2, the
+// factor update in slot 3).  Coefficient table: [0] = 1/lam, [1] = 1/m with
+// m = (1 + eps)/2, then (a_k, b_k^2, 1/q_k) for k = 1..n.
+constexpr int CHEB_MAX_DEGREE = 64;
 
 enum EngPrecision : int { PREC_FP64 = 0, PREC_MIXED = 1 };
 
@@ -51,7 +58,9 @@ struct EngSystem {
     int maxit;
     int w;                            // x sites per thread group: 4, 2 or 1 (divides Nx)
     int stall_window;                 // mixed: forced RU after this many FP32 steps without one
-    int pad;
+    int cheb_n;                       // Chebyshev preconditioner degree n (0: plain CG; FP64 only)
+    const double *cheb;               // coefficient table (see CHEB_MAX_DEGREE)
+    double *z, *u;                    // FP64 preconditioner vectors (when cheb_n > 0)
 };
 
 // FP32 steps after which a mixed system takes a reliable update even if its
@@ -84,7 +93,7 @@ struct EngState {
     int stall;          // consecutive reliable updates without progress
     int fp64_steps;     // CG steps run in FP64
     int since_ru;       // CG steps since the last RU
-    int pad;
+    int pre_j;          // MODE_PRE sub-step, 0 .. 2 cheb_n - 1
 };
 
 struct EngTile {

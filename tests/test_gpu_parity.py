@@ -289,3 +289,49 @@ def test_checkpoint_resume_is_bit_identical(hh):
         ctx.get_field(resumed)
     assert np.array_equal(full, resumed)
     assert [i["dH"] for i in infos] == [first["dH"]] + [i["dH"] for i in rest]
+
+
+@pytest.mark.parametrize("d,nx,ntau,n,eps", [(1, 32, 64, 4, 1e-3), (3, 6, 8, 3, 1e-2), (1, 20, 40, 8, 1e-4)])
+def test_chebyshev_pcg_matches_oracle(hh, d, nx, ntau, n, eps):
+    """Preconditioned CG with the Chebyshev polynomial of Sec. 4.2: true
+    residual 1e-10, the oracle's solution, and the oracle's step count (the
+    two run the same algorithm; rounding may move the stop by a step or two)."""
+    lat = oracle.lattice(d, nx, ntau)
+    nsite = oracle.nsites(lat)
+    sigma = workloads.sigma_field(nsite, seed=900 + nx)
+    L = oracle.links(lat, A, sigma)
+    b = np.stack([workloads.source(nsite, seed=901, rhs=a) for a in range(2)])
+    lam = oracle.gershgorin_lambda_max(d, H, A)
+    with hh.Context(d, nx, ntau, cheb_degree=n, cheb_eps=eps) as ctx:
+        ctx.set_field(dev(sigma))
+        x = torch.zeros(2, nsite, dtype=torch.float64, device="cuda")
+        rc, info = ctx.solve(dev(b), x, 2)
+        xg = x.cpu().numpy()
+    assert rc == 0 and info["converged"] == 1 and info["true_relres"] <= 1e-10
+    its = []
+    for a in range(2):
+        res = b[a] - oracle.apply_MTM(lat, H, L, xg[a])
+        assert np.linalg.norm(res) <= 1.0001e-10 * np.linalg.norm(b[a])
+        x_ref, st, it, rr = oracle.pcg(lat, H, L, b[a], n, eps, lam)
+        assert st == 0
+        assert np.linalg.norm(xg[a] - x_ref) <= 1e-4 * np.linalg.norm(x_ref)
+        its.append(it)
+    assert abs(info["iterations"] - max(its)) <= 2 + 0.03 * max(its), (info, its)
+
+
+def test_chebyshev_pcg_trajectory_matches_plain_cg(hh):
+    d, nx, ntau = 1, 16, 32
+    n = nx * ntau
+    sigma = workloads.sigma_field(n, seed=61)
+    out = []
+    for deg in (0, 4):
+        with hh.Context(d, nx, ntau, seed=61, n_pf=2, cheb_degree=deg, cheb_eps=1e-3) as ctx:
+            ctx.set_field(dev(sigma))
+            out.append(ctx.trajectory(4, 0.1, 0))
+    assert abs(out[0]["dH"] - out[1]["dH"]) <= 1e-6
+    assert out[0]["accepted"] == out[1]["accepted"]
+
+
+def test_chebyshev_rejected_for_mixed_precision(hh):
+    with pytest.raises(hh.HHError):
+        hh.Context(1, 8, 8, precision="mixed", cheb_degree=2)
