@@ -132,8 +132,8 @@ struct Pending {
 
 // Device arrays of one slot, carved from the arena.
 struct SlotMem {
-    double *sigma, *sigma0, *L64, *pi, *tmp, *chi, *x, *r, *p, *t, *epart;
-    float *L32, *r32, *p32, *t32, *x32;
+    double *sigma, *sigma0, *L64, *pi, *tmp, *chi, *x, *r, *p, *p2, *t, *epart;
+    float *L32, *r32, *p32, *p32b, *t32, *x32;
     HmcScalars *sc;
 };
 
@@ -156,10 +156,12 @@ size_t slot_bytes(long long N, int nrhs, SlotMem *m, char *base)
     p = take(nrhs * N * d); if (m) m->x = (double *)p;
     p = take(nrhs * N * d); if (m) m->r = (double *)p;
     p = take(nrhs * N * d); if (m) m->p = (double *)p;
+    p = take(nrhs * N * d); if (m) m->p2 = (double *)p;
     p = take(nrhs * N * d); if (m) m->t = (double *)p;
     p = take(N * f); if (m) m->L32 = (float *)p;
     p = take(nrhs * N * f); if (m) m->r32 = (float *)p;
     p = take(nrhs * N * f); if (m) m->p32 = (float *)p;
+    p = take(nrhs * N * f); if (m) m->p32b = (float *)p;
     p = take(nrhs * N * f); if (m) m->t32 = (float *)p;
     p = take(nrhs * N * f); if (m) m->x32 = (float *)p;
     p = take(sizeof(HmcScalars)); if (m) m->sc = (HmcScalars *)p;
@@ -215,6 +217,7 @@ struct hh_batch {
     int max_sys = 0, ntiles = 0;
     int grid_of[4] = {0, 0, 0, 0};  // engine grid per kernel kind
     int kind = ENGINE_GENERIC;      // kernel of the current plan
+    int two_slot_of[4] = {0, 0, 0, 0};  // engine form per kernel kind
     int graph_kind = -1;
     long long k = 0;
     bool plan_dirty = true;
@@ -410,9 +413,11 @@ int build_plan(hh_batch *b)
             Y.x = S.m.x + o;
             Y.r = S.m.r + o;
             Y.p = S.m.p + o;
+            Y.p2 = S.m.p2 + o;
             Y.t = S.m.t + o;
             Y.r32 = S.m.r32 + o;
             Y.p32 = S.m.p32 + o;
+            Y.p32b = S.m.p32b + o;
             Y.t32 = S.m.t32 + o;
             Y.x32 = S.m.x32 + o;
             Y.precision = S.req.prm.precision == HH_MIXED ? PREC_MIXED : PREC_FP64;
@@ -473,6 +478,8 @@ EngLaunch make_launch(hh_batch *b)
     L.nsys = b->max_sys;
     L.ntiles = b->ntiles;
     L.max_iters = b->cfg.chunk_iters;
+    L.two_slot = b->two_slot_of[b->kind];
+    L.pad = 0;
     return L;
 }
 
@@ -733,6 +740,7 @@ int hh_batch_create(hh_batch **out, const hh_batch_config *cfg, void *cuda_strea
     b->grid_of[ENGINE_GENERIC] = engine_default_grid(ENGINE_GENERIC);
     b->grid_of[ENGINE_D1] = engine_default_grid(ENGINE_D1);
     b->grid_of[ENGINE_D3] = engine_default_grid(ENGINE_D3);
+    for (int k : {ENGINE_GENERIC, ENGINE_D1, ENGINE_D3}) b->two_slot_of[k] = engine_two_slot(k);
     cudaError_t e = (b->grid_of[0] > 0 && b->grid_of[1] > 0 && b->grid_of[3] > 0) ? cudaSuccess
                                                                                  : cudaErrorUnknown;
     if (e == cudaSuccess) e = b->arena.init(cfg->hbm_budget_bytes);

@@ -116,8 +116,9 @@ struct hh_ctx {
     double *sigma, *sigma0, *L64, *pi, *chi, *xsol, *tmp, *F;
     float *L32, *tmp32a, *tmp32b;
     // CG workspace (cap_rhs vectors each)
-    double *r, *p, *t;
-    float *r32, *p32, *t32, *x32;
+    double *r, *p, *t, *p2;
+    float *r32, *p32, *t32, *x32, *p32b;
+    int two_slot;           // engine launches run the two-slot form
     // engine
     EngSystem *d_sys;
     EngState *d_state[2];
@@ -163,7 +164,7 @@ cudaError_t dalloc(T **p, size_t n)
 void free_ctx(hh_ctx *c)
 {
     void *ptrs[] = {c->sigma, c->sigma0, c->L64, c->pi, c->chi, c->xsol, c->tmp, c->F, c->L32,
-                    c->tmp32a, c->tmp32b, c->r, c->p, c->t, c->r32, c->p32, c->t32, c->x32,
+                    c->tmp32a, c->tmp32b, c->r, c->p, c->p2, c->t, c->r32, c->p32, c->p32b, c->t32, c->x32,
                     c->d_sys, c->d_state[0], c->d_state[1], c->d_tiles, c->d_part_tt,
                     c->d_part_rr, c->d_ctl, c->d_stats, c->d_sc, c->d_energy_part,
                     c->d_energy_out};
@@ -207,9 +208,11 @@ int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
         size_t off = (size_t)a * c->N;
         Y.r = c->r + off;
         Y.p = c->p + off;
+        Y.p2 = c->p2 + off;
         Y.t = c->t + off;
         Y.r32 = c->r32 + off;
         Y.p32 = c->p32 + off;
+        Y.p32b = c->p32b + off;
         Y.t32 = c->t32 + off;
         Y.x32 = c->x32 + off;
         Y.tile0 = (int)tiles.size();
@@ -269,9 +272,12 @@ int run_engine(hh_ctx *c)
     L.ctl = c->d_ctl;
     L.nsys = P.nsys;
     L.ntiles = P.ntiles;
-    // Each CG step is one engine iteration, each true-residual check one more;
-    // the cap is a safety bound well above maxit.
-    L.max_iters = 3LL * (long long)c->prm.cg_maxit + 64;
+    // Each CG step is one engine iteration, each true-residual check one more,
+    // and with the Chebyshev preconditioner each of them is followed by 2n
+    // sub-steps; the cap is a safety bound well above maxit.
+    L.max_iters = (2LL * c->prm.cheb_degree + 1) * (3LL * (long long)c->prm.cg_maxit + 64);
+    L.two_slot = c->two_slot;
+    L.pad = 0;
     bool rec = c->profile && c->ev_used + 2 <= c->ev_cap;
     if (rec) HH_TRY(cudaEventRecord(c->ev[c->ev_used], c->stream));
     HH_TRY(engine_launch(L, P.grid, ENGINE_BLOCK, c->stream, c->kind));
@@ -385,6 +391,7 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
     c->cap_rhs = p->n_pf > 4 ? p->n_pf : 4;
     c->timeout_ns = 5LL * 1000 * 1000 * 1000;
     c->kind = lat->d == 1 ? ENGINE_D1 : ENGINE_D3;
+    c->two_slot = engine_two_slot(c->kind);
     int max_grid = engine_default_grid(c->kind);
     if (max_grid <= 0) {
         delete c;
@@ -408,6 +415,8 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
     if (e == cudaSuccess) e = dalloc(&c->xsol, nr);
     if (e == cudaSuccess) e = dalloc(&c->r, nr);
     if (e == cudaSuccess) e = dalloc(&c->p, nr);
+    if (e == cudaSuccess) e = dalloc(&c->p2, nr);
+    if (e == cudaSuccess) e = dalloc(&c->p32b, nr);
     if (e == cudaSuccess) e = dalloc(&c->t, nr);
     if (e == cudaSuccess) e = dalloc(&c->r32, nr);
     if (e == cudaSuccess) e = dalloc(&c->p32, nr);

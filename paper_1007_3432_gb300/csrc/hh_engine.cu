@@ -161,6 +161,99 @@ __device__ double gloop_cheb_z(const Geo g, const double h, const double *__rest
     return acc;
 }
 
+// Two-slot CG step: p_new = src + beta p_old on the tile's sites (stored), and
+// t = M p_new with p_new recomputed at the neighbour sites from src and p_old,
+// which are final there; acc += t^2.  The recomputed values are bitwise the
+// ones their owners store (the same fma on the same inputs).
+template <int D, typename T, int W>
+__device__ double gloop_pM(const Geo g, const T h, const T *__restrict__ L, const T *src, const T *pold,
+                           T *pnew, T *t, const T beta, bool restart, int b, int e)
+{
+    T acc = T(0);
+    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+        GroupNbr nb;
+        group_nbrs<D, W>(g, i, nb);
+        auto pn_at = [&](int j) -> T {
+            const T sv = src[j];
+            return restart ? sv : fma(beta, pold[j], sv);
+        };
+        auto pn_row = [&](int j) -> Vec<T, W> {
+            Vec<T, W> sv = vld<T, W>(src + j);
+            if (!restart) {
+                const Vec<T, W> q = vld<T, W>(pold + j);
+#pragma unroll
+                for (int u = 0; u < W; ++u) sv.a[u] = fma(beta, q.a[u], sv.a[u]);
+            }
+            return sv;
+        };
+        const Vec<T, W> self = pn_row(i);
+        vst<T, W>(pnew + i, self);
+        const T vl = pn_at(nb.left), vr = pn_at(nb.right);
+        Vec<T, W> yp, ym, zp, zm;
+        if (D == 3) {
+            yp = pn_row(nb.yp);
+            ym = pn_row(nb.ym);
+            zp = pn_row(nb.zp);
+            zm = pn_row(nb.zm);
+        }
+        const Vec<T, W> pv = pn_row(nb.prev);
+        const Vec<T, W> lk = vldg<T, W>(L + nb.prev);
+        Vec<T, W> out;
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            T xr = (u == W - 1) ? vr : self.a[u + 1 < W ? u + 1 : u];
+            T xl = (u == 0) ? vl : self.a[u > 0 ? u - 1 : 0];
+            T hsum = xr + xl;
+            if (D == 3) hsum += (yp.a[u] + ym.a[u]) + (zp.a[u] + zm.a[u]);
+            out.a[u] = fma(lk.a[u], pv.a[u], fma(-h, hsum, self.a[u]));
+            acc = fma(out.a[u], out.a[u], acc);
+        }
+        vst<T, W>(t + i, out);
+    }
+    return (double)acc;
+}
+
+// Two-slot reliable update, first half: t64 = M (x64 + x32) with the sum
+// formed at every site read (x64 and x32 are only written in slot 3).
+template <int D, int W>
+__device__ void gloop_accM(const Geo g, const double h, const double *__restrict__ L, const double *x,
+                           const float *x32, double *t, int b, int e)
+{
+    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+        GroupNbr nb;
+        group_nbrs<D, W>(g, i, nb);
+        auto xs_at = [&](int j) -> double { return x[j] + (double)x32[j]; };
+        auto xs_row = [&](int j) -> Vec<double, W> {
+            Vec<double, W> a = vld<double, W>(x + j);
+            const Vec<float, W> c = vld<float, W>(x32 + j);
+#pragma unroll
+            for (int u = 0; u < W; ++u) a.a[u] += (double)c.a[u];
+            return a;
+        };
+        const Vec<double, W> self = xs_row(i);
+        const double vl = xs_at(nb.left), vr = xs_at(nb.right);
+        Vec<double, W> yp, ym, zp, zm;
+        if (D == 3) {
+            yp = xs_row(nb.yp);
+            ym = xs_row(nb.ym);
+            zp = xs_row(nb.zp);
+            zm = xs_row(nb.zm);
+        }
+        const Vec<double, W> pv = xs_row(nb.prev);
+        const Vec<double, W> lk = vldg<double, W>(L + nb.prev);
+        Vec<double, W> out;
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            double xr = (u == W - 1) ? vr : self.a[u + 1 < W ? u + 1 : u];
+            double xl = (u == 0) ? vl : self.a[u > 0 ? u - 1 : 0];
+            double hsum = xr + xl;
+            if (D == 3) hsum += (yp.a[u] + ym.a[u]) + (zp.a[u] + zm.a[u]);
+            out.a[u] = fma(lk.a[u], pv.a[u], fma(-h, hsum, self.a[u]));
+        }
+        vst<double, W>(t + i, out);
+    }
+}
+
 // p = r + beta p (restart: p = r).
 template <typename T, int W>
 __device__ void gloop_direction(const T *r, T *p, const T beta, bool restart, int b, int e)
@@ -215,8 +308,9 @@ __device__ double sum_partials(const double *part, int t0, int n, double *s_val)
     return r;
 }
 
-// Next mode of a system from its previous state and the |r|^2 reduced from the
-// previous iteration's slot 3.  Pure function of its inputs: all blocks agree.
+// Next mode of a system from its previous state and the |r|^2 (or, after the
+// last preconditioner sub-step, <r, z>) reduced from the previous iteration's
+// slot 3.  Pure function of its inputs: all blocks agree.
 __device__ EngState decide(const EngSystem &Y, const EngState &P, double rr)
 {
     EngState S = P;
@@ -262,7 +356,7 @@ __device__ EngState decide(const EngSystem &Y, const EngState &P, double rr)
         }
         return S;
     case MODE_PRE: {
-        // rr is <r, z> after the last sub-step (reduced from part_tt).
+        // rr is <r, z> after the last sub-step (reduced from part_rr).
         if (P.pre_j + 1 < 2 * Y.cheb_n) {
             S.pre_j = P.pre_j + 1;
             return S;
@@ -371,9 +465,51 @@ __device__ EngState decide(const EngSystem &Y, const EngState &P, double rr)
 // Slot bodies for one tile (D and W fixed; mode and precision from the state).
 // ---------------------------------------------------------------------------
 struct TileCtl {
-    int mode, prec, pre_j, pad;
+    int mode, prec, pre_j, two;    // two: the launch runs the two-slot form
+    int pold, pnew, pad0, pad1;    // p buffers holding the previous / new direction
     double beta, alpha;
 };
+
+// Tile controls of a system in state S.  Three-slot form: the direction is
+// updated in place in buffer S.pbuf.  Two-slot form: each CG step writes the
+// new direction to S.pbuf and reads the previous one from the other buffer.
+__device__ __forceinline__ TileCtl make_ctl(const EngState &S, int two)
+{
+    TileCtl c;
+    c.mode = S.mode;
+    c.prec = S.prec;
+    c.pre_j = S.pre_j;
+    c.two = two;
+    c.pnew = S.pbuf;
+    c.pold = two ? (S.pbuf ^ 1) : S.pbuf;
+    c.pad0 = c.pad1 = 0;
+    c.beta = S.beta;
+    c.alpha = 0.0;
+    return c;
+}
+
+__device__ __forceinline__ double *pbuf64(const EngSystem &Y, int k)
+{
+    return k ? Y.p2 : Y.p;
+}
+
+__device__ __forceinline__ float *pbuf32(const EngSystem &Y, int k)
+{
+    return k ? Y.p32b : Y.p32;
+}
+
+// r = b (and r32 = b for a mixed system); returns this thread's |b|^2.
+__device__ double init_residual(const EngSystem &Y, const EngTile &T)
+{
+    double acc = 0.0;
+    for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
+        double bi = __ldg(Y.b + i);
+        Y.r[i] = bi;
+        if (Y.precision == PREC_MIXED) Y.r32[i] = (float)bi;
+        acc = fma(bi, bi, acc);
+    }
+    return acc;
+}
 
 template <int D, int W>
 __device__ void slot1(const EngSystem &Y, const TileCtl &c, const EngTile &T)
@@ -383,13 +519,13 @@ __device__ void slot1(const EngSystem &Y, const TileCtl &c, const EngTile &T)
     } else if (c.mode == MODE_CG) {
         bool restart = (c.beta == 0.0);
         if (Y.cheb_n > 0)
-            gloop_direction<double, W>(Y.z, Y.p, c.beta, restart, T.begin, T.end);
+            gloop_direction<double, W>(Y.z, pbuf64(Y, c.pnew), c.beta, restart, T.begin, T.end);
         else if (c.prec == PREC_FP64)
-            gloop_direction<double, W>(Y.r, Y.p, c.beta, restart, T.begin, T.end);
+            gloop_direction<double, W>(Y.r, pbuf64(Y, c.pnew), c.beta, restart, T.begin, T.end);
         else
-            gloop_direction<float, W>(Y.r32, Y.p32, (float)c.beta, restart, T.begin, T.end);
+            gloop_direction<float, W>(Y.r32, pbuf32(Y, c.pnew), (float)c.beta, restart, T.begin, T.end);
     } else if (c.mode == MODE_RU) {
-        if (c.prec == PREC_MIXED) gloop_accumulate<W>(Y.x, Y.x32, T.begin, T.end);
+        if (c.prec == PREC_MIXED && !c.two) gloop_accumulate<W>(Y.x, Y.x32, T.begin, T.end);
     } else if (c.mode == MODE_INIT) {
         for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) Y.x[i] = 0.0;
         if (Y.precision == PREC_MIXED)
@@ -402,8 +538,8 @@ __device__ double slot2(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 {
     if (c.mode == MODE_CG) {
         if (c.prec == PREC_FP64)
-            return gloop_M<D, double, W>(Y.g, Y.h, Y.L64, Y.p, Y.t, T.begin, T.end);
-        return gloop_M<D, float, W>(Y.g, (float)Y.h, Y.L32, Y.p32, Y.t32, T.begin, T.end);
+            return gloop_M<D, double, W>(Y.g, Y.h, Y.L64, pbuf64(Y, c.pnew), Y.t, T.begin, T.end);
+        return gloop_M<D, float, W>(Y.g, (float)Y.h, Y.L32, pbuf32(Y, c.pnew), Y.t32, T.begin, T.end);
     }
     if (c.mode == MODE_RU) gloop_M<D, double, W>(Y.g, Y.h, Y.L64, Y.x, Y.t, T.begin, T.end);
     if (c.mode == MODE_PRE)
@@ -416,14 +552,18 @@ __device__ double slot3(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 {
     if (c.mode == MODE_CG) {
         if (c.prec == PREC_FP64)
-            return gloop_update<D, double, W>(Y.g, Y.h, Y.L64, Y.t, Y.x, Y.p, Y.r, c.alpha, T.begin,
-                                              T.end);
-        return gloop_update<D, float, W>(Y.g, (float)Y.h, Y.L32, Y.t32, Y.x32, Y.p32, Y.r32,
+            return gloop_update<D, double, W>(Y.g, Y.h, Y.L64, Y.t, Y.x, pbuf64(Y, c.pnew), Y.r, c.alpha,
+                                              T.begin, T.end);
+        return gloop_update<D, float, W>(Y.g, (float)Y.h, Y.L32, Y.t32, Y.x32, pbuf32(Y, c.pnew), Y.r32,
                                          (float)c.alpha, T.begin, T.end);
     }
-    if (c.mode == MODE_RU)
+    if (c.mode == MODE_RU) {
+        // Two-slot form: the mixed reliable update accumulates here, after
+        // every block has read x64 + x32 for t64 in the previous slot.
+        if (c.two && c.prec == PREC_MIXED) gloop_accumulate<W>(Y.x, Y.x32, T.begin, T.end);
         return gloop_residual<D, W>(Y.g, Y.h, Y.L64, Y.t, Y.b, Y.r,
                                     Y.precision == PREC_MIXED ? Y.r32 : nullptr, T.begin, T.end);
+    }
     if (c.mode == MODE_PRE) {
         const int k = c.pre_j >> 1;
         const double invlam = __ldg(Y.cheb), a = __ldg(Y.cheb + 2 + 3 * k);
@@ -436,16 +576,41 @@ __device__ double slot3(const EngSystem &Y, const TileCtl &c, const EngTile &T)
         return gloop_cheb_z<D, W>(Y.g, Y.h, Y.L64, Y.t, Y.u, Y.z, Y.r, invlam, a, b2, invq,
                                   last ? __ldg(Y.cheb + 1) : 1.0, last, T.begin, T.end);
     }
-    if (c.mode == MODE_INIT) {
-        double acc = 0.0;
-        for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
-            double bi = __ldg(Y.b + i);
-            Y.r[i] = bi;
-            if (Y.precision == PREC_MIXED) Y.r32[i] = (float)bi;
-            acc = fma(bi, bi, acc);
-        }
-        return acc;
+    if (c.mode == MODE_INIT) return init_residual(Y, T);
+    return 0.0;
+}
+
+// Two-slot first slot: slot 1 folded into slot 2.  Returns this thread's
+// |t|^2 partial for a CG step (0 otherwise).
+template <int D, int W>
+__device__ double slotA(const EngSystem &Y, const TileCtl &c, const EngTile &T)
+{
+    if (c.mode == MODE_CG) {
+        const bool restart = (c.beta == 0.0);
+        if (Y.cheb_n > 0)
+            return gloop_pM<D, double, W>(Y.g, Y.h, Y.L64, Y.z, pbuf64(Y, c.pold), pbuf64(Y, c.pnew), Y.t,
+                                          c.beta, restart, T.begin, T.end);
+        if (c.prec == PREC_FP64)
+            return gloop_pM<D, double, W>(Y.g, Y.h, Y.L64, Y.r, pbuf64(Y, c.pold), pbuf64(Y, c.pnew), Y.t,
+                                          c.beta, restart, T.begin, T.end);
+        return gloop_pM<D, float, W>(Y.g, (float)Y.h, Y.L32, Y.r32, pbuf32(Y, c.pold), pbuf32(Y, c.pnew),
+                                     Y.t32, (float)c.beta, restart, T.begin, T.end);
     }
+    if (c.mode == MODE_RU) {
+        if (c.prec == PREC_MIXED)
+            gloop_accM<D, W>(Y.g, Y.h, Y.L64, Y.x, Y.x32, Y.t, T.begin, T.end);
+        else
+            gloop_M<D, double, W>(Y.g, Y.h, Y.L64, Y.x, Y.t, T.begin, T.end);
+        return 0.0;
+    }
+    if (c.mode == MODE_PRE) {
+        if (c.pre_j == 0)
+            gloop_pM<D, double, W>(Y.g, Y.h, Y.L64, Y.r, Y.r, Y.z, Y.t, 0.0, true, T.begin, T.end);
+        else
+            gloop_M<D, double, W>(Y.g, Y.h, Y.L64, (c.pre_j & 1) ? Y.u : Y.z, Y.t, T.begin, T.end);
+        return 0.0;
+    }
+    if (c.mode == MODE_INIT) slot1<D, W>(Y, c, T);
     return 0.0;
 }
 
@@ -459,6 +624,8 @@ __device__ double run_slot(const EngSystem &Y, const TileCtl &c, const EngTile &
         return 0.0;                                          \
     } else if (SLOT == 2) {                                  \
         return slot2<D, W>(Y, c, T);                         \
+    } else if (SLOT == 4) {                                  \
+        return slotA<D, W>(Y, c, T);                         \
     } else {                                                 \
         return slot3<D, W>(Y, c, T);                         \
     }
@@ -545,11 +712,13 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
         __syncthreads();
     }
 
+    const int two = L.two_slot;
     for (long long it = 0; it < L.max_iters; ++it, ++k) {
         EngState *cur = (k & 1) ? L.state[1] : L.state[0];
         EngState *nxt = (k & 1) ? L.state[0] : L.state[1];
 
-        // ---- slot 1: decide, then direction update / reliable-update accumulate ----
+        // ---- first slot: decide; then slot 1 (three-slot form) or slot 1
+        //      fused with slot 2 (two-slot form) ----
         {
             int last = -1, j = 0;
             for (int tile = blockIdx.x; tile < L.ntiles; tile += G, ++j) {
@@ -564,29 +733,33 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                     __syncthreads();
                     const int pm = s_cache[slot].mode;
                     double rr = 0.0;
-                    if (pm == MODE_INIT || pm == MODE_CG || pm == MODE_RU)
+                    if (pm == MODE_INIT || pm == MODE_CG || pm == MODE_RU ||
+                        (pm == MODE_PRE && s_cache[slot].pre_j == 2 * Y.cheb_n - 1))
                         rr = sum_partials(L.part_rr, Y.part0, Y.ntiles, &s_val);
-                    else if (pm == MODE_PRE && s_cache[slot].pre_j == 2 * Y.cheb_n - 1)
-                        rr = sum_partials(L.part_tt, Y.part0, Y.ntiles, &s_val);
                     if (threadIdx.x == 0) {
                         const EngState P = s_cache[slot];
-                        const EngState S = decide(Y, P, rr);
+                        EngState S = decide(Y, P, rr);
+                        if (two && S.mode == MODE_CG) S.pbuf = P.pbuf ^ 1;
                         if ((int)blockIdx.x == Y.owner) {
                             nxt[T.sys] = S;
                             if (S.mode == MODE_DONE && P.mode != MODE_DONE) atomicSub(&ctl->active, 1);
                         }
                         s_cache[slot] = S;
-                        s_tctl[slot].mode = S.mode;
-                        s_tctl[slot].prec = S.prec;
-                        s_tctl[slot].pre_j = S.pre_j;
-                        s_tctl[slot].beta = S.beta;
-                        s_tctl[slot].alpha = 0.0;
+                        s_tctl[slot] = make_ctl(S, two);
                     }
                     __syncthreads();
                     last = T.sys;
                 }
                 const TileCtl c = s_tctl[slot];
-                run_slot<1, FD>(Y, c, T);
+                if (two) {
+                    double v = run_slot<4, FD>(Y, c, T);
+                    if (c.mode == MODE_CG) {
+                        double tot = block_sum(v, s_red);
+                        if (threadIdx.x == 0) L.part_tt[T.part] = tot;
+                    }
+                } else {
+                    run_slot<1, FD>(Y, c, T);
+                }
             }
         }
         if (!grid_barrier(ctl, G, target, &s_flag)) return;
@@ -595,8 +768,8 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
             return;
         }
 
-        // ---- slot 2 ----
-        {
+        // ---- slot 2 (three-slot form only) ----
+        if (!two) {
             int last = -1, j = 0;
             for (int tile = blockIdx.x; tile < L.ntiles; tile += G, ++j) {
                 const int slot = cached ? s_slot[j] : 0;
@@ -607,11 +780,7 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                     if (threadIdx.x == 0) {
                         const EngState S = nxt[T.sys];
                         s_cache[0] = S;
-                        s_tctl[0].mode = S.mode;
-                        s_tctl[0].prec = S.prec;
-                        s_tctl[0].pre_j = S.pre_j;
-                        s_tctl[0].beta = S.beta;
-                        s_tctl[0].alpha = 0.0;
+                        s_tctl[0] = make_ctl(S, two);
                     }
                     __syncthreads();
                     last = T.sys;
@@ -623,8 +792,8 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                     if (threadIdx.x == 0) L.part_tt[T.part] = tot;
                 }
             }
+            if (!grid_barrier(ctl, G, target, &s_flag)) return;
         }
-        if (!grid_barrier(ctl, G, target, &s_flag)) return;
 
         // ---- slot 3 ----
         {
@@ -638,10 +807,7 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                     if (!cached && threadIdx.x == 0) {
                         const EngState S = nxt[T.sys];
                         s_cache[0] = S;
-                        s_tctl[0].mode = S.mode;
-                        s_tctl[0].prec = S.prec;
-                        s_tctl[0].pre_j = S.pre_j;
-                        s_tctl[0].beta = S.beta;
+                        s_tctl[0] = make_ctl(S, two);
                     }
                     __syncthreads();
                     if (s_tctl[slot].mode == MODE_CG) {
@@ -653,12 +819,12 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                 }
                 const TileCtl c = s_tctl[slot];
                 double v = run_slot<3, FD>(Y, c, T);
-                if (c.mode == MODE_CG || c.mode == MODE_RU || c.mode == MODE_INIT) {
+                // |r|^2 (CG, RU, INIT) or <r, z> after the last
+                // preconditioner sub-step: both feed the next decide().
+                if (c.mode == MODE_CG || c.mode == MODE_RU || c.mode == MODE_INIT ||
+                    (c.mode == MODE_PRE && c.pre_j == 2 * Y.cheb_n - 1)) {
                     double tot = block_sum(v, s_red);
                     if (threadIdx.x == 0) L.part_rr[T.part] = tot;
-                } else if (c.mode == MODE_PRE && c.pre_j == 2 * Y.cheb_n - 1) {
-                    double tot = block_sum(v, s_red);
-                    if (threadIdx.x == 0) L.part_tt[T.part] = tot;
                 }
             }
         }
@@ -702,6 +868,17 @@ int engine_max_grid(int block, int kind)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel_of(kind), block, 0) != cudaSuccess)
         return 0;
     return per * nsm;
+}
+
+int engine_two_slot(int kind)
+{
+    const char *env = getenv("HH_ENGINE_SLOTS");
+    if (env && atoi(env) == 3) return 0;
+    if (env && atoi(env) == 2) return 1;
+    // Measured on GB300: the fused form is faster for d = 1 (its neighbour
+    // recomputation is two x-halo sites and one earlier row), slower for
+    // d = 3, where it re-reads both operands of p at six neighbour rows.
+    return kind == ENGINE_D1 ? 1 : 0;
 }
 
 int engine_default_grid(int kind)

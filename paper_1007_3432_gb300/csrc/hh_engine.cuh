@@ -21,6 +21,18 @@
 // residual in FP64: it is the stopping test in FP64 mode (with residual
 // replacement when the recursive residual has drifted) and the reliable update
 // of the mixed mode (FP32 inner iteration, FP64 solution).
+//
+// Two-slot form (EngLaunch::two_slot): slot 1 is folded into slot 2.  The new
+// direction p = r + beta p_old is written to the other of two p buffers while
+// t = M p is computed from p recomputed at the neighbour sites (r and p_old
+// are final there), and the reliable update's x64 + x32 likewise; slot 3 is
+// unchanged.  One grid barrier and one read-write of p fewer per iteration,
+// for one extra read of r and p_old at each neighbour row.  Measured on
+// GB300, it is faster for d = 1 (two x-halo sites and one earlier row) and
+// slower for d = 3 (six neighbour rows), so the d = 1 kernel runs it and the
+// others do not.  The result is bitwise the same in both forms.  The <r, z>
+// partials after the last preconditioner sub-step go to part_rr in both
+// forms, so that no slot reads a partial array that the same slot writes.
 #pragma once
 
 #include "hh_device.cuh"
@@ -61,6 +73,8 @@ struct EngSystem {
     int cheb_n;                       // Chebyshev preconditioner degree n (0: plain CG; FP64 only)
     const double *cheb;               // coefficient table (see CHEB_MAX_DEGREE)
     double *z, *u;                    // FP64 preconditioner vectors (when cheb_n > 0)
+    double *p2;                       // second FP64 p buffer (two-slot launches)
+    float *p32b;                      // second FP32 p buffer (two-slot launches)
 };
 
 // FP32 steps after which a mixed system takes a reliable update even if its
@@ -94,6 +108,8 @@ struct EngState {
     int fp64_steps;     // CG steps run in FP64
     int since_ru;       // CG steps since the last RU
     int pre_j;          // MODE_PRE sub-step, 0 .. 2 cheb_n - 1
+    int pbuf;           // two-slot launches: p buffer (0: p/p32, 1: p2/p32b) holding p
+    int pad2;
 };
 
 struct EngTile {
@@ -111,6 +127,8 @@ struct EngLaunch {
     BarrierCtl *ctl;
     int nsys, ntiles;
     long long max_iters;    // engine iterations this launch may run
+    int two_slot;           // 1: two grid barriers per iteration (see above)
+    int pad;
 };
 
 // Engine kernels: ENGINE_GENERIC handles systems of both dimensions in one
@@ -136,6 +154,11 @@ constexpr int ENGINE_MIN_TILE = 512;   // sites per tile, at least one per threa
 // by co-residency.
 // HH_ENGINE_BLOCKS_PER_SM overrides the blocks per SM.
 int engine_default_grid(int kind);
+
+// 1 if launches of a kernel kind run the two-slot form: by default for
+// ENGINE_D1 only; HH_ENGINE_SLOTS=2 or 3 forces one form.  The forms give
+// bitwise identical results.
+int engine_two_slot(int kind);
 
 // Tiles of one system: 'tiles' contiguous ranges of 'chunk' sites (the last
 // one shorter), enough to give every block of the grid a tile when 'nsys'

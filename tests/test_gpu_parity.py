@@ -335,3 +335,67 @@ def test_chebyshev_pcg_trajectory_matches_plain_cg(hh):
 def test_chebyshev_rejected_for_mixed_precision(hh):
     with pytest.raises(hh.HHError):
         hh.Context(1, 8, 8, precision="mixed", cheb_degree=2)
+
+
+# Both forms of the engine iteration (three grid-wide slots, or the direction
+# update fused into t = M p) do the same arithmetic on the same operands in the
+# same order: solutions, iteration counts and residuals agree bit for bit.
+SLOT_CASES = [(1, 32, 64, "fp64", 0), (1, 48, 24, "mixed", 0), (3, 6, 8, "fp64", 0), (3, 8, 10, "mixed", 0),
+              (1, 32, 64, "fp64", 4), (3, 6, 8, "fp64", 3), (1, 19, 11, "mixed", 0)]
+
+
+@pytest.mark.parametrize("d,nx,ntau,precision,cheb", SLOT_CASES)
+def test_two_and_three_slot_forms_agree_bitwise(hh, monkeypatch, d, nx, ntau, precision, cheb):
+    n = nx ** d * ntau
+    sigma = workloads.sigma_field(n, seed=700 + nx)
+    b = np.stack([workloads.source(n, seed=701, rhs=a) for a in range(2)])
+    got = []
+    for slots in ("3", "2"):
+        monkeypatch.setenv("HH_ENGINE_SLOTS", slots)
+        with hh.Context(d, nx, ntau, precision=precision, cheb_degree=cheb, cheb_eps=1e-3) as ctx:
+            ctx.set_field(dev(sigma))
+            x = torch.zeros(2, n, dtype=torch.float64, device="cuda")
+            rc, info = ctx.solve(dev(b), x, 2)
+            got.append((rc, info, x.cpu().numpy()))
+    (rc3, i3, x3), (rc2, i2, x2) = got
+    assert rc3 == 0 and rc2 == 0
+    assert np.array_equal(x3, x2)
+    assert i3["iterations"] == i2["iterations"] and i3["true_relres"] == i2["true_relres"]
+
+
+def test_two_and_three_slot_forms_agree_through_fp64_fallback(hh, monkeypatch):
+    """A mixed solve on the d = 1, 1024 x 512 lattice stalls in FP32 and
+    continues in FP64 steps (Sec. 4.1 solver with FP32 inner iterations); both
+    forms take the same path through the switch."""
+    wl = workloads.C1
+    n = wl.nsites
+    sigma = workloads.sigma_field(n, seed=wl.seed)
+    b = workloads.source(n, seed=1)[None, :]
+    got = []
+    for slots in ("3", "2"):
+        monkeypatch.setenv("HH_ENGINE_SLOTS", slots)
+        with hh.Context(wl.d, wl.nx, wl.ntau, precision="mixed") as ctx:
+            ctx.set_field(dev(sigma))
+            x = torch.zeros(1, n, dtype=torch.float64, device="cuda")
+            ctx.counters_reset(True)
+            rc, info = ctx.solve(dev(b), x, 1)
+            got.append((rc, info, ctx.counters(), x.cpu().numpy()))
+    (rc3, i3, c3, x3), (rc2, i2, c2, x2) = got
+    assert rc3 == 0 and rc2 == 0 and i3["true_relres"] <= 1e-10
+    assert c3["fp64_steps"] > 0
+    assert np.array_equal(x3, x2)
+    assert i3["iterations"] == i2["iterations"]
+    assert c3["ru_steps"] == c2["ru_steps"] and c3["fp64_steps"] == c2["fp64_steps"]
+
+
+def test_chebyshev_pcg_iteration_cap_reports_no_convergence(hh):
+    """The cap counts PCG steps; each is followed by 2n preconditioner
+    sub-steps (Sec. 4.2), which must not exhaust the engine before it."""
+    d, nx, ntau = 1, 32, 64
+    n = nx * ntau
+    with hh.Context(d, nx, ntau, cg_maxit=7, cheb_degree=8, cheb_eps=1e-3) as ctx:
+        ctx.set_field(dev(workloads.sigma_field(n, seed=31)))
+        x = torch.zeros(1, n, dtype=torch.float64, device="cuda")
+        rc, info = ctx.solve(dev(workloads.source(n, seed=32))[None, :], x, 1,
+                             allow=(hh.binding.HH_ENOCONV,))
+    assert rc == hh.binding.HH_ENOCONV and info["converged"] == 0 and info["iterations"] == 7
