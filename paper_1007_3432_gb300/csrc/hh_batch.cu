@@ -212,8 +212,8 @@ struct hh_batch {
     EngSystem *d_sys = nullptr;
     EngState *d_state[2] = {nullptr, nullptr};
     EngTile *d_tiles = nullptr;
-    double *d_tt = nullptr, *d_rr = nullptr;
-    BarrierCtl *d_ctl = nullptr;
+    unsigned long long *d_sig = nullptr;   // engine signal slots, engine_sig_count(kMaxTiles)
+    EngCtl *d_ctl = nullptr;
     int max_sys = 0, ntiles = 0;
     int grid_of[4] = {0, 0, 0, 0};  // engine grid per kernel kind
     int kind = ENGINE_GENERIC;      // kernel of the current plan
@@ -224,7 +224,7 @@ struct hh_batch {
     std::vector<EngSystem> h_sys;
     std::vector<EngTile> h_tiles;
     EngState *h_states = nullptr;   // pinned mirror of one state buffer
-    BarrierCtl *h_ctl = nullptr;    // pinned
+    EngCtl *h_ctl = nullptr;    // pinned
     // graph of one chunk launch
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -286,6 +286,10 @@ int start_solve(hh_batch *b, int s)
         S.last_steps[a] = 0;
         S.rhs_done[a] = false;
     }
+    // Empty signal slots for the slot's tile partials (all 2 x 3 phases).
+    for (int ph = 0; ph < 6; ++ph)
+        HB_TRY(cudaMemsetAsync(b->d_sig + (size_t)ph * kMaxTiles + S.part_off, 0xFF,
+                               sizeof(unsigned long long) * (size_t)S.nrhs * S.tiles_per_rhs, b->stream));
     S.in_engine = true;
     b->plan_dirty = true;
     return HH_OK;
@@ -472,14 +476,15 @@ EngLaunch make_launch(hh_batch *b)
     L.state[0] = b->d_state[0];
     L.state[1] = b->d_state[1];
     L.tiles = b->d_tiles;
-    L.part_tt = b->d_tt;
-    L.part_rr = b->d_rr;
+    L.sig = b->d_sig;
+    L.sig_stride = kMaxTiles;
+    L.pad = 0;
     L.ctl = b->d_ctl;
     L.nsys = b->max_sys;
     L.ntiles = b->ntiles;
     L.max_iters = b->cfg.chunk_iters;
     L.two_slot = b->two_slot_of[b->kind];
-    L.pad = 0;
+    L.pad2 = 0;
     return L;
 }
 
@@ -616,12 +621,9 @@ int step(hh_batch *b)
 {
     int rc = admit_queued(b);
     if (rc) return rc;
-    int n_sys = 0, n_running = 0;
+    int n_sys = 0;
     for (auto &S : b->slots)
-        if (S.used && S.in_engine) {
-            n_sys += S.nrhs;
-            for (int a = 0; a < S.nrhs; ++a) n_running += S.rhs_done[a] ? 0 : 1;
-        }
+        if (S.used && S.in_engine) n_sys += S.nrhs;
     if (n_sys == 0) return HH_OK;
     if (b->plan_dirty) {
         rc = build_plan(b);
@@ -629,22 +631,22 @@ int step(hh_batch *b)
     }
     const int kgrid = b->grid_of[b->kind];
     int grid = b->ntiles < kgrid ? b->ntiles : kgrid;
-    BarrierCtl c;
+    EngCtl c;
     memset(&c, 0, sizeof(c));
-    c.active = n_running;
     c.k = b->k;
+    c.k_end = b->k;
     c.timeout_ns = 5LL * 1000 * 1000 * 1000;
     HB_TRY(cudaMemcpyAsync(b->d_ctl, &c, sizeof(c), cudaMemcpyHostToDevice, b->stream));
     rc = launch_chunk(b, grid);
     if (rc) return rc;
-    HB_TRY(cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(BarrierCtl), cudaMemcpyDeviceToHost, b->stream));
+    HB_TRY(cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(EngCtl), cudaMemcpyDeviceToHost, b->stream));
     HB_TRY(cudaStreamSynchronize(b->stream));
     if (b->h_ctl->error != 0) {
         fail_all_active(b, b->h_ctl->error);
         b->k = 0;
         return b->h_ctl->error;
     }
-    b->k = b->h_ctl->k;
+    b->k = b->h_ctl->k_end;
     HB_TRY(cudaMemcpyAsync(b->h_states, b->d_state[b->k & 1], sizeof(EngState) * b->max_sys,
                            cudaMemcpyDeviceToHost, b->stream));
     HB_TRY(cudaStreamSynchronize(b->stream));
@@ -700,7 +702,7 @@ void free_batch(hh_batch *b)
 {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    void *ptrs[] = {b->d_sys, b->d_state[0], b->d_state[1], b->d_tiles, b->d_tt, b->d_rr, b->d_ctl,
+    void *ptrs[] = {b->d_sys, b->d_state[0], b->d_state[1], b->d_tiles, b->d_sig, b->d_ctl,
                     b->arena.base};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -749,11 +751,10 @@ int hh_batch_create(hh_batch **out, const hh_batch_config *cfg, void *cuda_strea
     if (e == cudaSuccess) e = cudaMalloc(&b->d_state[0], sizeof(EngState) * b->max_sys);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_state[1], sizeof(EngState) * b->max_sys);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tiles, sizeof(EngTile) * kMaxTiles);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_tt, sizeof(double) * kMaxTiles);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_rr, sizeof(double) * kMaxTiles);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, sizeof(BarrierCtl));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sig, sizeof(unsigned long long) * engine_sig_count(kMaxTiles));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, sizeof(EngCtl));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_states, sizeof(EngState) * b->max_sys);
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_ctl, sizeof(BarrierCtl));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_ctl, sizeof(EngCtl));
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_state[0], 0, sizeof(EngState) * b->max_sys, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_state[1], 0, sizeof(EngState) * b->max_sys, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_sys, 0, sizeof(EngSystem) * b->max_sys, b->stream);

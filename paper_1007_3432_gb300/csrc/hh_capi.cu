@@ -28,8 +28,10 @@ struct EngStats {
     double max_relres;
 };
 
-__global__ void k_engine_reset(EngState *s0, EngState *s1, int nsys, BarrierCtl *ctl,
-                               long long timeout_ns)
+// New solves: states MODE_NEW, empty signal slots for 'parts' tile partials,
+// iteration counter 0.
+__global__ void k_engine_reset(EngState *s0, EngState *s1, int nsys, unsigned long long *sig, int parts,
+                               EngCtl *ctl, long long timeout_ns)
 {
     for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
         EngState z;
@@ -38,11 +40,12 @@ __global__ void k_engine_reset(EngState *s0, EngState *s1, int nsys, BarrierCtl 
         s0[s] = z;
         s1[s] = z;
     }
+    const int n = (int)engine_sig_count(parts);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sig[i] = kSigEmpty;
     if (threadIdx.x == 0) {
-        ctl->count = 0;
         ctl->error = 0;
-        ctl->active = nsys;
         ctl->k = 0;
+        ctl->k_end = 0;
         ctl->timeout_ns = timeout_ns;
     }
 }
@@ -61,11 +64,11 @@ struct EngTotals {
     long long cg_steps, ru_steps, solves, fp64_steps;
 };
 
-__global__ void k_engine_fold(EngState *s0, EngState *s1, int nsys, const BarrierCtl *ctl,
+__global__ void k_engine_fold(EngState *s0, EngState *s1, int nsys, const EngCtl *ctl,
                               EngStats *stats, EngTotals *tot)
 {
     if (threadIdx.x != 0) return;
-    const EngState *st = (ctl->k & 1) ? s1 : s0;
+    const EngState *st = (ctl->k_end & 1) ? s1 : s0;
     if (ctl->error != 0 && severity(ctl->error) > severity(stats->worst_status))
         stats->worst_status = ctl->error;
     if (ctl->error != 0) stats->error = ctl->error;
@@ -123,8 +126,8 @@ struct hh_ctx {
     EngSystem *d_sys;
     EngState *d_state[2];
     EngTile *d_tiles;
-    double *d_part_tt, *d_part_rr;
-    BarrierCtl *d_ctl;
+    unsigned long long *d_sig;      // engine signal slots, engine_sig_count(max_tiles)
+    EngCtl *d_ctl;
     EngStats *d_stats;
     int max_tiles;
     Plan plan;
@@ -165,8 +168,7 @@ void free_ctx(hh_ctx *c)
 {
     void *ptrs[] = {c->sigma, c->sigma0, c->L64, c->pi, c->chi, c->xsol, c->tmp, c->F, c->L32,
                     c->tmp32a, c->tmp32b, c->r, c->p, c->p2, c->t, c->r32, c->p32, c->p32b, c->t32, c->x32,
-                    c->d_sys, c->d_state[0], c->d_state[1], c->d_tiles, c->d_part_tt,
-                    c->d_part_rr, c->d_ctl, c->d_stats, c->d_sc, c->d_energy_part,
+                    c->d_sys, c->d_state[0], c->d_state[1], c->d_tiles, c->d_sig, c->d_ctl, c->d_stats, c->d_sc, c->d_energy_part,
                     c->d_energy_out};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -259,16 +261,17 @@ int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
 int run_engine(hh_ctx *c)
 {
     const Plan &P = c->plan;
-    k_engine_reset<<<1, 64, 0, c->stream>>>(c->d_state[0], c->d_state[1], P.nsys, c->d_ctl,
-                                            c->timeout_ns);
+    k_engine_reset<<<1, 256, 0, c->stream>>>(c->d_state[0], c->d_state[1], P.nsys, c->d_sig,
+                                             c->max_tiles, c->d_ctl, c->timeout_ns);
     HH_TRY(cudaGetLastError());
     EngLaunch L;
     L.sys = c->d_sys;
     L.state[0] = c->d_state[0];
     L.state[1] = c->d_state[1];
     L.tiles = c->d_tiles;
-    L.part_tt = c->d_part_tt;
-    L.part_rr = c->d_part_rr;
+    L.sig = c->d_sig;
+    L.sig_stride = c->max_tiles;
+    L.pad = 0;
     L.ctl = c->d_ctl;
     L.nsys = P.nsys;
     L.ntiles = P.ntiles;
@@ -277,7 +280,7 @@ int run_engine(hh_ctx *c)
     // sub-steps; the cap is a safety bound well above maxit.
     L.max_iters = (2LL * c->prm.cheb_degree + 1) * (3LL * (long long)c->prm.cg_maxit + 64);
     L.two_slot = c->two_slot;
-    L.pad = 0;
+    L.pad2 = 0;
     bool rec = c->profile && c->ev_used + 2 <= c->ev_cap;
     if (rec) HH_TRY(cudaEventRecord(c->ev[c->ev_used], c->stream));
     HH_TRY(engine_launch(L, P.grid, ENGINE_BLOCK, c->stream, c->kind));
@@ -426,8 +429,7 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
     if (e == cudaSuccess) e = dalloc(&c->d_state[0], (size_t)c->cap_rhs);
     if (e == cudaSuccess) e = dalloc(&c->d_state[1], (size_t)c->cap_rhs);
     if (e == cudaSuccess) e = dalloc(&c->d_tiles, (size_t)c->max_tiles);
-    if (e == cudaSuccess) e = dalloc(&c->d_part_tt, (size_t)c->max_tiles);
-    if (e == cudaSuccess) e = dalloc(&c->d_part_rr, (size_t)c->max_tiles);
+    if (e == cudaSuccess) e = dalloc(&c->d_sig, engine_sig_count(c->max_tiles));
     if (e == cudaSuccess) e = dalloc(&c->d_ctl, 1);
     if (e == cudaSuccess) e = dalloc(&c->d_stats, 1);
     if (e == cudaSuccess) e = dalloc(&c->d_sc, 1);
@@ -468,7 +470,7 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
         return e == cudaErrorMemoryAllocation ? HH_ENOMEM : HH_ECUDA;
     }
     e = cudaMemsetAsync(c->sigma, 0, n * sizeof(double), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_ctl, 0, sizeof(BarrierCtl), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_ctl, 0, sizeof(EngCtl), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_sc, 0, sizeof(HmcScalars), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_totals, 0, sizeof(EngTotals), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_apply_err, 0, sizeof(int), c->stream);

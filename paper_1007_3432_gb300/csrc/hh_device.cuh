@@ -1,7 +1,7 @@
 // Device-side building blocks of the GB300 Hubbard HMC library: lattice
 // geometry with division by invariant integers, the stencil of the fermion
-// matrix, the Philox counter generator, deterministic block reductions and a
-// grid barrier whose waits are bounded in time.
+// matrix, the Philox counter generator, deterministic block reductions and the
+// signal slots of the persistent engine, whose waits are bounded in time.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -317,20 +317,25 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 }
 
 // ---------------------------------------------------------------------------
-// Grid barrier for cooperative (co-resident) launches.  Each block adds one to
-// a monotonic arrival counter (zeroed before every launch) and waits until the
-// counter reaches the next multiple of the grid size.  Every wait is bounded by
-// a wall-clock budget read from the global timer, after which the barrier
-// records an error and returns false.
+// Control block of a cooperative engine launch, and the signal slots through
+// which its blocks exchange per-tile partial sums.
+//
+// A tile publishes the partial of each phase it runs into a slot of a
+// parity-indexed pair (iteration k writes slot k & 1) with a release store,
+// after emptying the slot of the other parity.  A block that needs the phase
+// complete (its neighbour data written, its partial sums known) polls the
+// slots of every tile of that system with relaxed loads until none is empty,
+// then fences: one round trip both synchronises and delivers the values, and
+// a block waits only for the tiles of its own systems.  Every wait is bounded
+// by a wall-clock budget read from the global timer, after which it records
+// HH_ETIMEOUT (-6) and the kernel leaves.
 // ---------------------------------------------------------------------------
-struct BarrierCtl {
-    unsigned int count; // arrivals since the launch began; zeroed before each launch
-    unsigned int gen;   // unused padding kept for layout stability
-    int error;          // 0, or a negative library error code
-    int active;         // systems still running (engine bookkeeping)
-    long long k;        // engine iteration counter, persists across launches
-    long long timeout_ns;
-    int pad[2];
+struct EngCtl {
+    int error;              // 0, or a negative library error code (first one wins)
+    int pad0;
+    long long k;            // engine iteration counter when the launch starts
+    long long k_end;        // engine iteration counter after it (max over blocks)
+    long long timeout_ns;   // bound of every wait
 };
 
 __device__ __forceinline__ uint64_t global_ns()
@@ -340,51 +345,86 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ int ld_volatile_i32(const int *p)
 {
     return *(const volatile int *)p;
 }
 
-// 'target' is block-private and starts at 0.  Returns false if the barrier
-// timed out or another block recorded an error.
-__device__ __forceinline__ bool grid_barrier(BarrierCtl *ctl, unsigned nblocks, unsigned &target,
-                                             int *s_flag)
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
 {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        target += nblocks;
-        int ok = 1;
-        // Release: the block's writes (ordered before by bar.sync) become
-        // visible no later than this arrival.
-        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&ctl->count), "r"(1u) : "memory");
-        unsigned spins = 0;
-        uint64_t t0 = 0;
-        while ((int)(ld_acquire_u32(&ctl->count) - target) < 0) {
-            if ((++spins & 127u) == 0) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Empty slot: a NaN bit pattern no published value has (a NaN partial is
+// published as the canonical quiet NaN).
+constexpr unsigned long long kSigEmpty = ~0ull;
+constexpr unsigned long long kSigNaN = 0x7FF8000000000000ull;
+
+// Called by one thread after a __syncthreads() that follows all of the block's
+// writes of the phase: empties 'next' (the slot the tile writes next
+// iteration), then release-stores v into 'now'.
+__device__ __forceinline__ void sig_publish(unsigned long long *now, unsigned long long *next, double v)
+{
+    unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    if (v != v) bits = kSigNaN;
+    *next = kSigEmpty;
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(now), "l"(bits) : "memory");
+}
+
+// Called by all 32 lanes of one warp: waits until the n slots sig[0, n) are
+// published and returns their sum in lane 0 (lane-strided sums over
+// j = lane, lane + 32, ... in order, then a fixed shuffle tree; the same bits
+// in every block).  Returns false in every lane on a timeout or a recorded
+// error.
+__device__ __forceinline__ bool poll_sum(const unsigned long long *sig, int n, EngCtl *ctl, double &sum)
+{
+    constexpr int U = 8;
+    const int lane = (int)(threadIdx.x & 31u);
+    double v = 0.0;
+    bool ok = true;
+    unsigned spins = 0;
+    uint64_t t0 = 0;
+    for (int j0 = 0; j0 < n && ok; j0 += 32 * U) {
+        unsigned long long a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + 32 * u + lane;
+            a[u] = j < n ? ld_relaxed_u64(sig + j) : 0ull;
+        }
+        while (true) {
+            bool ready = true;
+#pragma unroll
+            for (int u = 0; u < U; ++u) ready = ready && (a[u] != kSigEmpty);
+            if (ready) break;
+            if ((++spins & 63u) == 0) {
                 if (t0 == 0) t0 = global_ns();
                 if (ld_volatile_i32(&ctl->error) != 0) {
-                    ok = 0;
+                    ok = false;
                     break;
                 }
                 if ((long long)(global_ns() - t0) > ctl->timeout_ns) {
                     atomicCAS(&ctl->error, 0, -6);
-                    ok = 0;
+                    ok = false;
                     break;
                 }
             }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (a[u] == kSigEmpty) a[u] = ld_relaxed_u64(sig + j0 + 32 * u + lane);
         }
-        if (ok && ld_volatile_i32(&ctl->error) != 0) ok = 0;
-        *s_flag = ok;
+        if (ok) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) v += __longlong_as_double((long long)a[u]);
+        }
     }
-    __syncthreads();
-    return *s_flag != 0;
+    // Acquire side: the relaxed loads above observed the publishers' release
+    // stores; the fence orders this block's later reads after their writes.
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    ok = __all_sync(0xffffffffu, ok);
+    sum = warp_sum(v);
+    return ok;
 }
 
 }  // namespace hh

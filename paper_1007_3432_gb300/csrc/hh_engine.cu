@@ -290,24 +290,6 @@ __device__ void gloop_accumulate(double *x, float *x32, int b, int e)
 // Per-system decisions.
 // ---------------------------------------------------------------------------
 
-// Fixed-order sum of per-tile partials [t0, t0 + n): lane-strided sequential
-// sums in warp 0 followed by a fixed shuffle tree, broadcast to the block.
-// Every block that calls it on the same data gets the same bits.
-__device__ double sum_partials(const double *part, int t0, int n, double *s_val)
-{
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double v = 0.0;
-        for (int j = threadIdx.x; j < n; j += 32) v += part[t0 + j];
-        v = warp_sum(v);
-        if (threadIdx.x == 0) *s_val = v;
-    }
-    __syncthreads();
-    double r = *s_val;
-    __syncthreads();
-    return r;
-}
-
 // Next mode of a system from its previous state and the |r|^2 (or, after the
 // last preconditioner sub-step, <r, z>) reduced from the previous iteration's
 // slot 3.  Pure function of its inputs: all blocks agree.
@@ -356,7 +338,7 @@ __device__ EngState decide(const EngSystem &Y, const EngState &P, double rr)
         }
         return S;
     case MODE_PRE: {
-        // rr is <r, z> after the last sub-step (reduced from part_rr).
+        // rr is <r, z> after the last sub-step (published in slot 3).
         if (P.pre_j + 1 < 2 * Y.cheb_n) {
             S.pre_j = P.pre_j + 1;
             return S;
@@ -656,7 +638,6 @@ template <int FD, int MINB>
 __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
 {
     __shared__ double s_red[ENGINE_BLOCK / 32];
-    __shared__ double s_val;
     __shared__ int s_flag;
     __shared__ EngState s_cache[kCacheSys];
     __shared__ TileCtl s_tctl[kCacheSys];
@@ -664,14 +645,13 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
     __shared__ unsigned char s_slot[kCacheTiles];
     __shared__ int s_ok;
     // Read-only descriptors of this block's tiles and systems, copied once:
-    // the acquire at every grid barrier invalidates L1, so re-reading them
-    // from global memory would cost two dependent L2 round trips per phase.
+    // re-reading them from global memory after each wait would cost two
+    // dependent L2 round trips per slot.
     __shared__ EngTile s_tiles[kCacheTiles];
     __shared__ EngSystem s_sysd[kCacheSys];
 
-    BarrierCtl *ctl = L.ctl;
+    EngCtl *ctl = L.ctl;
     const unsigned G = gridDim.x;
-    unsigned target = 0;
     long long k = *(volatile long long *)&ctl->k;
 
     if (threadIdx.x == 0) {
@@ -713,124 +693,116 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
     }
 
     const int two = L.two_slot;
+    const int nph = two ? 2 : 3;
+    const size_t stride = (size_t)L.sig_stride;
     for (long long it = 0; it < L.max_iters; ++it, ++k) {
         EngState *cur = (k & 1) ? L.state[1] : L.state[0];
         EngState *nxt = (k & 1) ? L.state[0] : L.state[1];
-
-        // ---- first slot: decide; then slot 1 (three-slot form) or slot 1
-        //      fused with slot 2 (two-slot form) ----
-        {
+        const int q = (int)(k & 1);
+        int live = 0;   // thread 0: a system of this block still runs after this iteration's decisions
+        for (int ph = 0; ph < nph; ++ph) {
+            // Slot of this phase: 1 (decide + direction), 2 (t = M p), 3 (update);
+            // two-slot form: 4 (decide + direction fused with t = M p), 3.
+            const int sl = ph == 0 ? (two ? 4 : 1) : (two ? 3 : ph + 1);
+            // Signal index of this phase and of the one it waits for.
+            const int id = ph == 0 ? 0 : (ph == nph - 1 ? 2 : 1);
+            const int id_prev = ph == 0 ? 2 : (ph == 1 ? 0 : 1);
+            unsigned long long *sig_now = L.sig + (size_t)(2 * id + q) * stride;
+            unsigned long long *sig_next = L.sig + (size_t)(2 * id + (q ^ 1)) * stride;
+            const unsigned long long *sig_wait = L.sig + (size_t)(2 * id_prev + (ph == 0 ? (q ^ 1) : q)) * stride;
             int last = -1, j = 0;
             for (int tile = blockIdx.x; tile < L.ntiles; tile += G, ++j) {
                 const int slot = cached ? s_slot[j] : 0;
                 const EngTile T = cached ? s_tiles[j] : L.tiles[tile];
                 const EngSystem &Y = cached ? s_sysd[slot] : L.sys[T.sys];
                 if (T.sys != last) {
-                    if (!cached || it == 0) {
-                        __syncthreads();
-                        if (threadIdx.x == 0) s_cache[slot] = cur[T.sys];
-                    }
                     __syncthreads();
-                    const int pm = s_cache[slot].mode;
-                    double rr = 0.0;
-                    if (pm == MODE_INIT || pm == MODE_CG || pm == MODE_RU ||
-                        (pm == MODE_PRE && s_cache[slot].pre_j == 2 * Y.cheb_n - 1))
-                        rr = sum_partials(L.part_rr, Y.part0, Y.ntiles, &s_val);
-                    if (threadIdx.x == 0) {
-                        const EngState P = s_cache[slot];
-                        EngState S = decide(Y, P, rr);
-                        if (two && S.mode == MODE_CG) S.pbuf = P.pbuf ^ 1;
-                        if ((int)blockIdx.x == Y.owner) {
-                            nxt[T.sys] = S;
-                            if (S.mode == MODE_DONE && P.mode != MODE_DONE) atomicSub(&ctl->active, 1);
+                    if (sl == 1 || sl == 4) {
+                        if (!cached || it == 0) {
+                            if (threadIdx.x == 0) s_cache[slot] = cur[T.sys];
+                            __syncthreads();
                         }
-                        s_cache[slot] = S;
-                        s_tctl[slot] = make_ctl(S, two);
+                        if (threadIdx.x < 32) {
+                            // Wait for the previous iteration's slot 3 of this system
+                            // (nothing to wait for at its first iteration or when done).
+                            const EngState &P = s_cache[slot];
+                            double rr = 0.0;
+                            bool ok = true;
+                            if (P.mode != MODE_NEW && P.mode != MODE_DONE)
+                                ok = poll_sum(sig_wait + Y.part0, Y.ntiles, ctl, rr);
+                            if (threadIdx.x == 0) {
+                                s_flag = ok ? 1 : 0;
+                                if (ok) {
+                                    EngState S = decide(Y, P, rr);
+                                    if (two && S.mode == MODE_CG) S.pbuf = P.pbuf ^ 1;
+                                    if ((int)blockIdx.x == Y.owner) {
+                                        nxt[T.sys] = S;
+                                        // A finished system's blocks leave at different
+                                        // iterations: keep its final state in both buffers.
+                                        if (S.mode == MODE_DONE && P.mode != MODE_DONE) cur[T.sys] = S;
+                                    }
+                                    if (S.mode != MODE_DONE) live = 1;
+                                    s_cache[slot] = S;
+                                    s_tctl[slot] = make_ctl(S, two);
+                                }
+                            }
+                        }
+                    } else {
+                        if (!cached && threadIdx.x == 0) {
+                            const EngState S = nxt[T.sys];
+                            s_cache[0] = S;
+                            s_tctl[0] = make_ctl(S, two);
+                        }
+                        __syncthreads();
+                        if (threadIdx.x < 32) {
+                            bool ok = true;
+                            double tt = 0.0;
+                            if (s_tctl[slot].mode != MODE_DONE)
+                                ok = poll_sum(sig_wait + Y.part0, Y.ntiles, ctl, tt);
+                            if (threadIdx.x == 0) {
+                                s_flag = ok ? 1 : 0;
+                                if (ok && sl == 3 && s_tctl[slot].mode == MODE_CG)
+                                    s_tctl[slot].alpha = s_cache[slot].rr_alpha / tt;
+                            }
+                        }
                     }
                     __syncthreads();
+                    if (!s_flag) return;
                     last = T.sys;
                 }
                 const TileCtl c = s_tctl[slot];
-                if (two) {
-                    double v = run_slot<4, FD>(Y, c, T);
-                    if (c.mode == MODE_CG) {
-                        double tot = block_sum(v, s_red);
-                        if (threadIdx.x == 0) L.part_tt[T.part] = tot;
-                    }
-                } else {
+                if (c.mode == MODE_DONE) continue;
+                double v;
+                if (sl == 1) {
                     run_slot<1, FD>(Y, c, T);
+                    v = 0.0;
+                } else if (sl == 2) {
+                    v = run_slot<2, FD>(Y, c, T);
+                } else if (sl == 4) {
+                    v = run_slot<4, FD>(Y, c, T);
+                } else {
+                    v = run_slot<3, FD>(Y, c, T);
+                }
+                // |t|^2 (CG, slot 2 or 4), |r|^2 (CG, RU, INIT, slot 3), <r, z>
+                // after the last preconditioner sub-step, else 0; the block sum
+                // ends with a __syncthreads() after all of the tile's writes.
+                const double tot = block_sum(v, s_red);
+                if (threadIdx.x == 0) sig_publish(sig_now + T.part, sig_next + T.part, tot);
+            }
+            if (ph == 0) {
+                // Leave once every system of this block is done: no other block
+                // waits for its tiles any more.
+                __syncthreads();
+                if (threadIdx.x == 0) s_flag = live;
+                __syncthreads();
+                if (!s_flag) {
+                    if (threadIdx.x == 0) atomicMax((long long *)&ctl->k_end, k + 1);
+                    return;
                 }
             }
         }
-        if (!grid_barrier(ctl, G, target, &s_flag)) return;
-        if (ld_volatile_i32(&ctl->active) <= 0) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) ctl->k = k + 1;
-            return;
-        }
-
-        // ---- slot 2 (three-slot form only) ----
-        if (!two) {
-            int last = -1, j = 0;
-            for (int tile = blockIdx.x; tile < L.ntiles; tile += G, ++j) {
-                const int slot = cached ? s_slot[j] : 0;
-                const EngTile T = cached ? s_tiles[j] : L.tiles[tile];
-                const EngSystem &Y = cached ? s_sysd[slot] : L.sys[T.sys];
-                if (!cached && T.sys != last) {
-                    __syncthreads();
-                    if (threadIdx.x == 0) {
-                        const EngState S = nxt[T.sys];
-                        s_cache[0] = S;
-                        s_tctl[0] = make_ctl(S, two);
-                    }
-                    __syncthreads();
-                    last = T.sys;
-                }
-                const TileCtl c = s_tctl[slot];
-                double v = run_slot<2, FD>(Y, c, T);
-                if (c.mode == MODE_CG) {
-                    double tot = block_sum(v, s_red);
-                    if (threadIdx.x == 0) L.part_tt[T.part] = tot;
-                }
-            }
-            if (!grid_barrier(ctl, G, target, &s_flag)) return;
-        }
-
-        // ---- slot 3 ----
-        {
-            int last = -1, j = 0;
-            for (int tile = blockIdx.x; tile < L.ntiles; tile += G, ++j) {
-                const int slot = cached ? s_slot[j] : 0;
-                const EngTile T = cached ? s_tiles[j] : L.tiles[tile];
-                const EngSystem &Y = cached ? s_sysd[slot] : L.sys[T.sys];
-                if (T.sys != last) {
-                    __syncthreads();
-                    if (!cached && threadIdx.x == 0) {
-                        const EngState S = nxt[T.sys];
-                        s_cache[0] = S;
-                        s_tctl[0] = make_ctl(S, two);
-                    }
-                    __syncthreads();
-                    if (s_tctl[slot].mode == MODE_CG) {
-                        double tt = sum_partials(L.part_tt, Y.part0, Y.ntiles, &s_val);
-                        if (threadIdx.x == 0) s_tctl[slot].alpha = s_cache[slot].rr_alpha / tt;
-                    }
-                    __syncthreads();
-                    last = T.sys;
-                }
-                const TileCtl c = s_tctl[slot];
-                double v = run_slot<3, FD>(Y, c, T);
-                // |r|^2 (CG, RU, INIT) or <r, z> after the last
-                // preconditioner sub-step: both feed the next decide().
-                if (c.mode == MODE_CG || c.mode == MODE_RU || c.mode == MODE_INIT ||
-                    (c.mode == MODE_PRE && c.pre_j == 2 * Y.cheb_n - 1)) {
-                    double tot = block_sum(v, s_red);
-                    if (threadIdx.x == 0) L.part_rr[T.part] = tot;
-                }
-            }
-        }
-        if (!grid_barrier(ctl, G, target, &s_flag)) return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->k = k;
+    if (threadIdx.x == 0) atomicMax((long long *)&ctl->k_end, k);
 }
 
 }  // namespace

@@ -3,8 +3,8 @@
 // One cooperative launch runs CG (Sec. 4.1) on a table of independent linear
 // systems Q_s x_s = b_s (right-hand sides of one lattice, or chains of
 // different lattices).  Each system is cut into tiles of contiguous sites; the
-// blocks of the grid own fixed tiles.  An engine iteration has three slots
-// separated by grid barriers, and each system executes one mode per iteration:
+// blocks of the grid own fixed tiles.  An engine iteration has three slots,
+// and each system executes one mode per iteration:
 //
 //   mode   slot 1                 slot 2                slot 3
 //   INIT   x = 0                  -                     r = b, partial |r|^2
@@ -14,25 +14,27 @@
 //   RU     x64 += x32, x32 = 0    t64 = M x64 (FP64)    r = b - M^T t64 (FP64),
 //          (mixed only)                                 partial |r|^2
 //
-// At slot 1 every block that owns a tile of system s sums that system's
-// per-tile partials in a fixed order and takes the same decision (next mode,
-// beta, convergence), so no atomics or extra barriers are needed; one
-// designated block writes the system's state.  RU recomputes the true
-// residual in FP64: it is the stopping test in FP64 mode (with residual
-// replacement when the recursive residual has drifted) and the reliable update
-// of the mixed mode (FP32 inner iteration, FP64 solution).
+// Slots are ordered per system, not across the grid: at the end of each slot
+// every tile publishes its partial sum into a signal slot (see EngCtl), and a
+// block starts the next slot of a system once every tile of that system has
+// published; the poll that waits also delivers the partials.  A block whose
+// systems are all done leaves the kernel.  At slot 1 every block that owns a
+// tile of system s sums that system's per-tile partials in a fixed order and
+// takes the same decision (next mode, beta, convergence), so no atomics are
+// needed; one designated block writes the system's state.  RU recomputes the
+// true residual in FP64: it is the stopping test in FP64 mode (with residual
+// replacement when the recursive residual has drifted) and the reliable
+// update of the mixed mode (FP32 inner iteration, FP64 solution).
 //
 // Two-slot form (EngLaunch::two_slot): slot 1 is folded into slot 2.  The new
 // direction p = r + beta p_old is written to the other of two p buffers while
 // t = M p is computed from p recomputed at the neighbour sites (r and p_old
 // are final there), and the reliable update's x64 + x32 likewise; slot 3 is
-// unchanged.  One grid barrier and one read-write of p fewer per iteration,
-// for one extra read of r and p_old at each neighbour row.  Measured on
-// GB300, it is faster for d = 1 (two x-halo sites and one earlier row) and
-// slower for d = 3 (six neighbour rows), so the d = 1 kernel runs it and the
-// others do not.  The result is bitwise the same in both forms.  The <r, z>
-// partials after the last preconditioner sub-step go to part_rr in both
-// forms, so that no slot reads a partial array that the same slot writes.
+// unchanged.  One synchronisation and one read-write of p fewer per
+// iteration, for one extra read of r and p_old at each neighbour row.
+// Measured on GB300, it is faster for d = 1 (two x-halo sites and one earlier
+// row) and slower for d = 3 (six neighbour rows), so the d = 1 kernel runs it
+// and the others do not.  The result is bitwise the same in both forms.
 #pragma once
 
 #include "hh_device.cuh"
@@ -122,14 +124,25 @@ struct EngLaunch {
     const EngSystem *sys;
     EngState *state[2];     // double buffer by engine-iteration parity
     const EngTile *tiles;
-    double *part_tt;        // per-tile partials of |t|^2
-    double *part_rr;        // per-tile partials of |r|^2
-    BarrierCtl *ctl;
+    // Signal slots (see EngCtl): slot of tile part p for the phase with index
+    // ph (0: first slot, 1: slot 2 of the three-slot form, 2: slot 3) at
+    // iteration parity q is sig[(2 * ph + q) * sig_stride + p].  A system's
+    // slots must be empty (kSigEmpty) when it enters as MODE_NEW.
+    unsigned long long *sig;
+    int sig_stride;
+    int pad;
+    EngCtl *ctl;
     int nsys, ntiles;
     long long max_iters;    // engine iterations this launch may run
-    int two_slot;           // 1: two grid barriers per iteration (see above)
-    int pad;
+    int two_slot;           // 1: two phases per iteration (see above)
+    int pad2;
 };
+
+// Signal slots needed for 'parts' tile partial indices.
+__host__ __device__ constexpr size_t engine_sig_count(int parts)
+{
+    return (size_t)6 * (size_t)parts;
+}
 
 // Engine kernels: ENGINE_GENERIC handles systems of both dimensions in one
 // launch; ENGINE_D1 / ENGINE_D3 require every system of the launch to have

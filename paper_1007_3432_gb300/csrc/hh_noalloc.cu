@@ -45,10 +45,9 @@ constexpr size_t kOffT = kOffP + align256(sizeof(double) * kMaxSites);
 constexpr size_t kOffSys = kOffT + align256(sizeof(double) * kMaxSites);
 constexpr size_t kOffState = kOffSys + align256(sizeof(EngSystem));
 constexpr size_t kOffTiles = kOffState + align256(2 * sizeof(EngState));
-constexpr size_t kOffPartTT = kOffTiles + align256(sizeof(EngTile) * kMaxTiles);
-constexpr size_t kOffPartRR = kOffPartTT + align256(sizeof(double) * kMaxTiles);
-constexpr size_t kOffCtl = kOffPartRR + align256(sizeof(double) * kMaxTiles);
-constexpr size_t kScratchBytes = kOffCtl + align256(sizeof(BarrierCtl));
+constexpr size_t kOffSig = kOffTiles + align256(sizeof(EngTile) * kMaxTiles);
+constexpr size_t kOffCtl = kOffSig + align256(sizeof(unsigned long long) * engine_sig_count(kMaxTiles));
+constexpr size_t kScratchBytes = kOffCtl + align256(sizeof(EngCtl));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -78,8 +77,8 @@ int setup_device(int dev, int d, unsigned char **base, int *max_grid)
     return HH_OK;
 }
 
-// Writes the system table and the tiles into the scratch array and clears
-// the engine state and the barrier word.
+// Writes the system table and the tiles into the scratch array, and resets
+// the engine state, the signal slots of the tiles and the control block.
 __global__ void k_noalloc_plan(unsigned char *base, Geo g, double h, const double *b, double *x,
                                double tol, int maxit, int chunk, int ntiles, int grid,
                                long long timeout_ns)
@@ -93,6 +92,9 @@ __global__ void k_noalloc_plan(unsigned char *base, Geo g, double h, const doubl
         T.part = j;
         tiles[j] = T;
     }
+    unsigned long long *sig = (unsigned long long *)(base + kOffSig);
+    for (int ph = 0; ph < 6; ++ph)
+        for (int j = threadIdx.x; j < ntiles; j += blockDim.x) sig[(size_t)ph * kMaxTiles + j] = kSigEmpty;
     if (threadIdx.x == 0) {
         EngSystem Y;
         memset(&Y, 0, sizeof(Y));
@@ -122,11 +124,10 @@ __global__ void k_noalloc_plan(unsigned char *base, Geo g, double h, const doubl
         EngState *st = (EngState *)(base + kOffState);
         st[0] = z;
         st[1] = z;
-        BarrierCtl *ctl = (BarrierCtl *)(base + kOffCtl);
-        ctl->count = 0;
+        EngCtl *ctl = (EngCtl *)(base + kOffCtl);
         ctl->error = 0;
-        ctl->active = 1;
         ctl->k = 0;
+        ctl->k_end = 0;
         ctl->timeout_ns = timeout_ns;
     }
 }
@@ -172,25 +173,26 @@ extern "C" int hh_solve_noalloc(const hh_lattice *lat, const hh_params *p, const
     L.state[0] = (EngState *)(base + kOffState);
     L.state[1] = L.state[0] + 1;
     L.tiles = (const EngTile *)(base + kOffTiles);
-    L.part_tt = (double *)(base + kOffPartTT);
-    L.part_rr = (double *)(base + kOffPartRR);
-    L.ctl = (BarrierCtl *)(base + kOffCtl);
+    L.sig = (unsigned long long *)(base + kOffSig);
+    L.sig_stride = kMaxTiles;
+    L.pad = 0;
+    L.ctl = (EngCtl *)(base + kOffCtl);
     L.nsys = 1;
     L.ntiles = ntiles;
     L.max_iters = 3LL * (long long)p->cg_maxit + 64;
     L.two_slot = 0;     // one p buffer in the static scratch
-    L.pad = 0;
+    L.pad2 = 0;
     if (engine_launch(L, grid, ENGINE_BLOCK, st, lat->d == 1 ? ENGINE_D1 : ENGINE_D3) != cudaSuccess)
         return HH_ECUDA;
     if (!info) return HH_OK;
 
     // Results into caller stack memory (pageable copies, no allocation).
-    BarrierCtl ctl;
+    EngCtl ctl;
     EngState S;
     if (cudaMemcpyAsync(&ctl, L.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return HH_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return HH_ECUDA;
-    if (cudaMemcpyAsync(&S, L.state[ctl.k & 1], sizeof(S), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    if (cudaMemcpyAsync(&S, L.state[ctl.k_end & 1], sizeof(S), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return HH_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return HH_ECUDA;
     info->iterations = S.cg_steps;
