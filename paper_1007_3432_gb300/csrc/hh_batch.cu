@@ -218,6 +218,7 @@ struct hh_batch {
     int grid_of[4] = {0, 0, 0, 0};  // engine grid per kernel kind
     int kind = ENGINE_GENERIC;      // kernel of the current plan
     int two_slot_of[4] = {0, 0, 0, 0};  // engine form per kernel kind
+    int ctl_warp = 1;               // engine launches use a control warp
     int graph_kind = -1;
     long long k = 0;
     bool plan_dirty = true;
@@ -478,13 +479,13 @@ EngLaunch make_launch(hh_batch *b)
     L.tiles = b->d_tiles;
     L.sig = b->d_sig;
     L.sig_stride = kMaxTiles;
-    L.pad = 0;
+    L.ctl_warp = b->ctl_warp;
     L.ctl = b->d_ctl;
     L.nsys = b->max_sys;
     L.ntiles = b->ntiles;
     L.max_iters = b->cfg.chunk_iters;
     L.two_slot = b->two_slot_of[b->kind];
-    L.pad2 = 0;
+    L.homogeneous = 0;
     return L;
 }
 
@@ -743,6 +744,10 @@ int hh_batch_create(hh_batch **out, const hh_batch_config *cfg, void *cuda_strea
     b->grid_of[ENGINE_D1] = engine_default_grid(ENGINE_D1);
     b->grid_of[ENGINE_D3] = engine_default_grid(ENGINE_D3);
     for (int k : {ENGINE_GENERIC, ENGINE_D1, ENGINE_D3}) b->two_slot_of[k] = engine_two_slot(k);
+    {
+        const char *env = getenv("HH_BATCH_CTL_WARP");
+        b->ctl_warp = env ? (atoi(env) != 0) : 1;
+    }
     cudaError_t e = (b->grid_of[0] > 0 && b->grid_of[1] > 0 && b->grid_of[3] > 0) ? cudaSuccess
                                                                                  : cudaErrorUnknown;
     if (e == cudaSuccess) e = b->arena.init(cfg->hbm_budget_bytes);

@@ -97,7 +97,7 @@ __global__ void k_zero_stats(EngStats *stats)
 
 // Plan of one engine launch: the system table and tiles in device memory.
 struct Plan {
-    int nsys = 0, ntiles = 0, grid = 0;
+    int nsys = 0, ntiles = 0, grid = 0, homogeneous = 0;
     int precision = -1;
     const double *b = nullptr;
     double *x = nullptr;
@@ -190,10 +190,18 @@ int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
 {
     Plan &P = c->plan;
     if (P.nsys == n_rhs && P.b == b && P.x == x && P.precision == c->prm.precision) return HH_OK;
-    Tiling tl = engine_tiling(c->N, n_rhs, c->max_grid);
+    // Overlapped layout: every system is tiled over the whole grid, so each
+    // block holds one tile of each system, in system order, and the engine's
+    // control warp prepares and publishes one system's slots while the compute
+    // warps run another's (EngLaunch::homogeneous).  It pays when a tile's slot
+    // takes longer than the control warp's wait, decision and publication
+    // (about 3.5 us on GB300): FP64 systems from 2^18 sites, mixed ones from
+    // 2^21.  Otherwise the systems share the grid, one tile per block.
+    const bool overlap = engine_overlap(n_rhs, c->N, c->prm.precision == HH_MIXED);
+    Tiling tl = engine_tiling(c->N, overlap ? 1 : n_rhs, c->max_grid);
     int ntiles = tl.tiles * n_rhs;
     if (ntiles > c->max_tiles) return HH_EINVAL;
-    int grid = ntiles < c->max_grid ? ntiles : c->max_grid;
+    const int grid = overlap ? tl.tiles : (ntiles < c->max_grid ? ntiles : c->max_grid);
     std::vector<EngSystem> sys(n_rhs);
     std::vector<EngTile> tiles;
     tiles.reserve(ntiles);
@@ -228,7 +236,7 @@ int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
         }
         Y.ntiles = (int)tiles.size() - Y.tile0;
         Y.part0 = Y.tile0;
-        Y.owner = Y.tile0 % grid;
+        Y.owner = overlap ? a % grid : Y.tile0 % grid;
         Y.precision = c->prm.precision;
         Y.tol2 = c->prm.cg_tol * c->prm.cg_tol;
         Y.delta2 = c->prm.reliable_delta * c->prm.reliable_delta;
@@ -241,8 +249,6 @@ int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
         Y.u = c->u ? c->u + off : nullptr;
     }
     ntiles = (int)tiles.size();
-    grid = ntiles < c->max_grid ? ntiles : c->max_grid;
-    for (auto &Y : sys) Y.owner = Y.tile0 % grid;
     // Pageable sources: the copies have consumed the host buffers on return.
     HH_TRY(cudaMemcpyAsync(c->d_sys, sys.data(), sizeof(EngSystem) * n_rhs, cudaMemcpyHostToDevice,
                            c->stream));
@@ -251,6 +257,7 @@ int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
     P.nsys = n_rhs;
     P.ntiles = ntiles;
     P.grid = grid;
+    P.homogeneous = overlap ? 1 : 0;
     P.b = b;
     P.x = x;
     P.precision = c->prm.precision;
@@ -271,7 +278,7 @@ int run_engine(hh_ctx *c)
     L.tiles = c->d_tiles;
     L.sig = c->d_sig;
     L.sig_stride = c->max_tiles;
-    L.pad = 0;
+    L.ctl_warp = P.homogeneous;
     L.ctl = c->d_ctl;
     L.nsys = P.nsys;
     L.ntiles = P.ntiles;
@@ -280,7 +287,7 @@ int run_engine(hh_ctx *c)
     // sub-steps; the cap is a safety bound well above maxit.
     L.max_iters = (2LL * c->prm.cheb_degree + 1) * (3LL * (long long)c->prm.cg_maxit + 64);
     L.two_slot = c->two_slot;
-    L.pad2 = 0;
+    L.homogeneous = P.homogeneous;
     bool rec = c->profile && c->ev_used + 2 <= c->ev_cap;
     if (rec) HH_TRY(cudaEventRecord(c->ev[c->ev_used], c->stream));
     HH_TRY(engine_launch(L, P.grid, ENGINE_BLOCK, c->stream, c->kind));

@@ -25,12 +25,25 @@ constexpr int kNoConv = -4;
 // ---------------------------------------------------------------------------
 
 // t = M v; acc += t^2.                                      (Eq. (10))
+// The engine block's compute threads: all of its threads in a flat launch,
+// warps 1 .. 15 when warp 0 is the control warp (see the kernel).
+constexpr int kCtlThreads = 32;
+__shared__ int s_ctl_threads;
+__device__ __forceinline__ int ctid()
+{
+    return (int)threadIdx.x - s_ctl_threads;
+}
+__device__ __forceinline__ int cnth()
+{
+    return (int)blockDim.x - s_ctl_threads;
+}
+
 template <int D, typename T, int W>
 __device__ double gloop_M(const Geo g, const T h, const T *__restrict__ L, const T *v, T *t, int b,
                           int e)
 {
     T acc = T(0);
-    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+    for (int i = b + W * ctid(); i < e; i += W * cnth()) {
         GroupNbr nb;
         group_nbrs<D, W>(g, i, nb);
         Vec<T, W> self = vld<T, W>(v + i);
@@ -54,7 +67,7 @@ __device__ double gloop_update(const Geo g, const T h, const T *__restrict__ L, 
                                const T *p, T *r, const T alpha, int b, int e)
 {
     T acc = T(0);
-    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+    for (int i = b + W * ctid(); i < e; i += W * cnth()) {
         GroupNbr nb;
         group_nbrs<D, W>(g, i, nb);
         Vec<T, W> self = vld<T, W>(t + i);
@@ -85,7 +98,7 @@ __device__ double gloop_residual(const Geo g, const double h, const double *__re
                                  int b, int e)
 {
     double acc = 0.0;
-    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+    for (int i = b + W * ctid(); i < e; i += W * cnth()) {
         GroupNbr nb;
         group_nbrs<D, W>(g, i, nb);
         Vec<double, W> self = vld<double, W>(t + i);
@@ -112,7 +125,7 @@ template <int D, int W>
 __device__ void gloop_cheb_u(const Geo g, const double h, const double *__restrict__ L, const double *t,
                              const double *z, double *u, const double invlam, const double a, int b, int e)
 {
-    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+    for (int i = b + W * ctid(); i < e; i += W * cnth()) {
         GroupNbr nb;
         group_nbrs<D, W>(g, i, nb);
         Vec<double, W> self = vld<double, W>(t + i);
@@ -138,7 +151,7 @@ __device__ double gloop_cheb_z(const Geo g, const double h, const double *__rest
                                bool dot, int b, int e)
 {
     double acc = 0.0;
-    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+    for (int i = b + W * ctid(); i < e; i += W * cnth()) {
         GroupNbr nb;
         group_nbrs<D, W>(g, i, nb);
         Vec<double, W> self = vld<double, W>(t + i);
@@ -170,7 +183,7 @@ __device__ double gloop_pM(const Geo g, const T h, const T *__restrict__ L, cons
                            T *pnew, T *t, const T beta, bool restart, int b, int e)
 {
     T acc = T(0);
-    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+    for (int i = b + W * ctid(); i < e; i += W * cnth()) {
         GroupNbr nb;
         group_nbrs<D, W>(g, i, nb);
         auto pn_at = [&](int j) -> T {
@@ -219,7 +232,7 @@ template <int D, int W>
 __device__ void gloop_accM(const Geo g, const double h, const double *__restrict__ L, const double *x,
                            const float *x32, double *t, int b, int e)
 {
-    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+    for (int i = b + W * ctid(); i < e; i += W * cnth()) {
         GroupNbr nb;
         group_nbrs<D, W>(g, i, nb);
         auto xs_at = [&](int j) -> double { return x[j] + (double)x32[j]; };
@@ -258,7 +271,7 @@ __device__ void gloop_accM(const Geo g, const double h, const double *__restrict
 template <typename T, int W>
 __device__ void gloop_direction(const T *r, T *p, const T beta, bool restart, int b, int e)
 {
-    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+    for (int i = b + W * ctid(); i < e; i += W * cnth()) {
         Vec<T, W> rv = vld<T, W>(r + i);
         if (!restart) {
             Vec<T, W> pv = vld<T, W>(p + i);
@@ -273,7 +286,7 @@ __device__ void gloop_direction(const T *r, T *p, const T beta, bool restart, in
 template <int W>
 __device__ void gloop_accumulate(double *x, float *x32, int b, int e)
 {
-    for (int i = b + W * (int)threadIdx.x; i < e; i += W * (int)blockDim.x) {
+    for (int i = b + W * ctid(); i < e; i += W * cnth()) {
         Vec<double, W> xv = vld<double, W>(x + i);
         Vec<float, W> yv = vld<float, W>(x32 + i), z;
 #pragma unroll
@@ -484,7 +497,7 @@ __device__ __forceinline__ float *pbuf32(const EngSystem &Y, int k)
 __device__ double init_residual(const EngSystem &Y, const EngTile &T)
 {
     double acc = 0.0;
-    for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
+    for (int i = T.begin + ctid(); i < T.end; i += cnth()) {
         double bi = __ldg(Y.b + i);
         Y.r[i] = bi;
         if (Y.precision == PREC_MIXED) Y.r32[i] = (float)bi;
@@ -509,9 +522,9 @@ __device__ void slot1(const EngSystem &Y, const TileCtl &c, const EngTile &T)
     } else if (c.mode == MODE_RU) {
         if (c.prec == PREC_MIXED && !c.two) gloop_accumulate<W>(Y.x, Y.x32, T.begin, T.end);
     } else if (c.mode == MODE_INIT) {
-        for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) Y.x[i] = 0.0;
+        for (int i = T.begin + ctid(); i < T.end; i += cnth()) Y.x[i] = 0.0;
         if (Y.precision == PREC_MIXED)
-            for (int i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) Y.x32[i] = 0.0f;
+            for (int i = T.begin + ctid(); i < T.end; i += cnth()) Y.x32[i] = 0.0f;
     }
 }
 
@@ -634,9 +647,38 @@ __device__ double run_slot(const EngSystem &Y, const TileCtl &c, const EngTile &
 constexpr int kCacheSys = 32;
 constexpr int kCacheTiles = 128;
 
+// A task the control warp posts to the compute warps: one slot of one tile.
+struct TaskMsg {
+    TileCtl c;
+    int sl;             // slot kind: 1, 2, 3, or 4 (two-slot first slot)
+    int j;              // index of the tile in this block's list
+    int slot;           // cache index of its system
+    int tile;           // index of the tile in the launch's tile list
+    int exit;           // 1: no more tasks
+    int pad;
+};
+
+// Named barriers of the control / compute hand-off (0 is __syncthreads):
+// kBarReady + b: a task is posted in s_task[b]; kBarDone + b: the compute
+// warps have ended it and written their partials to s_part[b].
+constexpr int kBarReady = 1;
+constexpr int kBarDone = 3;
+
+__device__ __forceinline__ void named_sync(int id, unsigned n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void named_arrive(int id, unsigned n)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 template <int FD, int MINB>
 __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
 {
+    __shared__ TaskMsg s_task[2];
+    __shared__ double s_part[2][ENGINE_BLOCK / 32];
     __shared__ double s_red[ENGINE_BLOCK / 32];
     __shared__ int s_flag;
     __shared__ EngState s_cache[kCacheSys];
@@ -692,15 +734,183 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
         __syncthreads();
     }
 
+    if (!L.ctl_warp) {
+        // ---- flat form: every warp computes; the block waits and decides
+        //      together ----
+        if (threadIdx.x == 0) s_ctl_threads = 0;
+        __syncthreads();
+        const int two = L.two_slot;
+        const int nph = two ? 2 : 3;
+        const size_t stride = (size_t)L.sig_stride;
+        for (long long it = 0; it < L.max_iters; ++it, ++k) {
+            EngState *cur = (k & 1) ? L.state[1] : L.state[0];
+            EngState *nxt = (k & 1) ? L.state[0] : L.state[1];
+            const int q = (int)(k & 1);
+            int live = 0;   // thread 0: a system of this block still runs after this iteration's decisions
+            for (int ph = 0; ph < nph; ++ph) {
+                // Slot of this phase: 1 (decide + direction), 2 (t = M p), 3 (update);
+                // two-slot form: 4 (decide + direction fused with t = M p), 3.
+                const int sl = ph == 0 ? (two ? 4 : 1) : (two ? 3 : ph + 1);
+                // Signal index of this phase and of the one it waits for.
+                const int id = ph == 0 ? 0 : (ph == nph - 1 ? 2 : 1);
+                const int id_prev = ph == 0 ? 2 : (ph == 1 ? 0 : 1);
+                unsigned long long *sig_now = L.sig + (size_t)(2 * id + q) * stride;
+                unsigned long long *sig_next = L.sig + (size_t)(2 * id + (q ^ 1)) * stride;
+                const unsigned long long *sig_wait = L.sig + (size_t)(2 * id_prev + (ph == 0 ? (q ^ 1) : q)) * stride;
+                int last = -1, j = 0;
+                for (int tile = blockIdx.x; tile < L.ntiles; tile += G, ++j) {
+                    const int slot = cached ? s_slot[j] : 0;
+                    const EngTile T = cached ? s_tiles[j] : L.tiles[tile];
+                    const EngSystem &Y = cached ? s_sysd[slot] : L.sys[T.sys];
+                    if (T.sys != last) {
+                        __syncthreads();
+                        if (sl == 1 || sl == 4) {
+                            if (!cached || it == 0) {
+                                if (threadIdx.x == 0) s_cache[slot] = cur[T.sys];
+                                __syncthreads();
+                            }
+                            if (threadIdx.x < 32) {
+                                // Wait for the previous iteration's slot 3 of this system
+                                // (nothing to wait for at its first iteration or when done).
+                                const EngState &P = s_cache[slot];
+                                double rr = 0.0;
+                                bool ok = true;
+                                if (P.mode != MODE_NEW && P.mode != MODE_DONE)
+                                    ok = poll_sum(sig_wait + Y.part0, Y.ntiles, ctl, rr);
+                                if (threadIdx.x == 0) {
+                                    s_flag = ok ? 1 : 0;
+                                    if (ok) {
+                                        EngState S = decide(Y, P, rr);
+                                        if (two && S.mode == MODE_CG) S.pbuf = P.pbuf ^ 1;
+                                        if ((int)blockIdx.x == Y.owner) {
+                                            nxt[T.sys] = S;
+                                            // A finished system's blocks leave at different
+                                            // iterations: keep its final state in both buffers.
+                                            if (S.mode == MODE_DONE && P.mode != MODE_DONE) cur[T.sys] = S;
+                                        }
+                                        if (S.mode != MODE_DONE) live = 1;
+                                        s_cache[slot] = S;
+                                        s_tctl[slot] = make_ctl(S, two);
+                                    }
+                                }
+                            }
+                        } else {
+                            if (!cached && threadIdx.x == 0) {
+                                const EngState S = nxt[T.sys];
+                                s_cache[0] = S;
+                                s_tctl[0] = make_ctl(S, two);
+                            }
+                            __syncthreads();
+                            if (threadIdx.x < 32) {
+                                bool ok = true;
+                                double tt = 0.0;
+                                if (s_tctl[slot].mode != MODE_DONE)
+                                    ok = poll_sum(sig_wait + Y.part0, Y.ntiles, ctl, tt);
+                                if (threadIdx.x == 0) {
+                                    s_flag = ok ? 1 : 0;
+                                    if (ok && sl == 3 && s_tctl[slot].mode == MODE_CG)
+                                        s_tctl[slot].alpha = s_cache[slot].rr_alpha / tt;
+                                }
+                            }
+                        }
+                        __syncthreads();
+                        if (!s_flag) return;
+                        last = T.sys;
+                    }
+                    const TileCtl c = s_tctl[slot];
+                    if (c.mode == MODE_DONE) continue;
+                    double v;
+                    if (sl == 1) {
+                        run_slot<1, FD>(Y, c, T);
+                        v = 0.0;
+                    } else if (sl == 2) {
+                        v = run_slot<2, FD>(Y, c, T);
+                    } else if (sl == 4) {
+                        v = run_slot<4, FD>(Y, c, T);
+                    } else {
+                        v = run_slot<3, FD>(Y, c, T);
+                    }
+                    // |t|^2 (CG, slot 2 or 4), |r|^2 (CG, RU, INIT, slot 3), <r, z>
+                    // after the last preconditioner sub-step, else 0; the block sum
+                    // ends with a __syncthreads() after all of the tile's writes.
+                    const double tot = block_sum(v, s_red);
+                    if (threadIdx.x == 0) sig_publish(sig_now + T.part, sig_next + T.part, tot);
+                }
+                if (ph == 0) {
+                    // Leave once every system of this block is done: no other block
+                    // waits for its tiles any more.
+                    __syncthreads();
+                    if (threadIdx.x == 0) s_flag = live;
+                    __syncthreads();
+                    if (!s_flag) {
+                        if (threadIdx.x == 0) atomicMax((long long *)&ctl->k_end, k + 1);
+                        return;
+                    }
+                }
+            }
+        }
+        if (threadIdx.x == 0) atomicMax((long long *)&ctl->k_end, k);
+        return;
+    }
+
+    if (threadIdx.x == 0) s_ctl_threads = kCtlThreads;
+    __syncthreads();
+    if (threadIdx.x >= kCtlThreads) {
+        // ---- compute warps: run the tasks the control warp posts ----
+        const int warp = ((int)threadIdx.x >> 5) - 1;
+        for (int buf = 0;; buf ^= 1) {
+            named_sync(kBarReady + buf, blockDim.x);
+            const TaskMsg m = s_task[buf];
+            if (m.exit) return;
+            const EngTile T = cached ? s_tiles[m.j] : L.tiles[m.tile];
+            const EngSystem &Y = cached ? s_sysd[m.slot] : L.sys[T.sys];
+            double v = 0.0;
+            if (m.sl == 1)
+                run_slot<1, FD>(Y, m.c, T);
+            else if (m.sl == 2)
+                v = run_slot<2, FD>(Y, m.c, T);
+            else if (m.sl == 4)
+                v = run_slot<4, FD>(Y, m.c, T);
+            else
+                v = run_slot<3, FD>(Y, m.c, T);
+            // |t|^2 (CG, slot 2 or 4), |r|^2 (CG, RU, INIT, slot 3), <r, z>
+            // after the last preconditioner sub-step, else 0.
+            v = warp_sum(v);
+            if ((threadIdx.x & 31u) == 0) s_part[buf][warp] = v;
+            named_arrive(kBarDone + buf, blockDim.x);
+        }
+    }
+
+    // ---- control warp: waits, decisions, partial sums and signals ----
+    const int lane = (int)threadIdx.x;
+    const int ncw = (int)(blockDim.x >> 5) - 1;   // compute warps
     const int two = L.two_slot;
     const int nph = two ? 2 : 3;
     const size_t stride = (size_t)L.sig_stride;
-    for (long long it = 0; it < L.max_iters; ++it, ++k) {
+    int buf = 0;
+    // The posted task whose end has not been published yet.
+    bool pend = false, failed = false, stop = false;
+    int pend_buf = 0, pend_part = 0, pend_sys = -1;
+    long long pend_level = 0;
+    unsigned long long *pend_now = nullptr, *pend_next = nullptr;
+    // Waits for the compute warps to end the pending task, then publishes its
+    // partial (the sum of the per-warp partials in warp order).
+    auto finish = [&]() {
+        named_sync(kBarDone + pend_buf, blockDim.x);
+        if (lane == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < ncw; ++w) tot += s_part[pend_buf][w];
+            if (!failed) sig_publish(pend_now + pend_part, pend_next + pend_part, tot);
+        }
+        __syncwarp();
+        pend = false;
+    };
+    for (long long it = 0; it < L.max_iters && !failed && !stop; ++it, ++k) {
         EngState *cur = (k & 1) ? L.state[1] : L.state[0];
         EngState *nxt = (k & 1) ? L.state[0] : L.state[1];
         const int q = (int)(k & 1);
-        int live = 0;   // thread 0: a system of this block still runs after this iteration's decisions
-        for (int ph = 0; ph < nph; ++ph) {
+        int live = 0;   // lane 0: a system of this block still runs after this iteration's decisions
+        for (int ph = 0; ph < nph && !failed && !stop; ++ph) {
             // Slot of this phase: 1 (decide + direction), 2 (t = M p), 3 (update);
             // two-slot form: 4 (decide + direction fused with t = M p), 3.
             const int sl = ph == 0 ? (two ? 4 : 1) : (two ? 3 : ph + 1);
@@ -710,99 +920,107 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
             unsigned long long *sig_now = L.sig + (size_t)(2 * id + q) * stride;
             unsigned long long *sig_next = L.sig + (size_t)(2 * id + (q ^ 1)) * stride;
             const unsigned long long *sig_wait = L.sig + (size_t)(2 * id_prev + (ph == 0 ? (q ^ 1) : q)) * stride;
+            const long long level = it * nph + ph;
             int last = -1, j = 0;
             for (int tile = blockIdx.x; tile < L.ntiles; tile += G, ++j) {
                 const int slot = cached ? s_slot[j] : 0;
                 const EngTile T = cached ? s_tiles[j] : L.tiles[tile];
                 const EngSystem &Y = cached ? s_sysd[slot] : L.sys[T.sys];
                 if (T.sys != last) {
-                    __syncthreads();
+                    // The wait below may need the pending task's signal: its own
+                    // system's, or, through another block, any of an earlier
+                    // phase.  Publish it first, unless it is of another system
+                    // and the phase is the same or every block runs the same
+                    // sequence of systems (then the wait needs signals of tasks
+                    // two or more places back, all published).
+                    if (pend && (pend_sys == T.sys || (!L.homogeneous && pend_level != level))) finish();
+                    bool ok = true;
                     if (sl == 1 || sl == 4) {
                         if (!cached || it == 0) {
-                            if (threadIdx.x == 0) s_cache[slot] = cur[T.sys];
-                            __syncthreads();
+                            if (lane == 0) s_cache[slot] = cur[T.sys];
+                            __syncwarp();
                         }
-                        if (threadIdx.x < 32) {
-                            // Wait for the previous iteration's slot 3 of this system
-                            // (nothing to wait for at its first iteration or when done).
-                            const EngState &P = s_cache[slot];
-                            double rr = 0.0;
-                            bool ok = true;
-                            if (P.mode != MODE_NEW && P.mode != MODE_DONE)
-                                ok = poll_sum(sig_wait + Y.part0, Y.ntiles, ctl, rr);
-                            if (threadIdx.x == 0) {
-                                s_flag = ok ? 1 : 0;
-                                if (ok) {
-                                    EngState S = decide(Y, P, rr);
-                                    if (two && S.mode == MODE_CG) S.pbuf = P.pbuf ^ 1;
-                                    if ((int)blockIdx.x == Y.owner) {
-                                        nxt[T.sys] = S;
-                                        // A finished system's blocks leave at different
-                                        // iterations: keep its final state in both buffers.
-                                        if (S.mode == MODE_DONE && P.mode != MODE_DONE) cur[T.sys] = S;
-                                    }
-                                    if (S.mode != MODE_DONE) live = 1;
-                                    s_cache[slot] = S;
-                                    s_tctl[slot] = make_ctl(S, two);
-                                }
+                        const int pm = s_cache[slot].mode;
+                        double rr = 0.0;
+                        // Nothing to wait for at a system's first iteration or once done.
+                        if (pm != MODE_NEW && pm != MODE_DONE) ok = poll_sum(sig_wait + Y.part0, Y.ntiles, ctl, rr);
+                        if (ok && lane == 0) {
+                            const EngState P = s_cache[slot];
+                            EngState S = decide(Y, P, rr);
+                            if (two && S.mode == MODE_CG) S.pbuf = P.pbuf ^ 1;
+                            if ((int)blockIdx.x == Y.owner) {
+                                nxt[T.sys] = S;
+                                // A finished system's blocks leave at different
+                                // iterations: keep its final state in both buffers.
+                                if (S.mode == MODE_DONE && P.mode != MODE_DONE) cur[T.sys] = S;
                             }
+                            if (S.mode != MODE_DONE) live = 1;
+                            s_cache[slot] = S;
+                            s_tctl[slot] = make_ctl(S, two);
                         }
                     } else {
-                        if (!cached && threadIdx.x == 0) {
-                            const EngState S = nxt[T.sys];
-                            s_cache[0] = S;
-                            s_tctl[0] = make_ctl(S, two);
-                        }
-                        __syncthreads();
-                        if (threadIdx.x < 32) {
-                            bool ok = true;
-                            double tt = 0.0;
-                            if (s_tctl[slot].mode != MODE_DONE)
-                                ok = poll_sum(sig_wait + Y.part0, Y.ntiles, ctl, tt);
-                            if (threadIdx.x == 0) {
-                                s_flag = ok ? 1 : 0;
-                                if (ok && sl == 3 && s_tctl[slot].mode == MODE_CG)
-                                    s_tctl[slot].alpha = s_cache[slot].rr_alpha / tt;
+                        if (!cached) {
+                            if (lane == 0) {
+                                const EngState S = nxt[T.sys];
+                                s_cache[0] = S;
+                                s_tctl[0] = make_ctl(S, two);
                             }
+                            __syncwarp();
                         }
+                        const int m = s_tctl[slot].mode;
+                        double tt = 0.0;
+                        if (m != MODE_DONE) ok = poll_sum(sig_wait + Y.part0, Y.ntiles, ctl, tt);
+                        if (ok && lane == 0 && sl == 3 && m == MODE_CG)
+                            s_tctl[slot].alpha = s_cache[slot].rr_alpha / tt;
                     }
-                    __syncthreads();
-                    if (!s_flag) return;
+                    __syncwarp();
+                    if (!ok) {
+                        failed = true;
+                        break;
+                    }
                     last = T.sys;
                 }
                 const TileCtl c = s_tctl[slot];
                 if (c.mode == MODE_DONE) continue;
-                double v;
-                if (sl == 1) {
-                    run_slot<1, FD>(Y, c, T);
-                    v = 0.0;
-                } else if (sl == 2) {
-                    v = run_slot<2, FD>(Y, c, T);
-                } else if (sl == 4) {
-                    v = run_slot<4, FD>(Y, c, T);
-                } else {
-                    v = run_slot<3, FD>(Y, c, T);
+                if (lane == 0) {
+                    TaskMsg &m = s_task[buf];
+                    m.c = c;
+                    m.sl = sl;
+                    m.j = j;
+                    m.slot = slot;
+                    m.tile = tile;
+                    m.exit = 0;
                 }
-                // |t|^2 (CG, slot 2 or 4), |r|^2 (CG, RU, INIT, slot 3), <r, z>
-                // after the last preconditioner sub-step, else 0; the block sum
-                // ends with a __syncthreads() after all of the tile's writes.
-                const double tot = block_sum(v, s_red);
-                if (threadIdx.x == 0) sig_publish(sig_now + T.part, sig_next + T.part, tot);
+                __syncwarp();
+                named_arrive(kBarReady + buf, blockDim.x);
+                if (pend) finish();
+                pend = true;
+                pend_buf = buf;
+                pend_part = T.part;
+                pend_level = level;
+                pend_sys = T.sys;
+                pend_now = sig_now;
+                pend_next = sig_next;
+                buf ^= 1;
             }
-            if (ph == 0) {
+            if (ph == 0 && !failed) {
                 // Leave once every system of this block is done: no other block
                 // waits for its tiles any more.
-                __syncthreads();
-                if (threadIdx.x == 0) s_flag = live;
-                __syncthreads();
-                if (!s_flag) {
-                    if (threadIdx.x == 0) atomicMax((long long *)&ctl->k_end, k + 1);
-                    return;
+                live = __shfl_sync(0xffffffffu, live, 0);
+                if (!live) {
+                    if (lane == 0) atomicMax((long long *)&ctl->k_end, k + 1);
+                    stop = true;
                 }
             }
         }
     }
-    if (threadIdx.x == 0) atomicMax((long long *)&ctl->k_end, k);
+    if (pend) finish();
+    if (lane == 0) {
+        s_task[buf].exit = 1;
+        if (!stop && !failed) atomicMax((long long *)&ctl->k_end, k);
+    }
+    __syncwarp();
+    named_arrive(kBarReady + buf, blockDim.x);
 }
 
 }  // namespace
@@ -840,6 +1058,14 @@ int engine_max_grid(int block, int kind)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel_of(kind), block, 0) != cudaSuccess)
         return 0;
     return per * nsm;
+}
+
+bool engine_overlap(int nsys, long long sites, bool mixed)
+{
+    const char *env = getenv("HH_ENGINE_OVERLAP");
+    if (nsys < 2) return false;
+    if (env) return atoi(env) != 0;
+    return sites >= (mixed ? (1LL << 21) : (1LL << 18));
 }
 
 int engine_two_slot(int kind)

@@ -130,12 +130,13 @@ struct EngLaunch {
     // slots must be empty (kSigEmpty) when it enters as MODE_NEW.
     unsigned long long *sig;
     int sig_stride;
-    int pad;
+    int ctl_warp;           // 1: warp 0 is a control warp (see the kernel); 0: flat
     EngCtl *ctl;
     int nsys, ntiles;
     long long max_iters;    // engine iterations this launch may run
     int two_slot;           // 1: two phases per iteration (see above)
-    int pad2;
+    int homogeneous;        // 1: every block holds one tile of each of the (two or
+                            // more) systems, in the same order (requires ctl_warp)
 };
 
 // Signal slots needed for 'parts' tile partial indices.
@@ -172,6 +173,10 @@ int engine_default_grid(int kind);
 // ENGINE_D1 only; HH_ENGINE_SLOTS=2 or 3 forces one form.  The forms give
 // bitwise identical results.
 int engine_two_slot(int kind);
+
+// Whether a launch of nsys systems of 'sites' sites each uses the overlapped
+// layout (see EngLaunch::homogeneous); HH_ENGINE_OVERLAP=0 or 1 forces it.
+bool engine_overlap(int nsys, long long sites, bool mixed);
 
 // Tiles of one system: 'tiles' contiguous ranges of 'chunk' sites (the last
 // one shorter), enough to give every block of the grid a tile when 'nsys'

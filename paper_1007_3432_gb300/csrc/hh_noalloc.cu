@@ -175,13 +175,13 @@ extern "C" int hh_solve_noalloc(const hh_lattice *lat, const hh_params *p, const
     L.tiles = (const EngTile *)(base + kOffTiles);
     L.sig = (unsigned long long *)(base + kOffSig);
     L.sig_stride = kMaxTiles;
-    L.pad = 0;
+    L.ctl_warp = 0;
     L.ctl = (EngCtl *)(base + kOffCtl);
     L.nsys = 1;
     L.ntiles = ntiles;
     L.max_iters = 3LL * (long long)p->cg_maxit + 64;
     L.two_slot = 0;     // one p buffer in the static scratch
-    L.pad2 = 0;
+    L.homogeneous = 0;
     if (engine_launch(L, grid, ENGINE_BLOCK, st, lat->d == 1 ? ENGINE_D1 : ENGINE_D3) != cudaSuccess)
         return HH_ECUDA;
     if (!info) return HH_OK;
