@@ -122,6 +122,7 @@ def cheb_poly(n, eps, z):
 
 
 def cheb_apply(lat, h, L, n, eps, lam, x):
+    assert 0 <= n <= 64
     x = np.ascontiguousarray(x, dtype=np.float64)
     L = np.ascontiguousarray(L, dtype=np.float64)
     y = np.empty(nsites(lat))
@@ -132,6 +133,7 @@ def cheb_apply(lat, h, L, n, eps, lam, x):
 
 def pcg(lat, h, L, b, n, eps, lam, tol=1e-10, maxit=100000):
     """Chebyshev-preconditioned CG; returns (x, status, iterations, true_relres)."""
+    assert 0 <= n <= 64
     b = np.ascontiguousarray(b, dtype=np.float64)
     L = np.ascontiguousarray(L, dtype=np.float64)
     x = np.empty(nsites(lat))

@@ -259,9 +259,49 @@ double oracle_cheb_poly(int n, double eps, double z)
     return pr;
 }
 
+/* Order of the real factors.  Sec. 4.2 leaves the ordering of the roots open
+ * (it points to an optimised one without giving it).  Applied to a vector,
+ * each factor's rounding error is relative to the whole vector, and the
+ * factors after it amplify it by the spread max_z / min_z of their product on
+ * [0, 1]; in the order k = 1..n that spread reaches 1e31 at n = 32.  Reading:
+ * Leja order of the real parts a_k (Reichel, BIT 30 (1990) 332): start with
+ * the largest a_k, then repeatedly take the a_k that maximises the product of
+ * its distances to those already taken (ties: the smallest k).  The spread
+ * then stays below 1e8 up to n = 64. */
+static void cheb_order(int n, double eps, int *order)
+{
+    double a[64], im;
+    int used[64];
+    for (int k = 1; k <= n; ++k) {
+        cheb_root(n, eps, k, &a[k - 1], &im);
+        used[k - 1] = 0;
+    }
+    int first = 0;
+    for (int k = 1; k < n; ++k)
+        if (fabs(a[k]) > fabs(a[first])) first = k;
+    order[0] = first + 1;
+    used[first] = 1;
+    for (int j = 1; j < n; ++j) {
+        int best = -1;
+        double bv = 0.0;
+        for (int k = 0; k < n; ++k) {
+            if (used[k]) continue;
+            double v = 0.0;
+            for (int i = 0; i < j; ++i) v += log(fabs(a[k] - a[order[i] - 1]));
+            if (best < 0 || v > bv) {
+                best = k;
+                bv = v;
+            }
+        }
+        order[j] = best + 1;
+        used[best] = 1;
+    }
+}
+
 /* y = P(Q/lam) x: the conjugate pair k, 2n+1-k gives the real factor
  * ((Q/lam - a)^2 + b^2) / ((m - a)^2 + b^2) with a = Re z_k, b = Im z_k;
- * factors applied for k = 1..n, then the overall 1/m. */
+ * factors applied in the order of cheb_order(), then the overall 1/m
+ * (n <= 64). */
 void oracle_cheb_apply(const oracle_lattice *lat, double h, const double *L, int n, double eps,
                        double lam, const double *x, double *y)
 {
@@ -271,9 +311,11 @@ void oracle_cheb_apply(const oracle_lattice *lat, double h, const double *L, int
     double *u = (double *)malloc(sizeof(double) * (size_t)N);
     double *w = (double *)malloc(sizeof(double) * (size_t)N);
     for (long i = 0; i < N; ++i) v[i] = x[i];
-    for (int k = 1; k <= n; ++k) {
+    int order[64];
+    cheb_order(n, eps, order);
+    for (int j = 0; j < n; ++j) {
         double a, b;
-        cheb_root(n, eps, k, &a, &b);
+        cheb_root(n, eps, order[j], &a, &b);
         double qm = (m - a) * (m - a) + b * b;
         /* u = (Q/lam - a) v */
         oracle_apply_MTM(lat, h, L, v, w);

@@ -73,7 +73,9 @@ int oracle_cg(const oracle_lattice *lat, double h, const double *L, const double
  * Roots z_k = m (1 - cos(2 pi k/(2n+1))) - i sqrt(eps) sin(2 pi k/(2n+1)),
  * m = (1 + eps)/2, k = 1..2n, for Q normalised to eigenvalues in [0, 1]. */
 double oracle_cheb_poly(int n, double eps, double z);
-/* y = P(Q/lam) x (normalisation lam >= lambda_max(Q)). */
+/* y = P(Q/lam) x (normalisation lam >= lambda_max(Q); n <= 64), as n real
+ * quadratic factors in the Leja order of their centres (a reading: the paper
+ * leaves the ordering open). */
 void oracle_cheb_apply(const oracle_lattice *lat, double h, const double *L, int n, double eps,
                        double lam, const double *x, double *y);
 /* Preconditioned CG with preconditioner P(Q/lam); x0 = 0; stop on the true

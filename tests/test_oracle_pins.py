@@ -495,6 +495,26 @@ def test_chebyshev_operator_is_spd_and_commutes(orc):
     assert np.allclose(P @ Q, Q @ P, atol=1e-10)
 
 
+@pytest.mark.parametrize("n,eps", [(8, 1e-4), (32, 1e-5), (64, 1e-6)])
+def test_chebyshev_apply_matches_spectral_evaluation(orc, n, eps):
+    """Random field: P(Q/lam) b from the factors equals V P(Lambda/lam) V^T b from
+    the eigendecomposition of the dense Q, with P evaluated as the scalar product
+    over all 2n roots (Eq. (15)).  Multiplying scalars keeps the relative
+    precision in any order; applied to a vector the order of the factors
+    matters, and the order k = 1..n misses this by many orders of magnitude at
+    n = 32 and 64."""
+    lat = orc.lattice(1, 8, 12)
+    nsite = orc.nsites(lat)
+    rng = np.random.default_rng(21)
+    L = orc.links(lat, 0.5, rng.uniform(-np.pi, np.pi, nsite))
+    lam = orc.gershgorin_lambda_max(1, H, 0.5)
+    b = rng.standard_normal(nsite)
+    w, V = np.linalg.eigh(orc.dense(lat, H, L, "MTM"))
+    ref = V @ (np.array([orc.cheb_poly(n, eps, z / lam) for z in w]) * (V.T @ b))
+    got = orc.cheb_apply(lat, H, L, n, eps, lam, b)
+    assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
 @pytest.mark.parametrize("d,nx,ntau", [(1, 8, 12), (3, 3, 4)])
 def test_pcg_matches_dense_lu(orc, d, nx, ntau):
     lat = orc.lattice(d, nx, ntau)
