@@ -255,7 +255,7 @@ def run_part(args, wl, world, rank, local, dev, stream):
     from paper_1007_3432_gb300.binding import HH_ENOCONV
     n = wl.nsites
     ctx = Context(wl.d, wl.nx, wl.ntau, seed=wl.seed, chain_id=rank, precision=args.precision,
-                  cg_maxit=args.cg_maxit, stream=stream)
+                  cg_maxit=args.cg_maxit, stream=stream, cheb_degree=args.cheb, cheb_eps=args.cheb_eps)
     ctx.set_field(torch.from_numpy(workloads.sigma_field(n, seed=wl.seed, chain=rank)).to(dev))
     flush = L2Flush(dev)
     if args.mode == "solve":
@@ -306,8 +306,13 @@ def run_part(args, wl, world, rank, local, dev, stream):
         units = sum_over_ranks(world, float(cnt["solves"]))
         unit = "CG solves/s"
         eng_s = cnt["engine_ms"] / 1000.0
+        # With the Chebyshev preconditioner every CG step and true-residual check
+        # is followed by 2n sub-steps, each one Q apply with its vector update
+        # (counted at the flops of a CG step).
+        q_per_step = 2 * args.cheb + 1
         if args.precision == "fp64":
             flops = n * (cnt["cg_steps"] * flops_per_site(wl.d, "cg", "fp64") + cnt["ru_steps"] * flops_per_site(wl.d, "ru", "fp64"))
+            flops += n * (cnt["cg_steps"] + cnt["ru_steps"]) * (q_per_step - 1) * flops_per_site(wl.d, "cg", "fp64")
             ach = flops / eng_s / 1e12
             roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak_tflops(), "unit": "TFLOP/s",
                     "frac": ach / fp64_peak_tflops(), "traffic": None, "kernel": "engine_kernel (FP64 CG)"}
@@ -317,7 +322,8 @@ def run_part(args, wl, world, rank, local, dev, stream):
             roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "engine_kernel (FP32-inner CG)"}
         extra = {"cg_steps_per_solve": cnt["cg_steps"] / max(1, cnt["solves"]),
-                 "ru_steps": cnt["ru_steps"], "fp64_steps": cnt["fp64_steps"]}
+                 "q_applies_per_solve": (cnt["cg_steps"] + cnt["ru_steps"]) * q_per_step / max(1, cnt["solves"]),
+                 "ru_steps": cnt["ru_steps"], "fp64_steps": cnt["fp64_steps"], "cheb_degree": args.cheb}
         e2e_bytes = (n * 16, n * 16)
     else:
         units = float(world * args.steps)
@@ -334,7 +340,9 @@ def run_part(args, wl, world, rank, local, dev, stream):
             "warmup": args.warmup, "ms_per_step": 1000.0 * t_dev / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else ("f32" if args.mode == "apply" else "f32+f64"),
-            "data": "synthetic", "config": dict(config_of(args, wl), mode=args.mode),
+            "data": "synthetic", "config": dict(config_of(args, wl), mode=args.mode,
+                                                **({"cheb_degree": args.cheb, "cheb_eps": args.cheb_eps}
+                                                   if args.cheb else {})),
             "e2e": {"value": units / t_wall, "unit": unit, "h2d_bytes_per_step": e2e_bytes[0],
                     "d2h_bytes_per_step": e2e_bytes[1]},
             "gpu_launches": int(cnt["kernel_launches"]), "clocks": clk, "roofline": roof}
@@ -423,6 +431,18 @@ def run_batch(args, world, rank, local, dev, stream):
         print(json.dumps(line), flush=True)
 
 
+def solver_for(r):
+    """Solver of a served request.  d = 1 lattices with N_tau >= 256 (beta >= 12.8)
+    use FP64 CG with the Chebyshev preconditioner of Sec. 4.2 (n = 8, eps =
+    1e-4): on some of them plain CG, FP64 or mixed, stalls near a relative
+    residual of 1e-7 (1255 x 504, seed 101103049: 400k FP64 CG steps reach
+    1.4e-7; the preconditioned solve converges in 4.2k steps).  The others use
+    mixed precision."""
+    if r.d == 1 and r.ntau >= 256:
+        return {"precision": "fp64", "cheb_degree": 8, "cheb_eps": 1e-4}
+    return {"precision": "mixed"}
+
+
 def run_serve(args, world, rank, local, dev, stream):
     """Poisson arrivals of solve and trajectory requests, served by the
     continuous-batching worker thread; p50/p99 latency and solves/s per rate."""
@@ -442,13 +462,13 @@ def run_serve(args, world, rank, local, dev, stream):
             while time.perf_counter() - t0 < r.arrival_s:
                 time.sleep(0.0002)
             sigma = workloads.sigma_field(r.nsites, seed=r.seed)
+            prm = solver_for(r)
             if r.kind == "solve":
-                req = B.make_request(HH_REQ_SOLVE, r.d, r.nx, r.ntau, sigma=sigma, precision="mixed",
-                                     seed=r.seed, n_pf=2, traj_index=r.rid)
+                req = B.make_request(HH_REQ_SOLVE, r.d, r.nx, r.ntau, sigma=sigma, seed=r.seed, n_pf=2,
+                                     traj_index=r.rid, **prm)
             else:
-                req = B.make_request(HH_REQ_TRAJECTORY, r.d, r.nx, r.ntau, sigma=sigma, precision="mixed",
-                                     seed=r.seed, n_pf=2, n_md=args.serve_n_md, dt=1.0 / args.serve_n_md,
-                                     traj_index=r.rid)
+                req = B.make_request(HH_REQ_TRAJECTORY, r.d, r.nx, r.ntau, sigma=sigma, seed=r.seed, n_pf=2,
+                                     n_md=args.serve_n_md, dt=1.0 / args.serve_n_md, traj_index=r.rid, **prm)
             keep.append(sigma)
             batch.submit(req)
             got += batch.poll()
@@ -478,7 +498,8 @@ def run_serve(args, world, rank, local, dev, stream):
             "data": "synthetic",
             "config": {"workload": "serve_poisson", "seed": workloads.SERVE_SEED, "requests_per_rate": args.requests,
                        "d1": {"nx": [64, 2048], "ntau": [64, 512]}, "d3": {"nx": [8, 24], "ntau": [40, 256]},
-                       "trajectory_n_md": args.serve_n_md, "hbm_budget_gb": args.budget_gb, "precision": "mixed",
+                       "trajectory_n_md": args.serve_n_md, "hbm_budget_gb": args.budget_gb,
+                       "precision": "mixed; FP64 + Chebyshev n=8 eps=1e-4 for d=1 with N_tau >= 256",
                        "mode": "serve", "parallelism": "replicas%d" % world},
             "per_rate": per_rate, "e2e": None, "gpu_launches": None}
     if rank == 0:
@@ -498,6 +519,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--mode", default="trajectory", choices=["trajectory", "solve", "apply", "batch", "serve"])
     ap.add_argument("--cg-maxit", type=int, default=1000000)
+    ap.add_argument("--cheb", type=int, default=0, help="solve mode: Chebyshev preconditioner degree n (FP64)")
+    ap.add_argument("--cheb-eps", type=float, default=1e-4)
     ap.add_argument("--rates", default="10,100,1000")
     ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--serve-n-md", type=int, default=4)

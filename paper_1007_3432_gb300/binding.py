@@ -304,7 +304,7 @@ def solve_noalloc(d, nx, ntau, sigma, b, x, t=1.0, dtau=0.05, A=0.5, cg_tol=1e-1
 
 
 def make_params(t=1.0, dtau=0.05, A=0.5, precision=HH_FP64, cg_tol=1e-10, cg_maxit=1000000,
-                reliable_delta=0.1, seed=0, n_pf=2, chain_id=0):
+                reliable_delta=0.1, seed=0, n_pf=2, chain_id=0, cheb_degree=0, cheb_eps=1e-3):
     L = load()
     p = hh_params()
     L.hh_default_params(ctypes.byref(p))
@@ -312,6 +312,7 @@ def make_params(t=1.0, dtau=0.05, A=0.5, precision=HH_FP64, cg_tol=1e-10, cg_max
     p.precision = {"fp64": HH_FP64, "mixed": HH_MIXED}.get(precision, precision)
     p.cg_tol, p.cg_maxit, p.reliable_delta = cg_tol, cg_maxit, reliable_delta
     p.seed, p.n_pf, p.chain_id = seed, n_pf, chain_id
+    p.cheb_degree, p.cheb_eps = cheb_degree, cheb_eps
     return p
 
 

@@ -134,10 +134,11 @@ struct Pending {
 struct SlotMem {
     double *sigma, *sigma0, *L64, *pi, *tmp, *chi, *x, *r, *p, *p2, *t, *epart;
     float *L32, *r32, *p32, *p32b, *t32, *x32;
+    double *z, *u, *cheb;   // Chebyshev preconditioner (requests with cheb_degree > 0)
     HmcScalars *sc;
 };
 
-size_t slot_bytes(long long N, int nrhs, SlotMem *m, char *base)
+size_t slot_bytes(long long N, int nrhs, bool cheb, SlotMem *m, char *base)
 {
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -166,6 +167,12 @@ size_t slot_bytes(long long N, int nrhs, SlotMem *m, char *base)
     p = take(nrhs * N * f); if (m) m->x32 = (float *)p;
     p = take(sizeof(HmcScalars)); if (m) m->sc = (HmcScalars *)p;
     p = take(energy_blocks((int)N) * d); if (m) m->epart = (double *)p;
+    if (m) m->z = m->u = m->cheb = nullptr;
+    if (cheb) {
+        p = take(nrhs * N * d); if (m) m->z = (double *)p;
+        p = take(nrhs * N * d); if (m) m->u = (double *)p;
+        p = take((2 + 3 * CHEB_MAX_DEGREE) * d); if (m) m->cheb = (double *)p;
+    }
     return off;
 }
 
@@ -264,7 +271,10 @@ int validate(const hh_request &r)
     if (r.prm.precision != HH_FP64 && r.prm.precision != HH_MIXED) return HH_EINVAL;
     if (!(r.prm.cg_tol > 0.0) || r.prm.cg_maxit < 1) return HH_EINVAL;
     if (r.kind == HH_REQ_TRAJECTORY && r.n_md < 1) return HH_EINVAL;
-    if (r.prm.cheb_degree != 0) return HH_EINVAL;  // the batch engine runs plain CG
+    // Chebyshev-preconditioned CG (Sec. 4.2) is FP64 only, as in the context solver.
+    if (r.prm.cheb_degree < 0 || r.prm.cheb_degree > CHEB_MAX_DEGREE) return HH_EINVAL;
+    if (r.prm.cheb_degree > 0 && (r.prm.precision != HH_FP64 || !(r.prm.cheb_eps > 0.0 && r.prm.cheb_eps < 1.0)))
+        return HH_EINVAL;
     return HH_OK;
 }
 
@@ -324,7 +334,7 @@ int admit(hh_batch *b, Pending &P, int s)
     S.cg_iters = 0;
     S.n_ru = S.n_solves = S.status = 0;
     S.max_relres = 0.0;
-    slot_bytes(S.N, S.nrhs, &S.m, b->arena.base + S.off);
+    slot_bytes(S.N, S.nrhs, r.prm.cheb_degree > 0, &S.m, b->arena.base + S.off);
     b->active_sites += S.N;
     b->n_active += 1;
     const uint64_t seed = r.prm.seed, chain = r.prm.chain_id;
@@ -336,6 +346,12 @@ int admit(hh_batch *b, Pending &P, int s)
         HB_TRY(launch_init_field(S.m.sigma, S.N, seed, chain, st));
     HB_TRY(launch_links(S.geo, r.prm.A, S.m.sigma, S.m.L64, S.m.L32, st));
     HB_TRY(cudaMemsetAsync(S.m.sc, 0, sizeof(HmcScalars), st));
+    if (S.m.cheb) {
+        // Pageable source: the copy has consumed the host table on return.
+        std::vector<double> tab(2 + 3 * CHEB_MAX_DEGREE);
+        engine_cheb_table(r.lat.d, h, r.prm.A, r.prm.cheb_degree, r.prm.cheb_eps, tab.data());
+        HB_TRY(cudaMemcpyAsync(S.m.cheb, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st));
+    }
     if (r.kind == HH_REQ_SOLVE) {
         if (!P.b.empty()) {
             HB_TRY(cudaMemcpyAsync(S.m.chi, P.b.data(), sizeof(double) * S.N * S.nrhs,
@@ -376,7 +392,7 @@ int admit_queued(hh_batch *b)
                     break;
                 }
             if (s < 0) return HH_OK;
-            size_t bytes = slot_bytes(N, front.req.prm.n_pf, nullptr, nullptr);
+            size_t bytes = slot_bytes(N, front.req.prm.n_pf, front.req.prm.cheb_degree > 0, nullptr, nullptr);
             int tpr = (int)((N + b->cfg.tile_sites - 1) / b->cfg.tile_sites);
             int part = b->parts.alloc(tpr * front.req.prm.n_pf);
             if (part < 0) return HH_OK;
@@ -431,6 +447,10 @@ int build_plan(hh_batch *b)
             Y.maxit = S.req.prm.cg_maxit;
             Y.w = engine_group_width(S.geo.nx);
             Y.stall_window = ENGINE_STALL_WINDOW;
+            Y.cheb_n = S.req.prm.cheb_degree;
+            Y.cheb = S.m.cheb;
+            Y.z = S.m.z ? S.m.z + o : nullptr;
+            Y.u = S.m.u ? S.m.u + o : nullptr;
             Y.tile0 = (int)b->h_tiles.size();
             Y.part0 = S.part_off + a * S.tiles_per_rhs;
             for (int s0 = 0, j = 0; s0 < S.N; s0 += tile, ++j) {
@@ -795,7 +815,7 @@ int hh_batch_submit(hh_batch *b, const hh_request *req, uint64_t *ticket)
     int rc = validate(*req);
     if (rc) return rc;
     long long N = lattice_sites(req->lat);
-    if (slot_bytes(N, req->prm.n_pf, nullptr, nullptr) > b->arena.size) return HH_EBUSY;
+    if (slot_bytes(N, req->prm.n_pf, req->prm.cheb_degree > 0, nullptr, nullptr) > b->arena.size) return HH_EBUSY;
     Pending P;
     P.req = *req;
     if (req->sigma) P.sigma.assign(req->sigma, req->sigma + N);

@@ -450,24 +450,8 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
         if (e == cudaSuccess) e = dalloc(&c->u, nr);
         if (e == cudaSuccess) e = dalloc(&c->d_cheb, (size_t)(2 + 3 * CHEB_MAX_DEGREE));
         if (e == cudaSuccess) {
-            // Sec. 4.2: roots z_k = m (1 - cos th_k) - i sqrt(eps) sin th_k,
-            // th_k = 2 pi k / (2n + 1), m = (1 + eps)/2, for Q / lam with lam the
-            // Gershgorin bound of its spectrum: each row of M has the unit
-            // diagonal, 2d hops of h and one link of size <= 1 + A.
-            const double pi = 3.14159265358979323846;
-            const double h = p->t * p->dtau, eps = p->cheb_eps, m = 0.5 * (1.0 + eps);
-            const double rowsum = 2.0 + 2.0 * lat->d * fabs(h) + fabs(p->A);
-            const double lam = rowsum * rowsum;
-            std::vector<double> tab(2 + 3 * CHEB_MAX_DEGREE, 0.0);
-            tab[0] = 1.0 / lam;
-            tab[1] = 1.0 / m;
-            for (int k = 1; k <= p->cheb_degree; ++k) {
-                double th = 2.0 * pi * k / (2.0 * p->cheb_degree + 1.0);
-                double a = m * (1.0 - cos(th)), b = sqrt(eps) * sin(th);
-                tab[2 + 3 * (k - 1)] = a;
-                tab[3 + 3 * (k - 1)] = b * b;
-                tab[4 + 3 * (k - 1)] = 1.0 / ((m - a) * (m - a) + b * b);
-            }
+            std::vector<double> tab(2 + 3 * CHEB_MAX_DEGREE);
+            engine_cheb_table(lat->d, p->t * p->dtau, p->A, p->cheb_degree, p->cheb_eps, tab.data());
             e = cudaMemcpy(c->d_cheb, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
         }
     }

@@ -174,6 +174,11 @@ int engine_default_grid(int kind);
 // bitwise identical results.
 int engine_two_slot(int kind);
 
+// Coefficient table of the Chebyshev preconditioner of degree n (see
+// CHEB_MAX_DEGREE) for the lattice dimension d, hop h = t dtau and coupling A:
+// writes 2 + 3 CHEB_MAX_DEGREE doubles.
+void engine_cheb_table(int d, double h, double A, int n, double eps, double *tab);
+
 // Whether a launch of nsys systems of 'sites' sites each uses the overlapped
 // layout (see EngLaunch::homogeneous); HH_ENGINE_OVERLAP=0 or 1 forces it.
 bool engine_overlap(int nsys, long long sites, bool mixed);

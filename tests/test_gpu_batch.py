@@ -212,3 +212,63 @@ def test_autotuner_returns_a_candidate(hh, tmp_path):
     best = B.autotune(reqs, hbm_budget_bytes=1 << 29, rounds=3, cache_path=cache)
     assert best["tile_sites"] in (2048, 8192) and best["chunk_iters"] in (16, 64)
     assert '"tile_sites"' in open(cache).read()
+
+
+def test_batched_chebyshev_pcg_matches_context(hh):
+    """FP64 requests with the Chebyshev preconditioner (Sec. 4.2) in the batch:
+    true residual 1e-10 by the oracle, the context solver's PCG solution within
+    the solver tolerance, and the same bits alone and next to plain-CG and
+    mixed requests."""
+    from paper_1007_3432_gb300 import binding as B
+    cases = [(1, 32, 64, 21, 4, 1e-3), (3, 6, 8, 22, 3, 1e-2)]
+
+    def pcg_req(d, nx, nt, seed, deg, eps):
+        n = nx ** d * nt
+        sigma = workloads.sigma_field(n, seed=seed)
+        b = np.stack([workloads.source(n, seed=seed, rhs=a) for a in range(2)])
+        out = np.zeros((2, n))
+        req = B.make_request(B.HH_REQ_SOLVE, d, nx, nt, sigma=sigma, b=b, out=out, precision="fp64", n_pf=2,
+                             cheb_degree=deg, cheb_eps=eps)
+        return req, (sigma, b, out)
+
+    outs = []
+    for with_mix in (False, True):
+        batch = B.Batch(max_slots=8, hbm_budget_bytes=1 << 30, chunk_iters=16, tile_sites=1024)
+        keep = []
+        if with_mix:
+            for d, nx, nt, seed, prec in MIX[:3]:
+                req, k = _solve_req(B, d, nx, nt, seed, prec)
+                batch.submit(req, keep=k)
+        for c in cases:
+            req, k = pcg_req(*c)
+            keep.append(k)
+            batch.submit(req, keep=k)
+        res = batch.run_until_idle()
+        batch.close()
+        assert all(r["status"] == 0 for r in res), res
+        outs.append([k[2].copy() for k in keep])
+        if with_mix:
+            continue
+        for (d, nx, nt, seed, deg, eps), (sigma, b, out) in zip(cases, keep):
+            lat = oracle.lattice(d, nx, nt)
+            L = oracle.links(lat, workloads.A_HS, sigma)
+            for a in range(2):
+                res_a = b[a] - oracle.apply_MTM(lat, H, L, out[a])
+                assert np.linalg.norm(res_a) <= 1.0001e-10 * np.linalg.norm(b[a])
+            with hh.Context(d, nx, nt, cheb_degree=deg, cheb_eps=eps) as ctx:
+                ctx.set_field(torch.from_numpy(sigma).cuda())
+                x = torch.zeros(2, nx ** d * nt, dtype=torch.float64, device="cuda")
+                ctx.solve(torch.from_numpy(b).cuda(), x, 2)
+                assert np.linalg.norm(x.cpu().numpy() - out) <= 1e-4 * np.linalg.norm(out)
+    for xa, xb in zip(*outs):
+        assert np.array_equal(xa, xb)
+
+
+def test_batched_chebyshev_rejected_for_mixed_precision(hh):
+    from paper_1007_3432_gb300 import binding as B
+    batch = B.Batch(max_slots=2, hbm_budget_bytes=1 << 26)
+    n = 8 * 8
+    req = B.make_request(B.HH_REQ_SOLVE, 1, 8, 8, sigma=np.zeros(n), precision="mixed", n_pf=1, cheb_degree=2)
+    rc, _ = batch.submit(req, allow=(B.HH_EINVAL,))
+    batch.close()
+    assert rc == B.HH_EINVAL
