@@ -227,7 +227,7 @@ def config_of(args, wl):
     return {"workload": wl.name, "d": wl.d, "nx": wl.nx, "ntau": wl.ntau, "sites": wl.nsites,
             "t": workloads.T_HOP, "dtau": workloads.DTAU, "A": workloads.A_HS, "seed": wl.seed,
             "n_md": args.n_md, "dt": 1.0 / args.n_md, "n_pf": 2, "cg_tol": 1e-10,
-            "precision": args.precision, "step": "one HMC trajectory",
+            "precision": args.precision, "step": "one HMC trajectory", "integrator": args.integrator,
             "l2": "flushed between steps (512 MiB write, then 512 MiB read)", "parallelism": "replicas%d" % args.gpus}
 
 
@@ -520,6 +520,7 @@ def main():
     ap.add_argument("--mode", default="trajectory", choices=["trajectory", "solve", "apply", "batch", "serve"])
     ap.add_argument("--cg-maxit", type=int, default=1000000)
     ap.add_argument("--cheb", type=int, default=0, help="solve mode: Chebyshev preconditioner degree n (FP64)")
+    ap.add_argument("--integrator", default="leapfrog", choices=["leapfrog", "omelyan"])
     ap.add_argument("--cheb-eps", type=float, default=1e-4)
     ap.add_argument("--rates", default="10,100,1000")
     ap.add_argument("--requests", type=int, default=24)
@@ -553,7 +554,7 @@ def main():
     n = wl.nsites
     sigma_h = workloads.sigma_field(n, seed=wl.seed, chain=rank)
     ctx = Context(wl.d, wl.nx, wl.ntau, seed=wl.seed, n_pf=2, chain_id=rank, precision=args.precision,
-                  cg_maxit=args.cg_maxit, stream=stream)
+                  cg_maxit=args.cg_maxit, stream=stream, integrator=args.integrator)
     flush = L2Flush(dev)
     dt = 1.0 / args.n_md
 

@@ -24,7 +24,7 @@ class Lattice(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("dtau", ctypes.c_double), ("A", ctypes.c_double),
                 ("cg_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int), ("n_pf", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("chain", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("chain", ctypes.c_uint64), ("integrator", ctypes.c_int)]
 
 
 class TrajInfo(ctypes.Structure):
@@ -63,8 +63,9 @@ def lattice(d, nx, ntau):
     return Lattice(d, nx, ntau)
 
 
-def params(t=1.0, dtau=0.05, A=0.5, cg_tol=1e-10, cg_maxit=100000, n_pf=2, seed=1007, chain=0):
-    return Params(t, dtau, A, cg_tol, cg_maxit, n_pf, seed, chain)
+def params(t=1.0, dtau=0.05, A=0.5, cg_tol=1e-10, cg_maxit=100000, n_pf=2, seed=1007, chain=0, integrator=0):
+    """integrator: 0 leapfrog (Sec. 4.1), 1 Omelyan's second-order minimum-norm scheme."""
+    return Params(t, dtau, A, cg_tol, cg_maxit, n_pf, seed, chain, integrator)
 
 
 def nsites(lat):

@@ -557,19 +557,54 @@ void oracle_force(const oracle_lattice *lat, const oracle_params *p, const doubl
 /* Leapfrog integration of d sigma/dt = pi, d pi/dt = -F (reading R6):
  * half momentum step, n_md full sigma steps with full momentum steps between
  * them, half momentum step at the end; n_md + 1 force evaluations. */
+/* pi -= eps F(sigma) */
+static void kick(const oracle_lattice *lat, const oracle_params *p, const double *sigma,
+                 double *pi, const double *chi, double eps, double *F, int *iters,
+                 double *relres, int *status)
+{
+    long n = oracle_nsites(lat);
+    oracle_force(lat, p, sigma, chi, F, iters, relres, status);
+    for (long i = 0; i < n; ++i) pi[i] -= eps * F[i];
+}
+
+/* sigma += eps pi */
+static void drift(long n, double *sigma, const double *pi, double eps)
+{
+    for (long i = 0; i < n; ++i) sigma[i] += eps * pi[i];
+}
+
+/* The parameter of Omelyan's second-order minimum-norm scheme, the root
+ * 1/2 - c/12 + 1/(6c), c = (2 sqrt(326) + 36)^(1/3), of its error norm. */
+static double omelyan_lambda(void)
+{
+    double c = cbrt(2.0 * sqrt(326.0) + 36.0);
+    return 0.5 - c / 12.0 + 1.0 / (6.0 * c);
+}
+
 void oracle_leapfrog(const oracle_lattice *lat, const oracle_params *p, double *sigma,
                      double *pi, const double *chi, int n_md, double dt, int *iters,
                      double *relres, int *status)
 {
     long n = oracle_nsites(lat);
     double *F = (double *)malloc(sizeof(double) * (size_t)n);
-    oracle_force(lat, p, sigma, chi, F, iters, relres, status);
-    for (long i = 0; i < n; ++i) pi[i] -= 0.5 * dt * F[i];
-    for (int k = 1; k <= n_md; ++k) {
-        for (long i = 0; i < n; ++i) sigma[i] += dt * pi[i];
-        oracle_force(lat, p, sigma, chi, F, iters, relres, status);
-        double eps = (k == n_md) ? 0.5 * dt : dt;
-        for (long i = 0; i < n; ++i) pi[i] -= eps * F[i];
+    if (p->integrator == 1) {
+        /* Per step: kick lambda dt, drift dt/2, kick (1 - 2 lambda) dt, drift
+         * dt/2, kick lambda dt; the end kick of a step and the first of the
+         * next merge into one of 2 lambda dt. */
+        double lam = omelyan_lambda();
+        kick(lat, p, sigma, pi, chi, lam * dt, F, iters, relres, status);
+        for (int k = 1; k <= n_md; ++k) {
+            drift(n, sigma, pi, 0.5 * dt);
+            kick(lat, p, sigma, pi, chi, (1.0 - 2.0 * lam) * dt, F, iters, relres, status);
+            drift(n, sigma, pi, 0.5 * dt);
+            kick(lat, p, sigma, pi, chi, (k == n_md ? lam : 2.0 * lam) * dt, F, iters, relres, status);
+        }
+    } else {
+        kick(lat, p, sigma, pi, chi, 0.5 * dt, F, iters, relres, status);
+        for (int k = 1; k <= n_md; ++k) {
+            drift(n, sigma, pi, dt);
+            kick(lat, p, sigma, pi, chi, (k == n_md) ? 0.5 * dt : dt, F, iters, relres, status);
+        }
     }
     free(F);
 }
@@ -605,7 +640,7 @@ int oracle_trajectory(const oracle_lattice *lat, const oracle_params *p, double 
     info->u = u;
     info->accepted = accepted;
     info->cg_iterations = iters;
-    info->n_solves = p->n_pf * (n_md + 3);
+    info->n_solves = p->n_pf * ((p->integrator == 1 ? 2 * n_md + 1 : n_md + 1) + 2);
     info->max_relres = relres;
     info->status = status;
     free(pi);

@@ -40,6 +40,9 @@ typedef struct {
     int n_pf;         /* real pseudofermion components (2 = one complex field) */
     uint64_t seed;    /* Philox key */
     uint64_t chain;   /* Philox counter word 3 */
+    int integrator;   /* 0: leapfrog (Sec. 4.1); 1: Omelyan's second-order
+                         minimum-norm scheme (Omelyan, Mryglod, Folk, Comput.
+                         Phys. Commun. 151 (2003) 272) */
 } oracle_params;
 
 typedef struct {
@@ -98,6 +101,8 @@ double oracle_action(const oracle_lattice *lat, const oracle_params *p,
                      int *status);
 void oracle_force(const oracle_lattice *lat, const oracle_params *p, const double *sigma,
                   const double *chi, double *F, int *iters, double *relres, int *status);
+/* n_md molecular-dynamics steps of size dt with the integrator of p:
+ * leapfrog (n_md + 1 forces) or Omelyan (2 n_md + 1 forces). */
 void oracle_leapfrog(const oracle_lattice *lat, const oracle_params *p, double *sigma,
                      double *pi, const double *chi, int n_md, double dt, int *iters,
                      double *relres, int *status);

@@ -36,7 +36,7 @@ class hh_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("cg_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
                 ("reliable_delta", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("n_pf", ctypes.c_int), ("chain_id", ctypes.c_uint64),
-                ("cheb_degree", ctypes.c_int), ("cheb_eps", ctypes.c_double)]
+                ("cheb_degree", ctypes.c_int), ("cheb_eps", ctypes.c_double), ("integrator", ctypes.c_int)]
 
 
 class hh_solve_info(ctypes.Structure):
@@ -94,6 +94,8 @@ class hh_batch_config(ctypes.Structure):
 
 
 HH_REQ_SOLVE, HH_REQ_TRAJECTORY = 0, 1
+HH_LEAPFROG, HH_OMELYAN = 0, 1
+INTEGRATORS = {"leapfrog": HH_LEAPFROG, "omelyan": HH_OMELYAN}
 
 _lib = None
 
@@ -188,7 +190,7 @@ class Context:
 
     def __init__(self, d, nx, ntau, t=1.0, dtau=0.05, A=0.5, precision=HH_FP64, cg_tol=1e-10,
                  cg_maxit=1000000, reliable_delta=0.1, seed=0, n_pf=2, chain_id=0, stream=None,
-                 cheb_degree=0, cheb_eps=1e-3):
+                 cheb_degree=0, cheb_eps=1e-3, integrator="leapfrog"):
         L = load()
         self._lib = L
         self.lat = hh_lattice(d, nx, ntau)
@@ -199,6 +201,7 @@ class Context:
         p.cg_tol, p.cg_maxit, p.reliable_delta = cg_tol, cg_maxit, reliable_delta
         p.seed, p.n_pf, p.chain_id = seed, n_pf, chain_id
         p.cheb_degree, p.cheb_eps = cheb_degree, cheb_eps
+        p.integrator = INTEGRATORS.get(integrator, integrator)
         self.params = p
         self.stream = stream
         h = ctypes.c_void_p()
@@ -304,7 +307,8 @@ def solve_noalloc(d, nx, ntau, sigma, b, x, t=1.0, dtau=0.05, A=0.5, cg_tol=1e-1
 
 
 def make_params(t=1.0, dtau=0.05, A=0.5, precision=HH_FP64, cg_tol=1e-10, cg_maxit=1000000,
-                reliable_delta=0.1, seed=0, n_pf=2, chain_id=0, cheb_degree=0, cheb_eps=1e-3):
+                reliable_delta=0.1, seed=0, n_pf=2, chain_id=0, cheb_degree=0, cheb_eps=1e-3,
+                integrator="leapfrog"):
     L = load()
     p = hh_params()
     L.hh_default_params(ctypes.byref(p))
@@ -313,6 +317,7 @@ def make_params(t=1.0, dtau=0.05, A=0.5, precision=HH_FP64, cg_tol=1e-10, cg_max
     p.cg_tol, p.cg_maxit, p.reliable_delta = cg_tol, cg_maxit, reliable_delta
     p.seed, p.n_pf, p.chain_id = seed, n_pf, chain_id
     p.cheb_degree, p.cheb_eps = cheb_degree, cheb_eps
+    p.integrator = INTEGRATORS.get(integrator, integrator)
     return p
 
 

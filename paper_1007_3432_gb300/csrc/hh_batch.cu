@@ -271,6 +271,7 @@ int validate(const hh_request &r)
     if (r.prm.precision != HH_FP64 && r.prm.precision != HH_MIXED) return HH_EINVAL;
     if (!(r.prm.cg_tol > 0.0) || r.prm.cg_maxit < 1) return HH_EINVAL;
     if (r.kind == HH_REQ_TRAJECTORY && r.n_md < 1) return HH_EINVAL;
+    if (r.prm.integrator != HH_LEAPFROG && r.prm.integrator != HH_OMELYAN) return HH_EINVAL;
     // Chebyshev-preconditioned CG (Sec. 4.2) is FP64 only, as in the context solver.
     if (r.prm.cheb_degree < 0 || r.prm.cheb_degree > CHEB_MAX_DEGREE) return HH_EINVAL;
     if (r.prm.cheb_degree > 0 && (r.prm.precision != HH_FP64 || !(r.prm.cheb_eps > 0.0 && r.prm.cheb_eps < 1.0)))
@@ -587,15 +588,17 @@ int advance(hh_batch *b, int s)
         push_result(b, res);
         return HH_OK;
     }
-    // Trajectory: leapfrog of Sec. 4.1 around solve number md_step.
+    // Trajectory: the molecular dynamics (leapfrog of Sec. 4.1 or Omelyan) around
+    // force number md_step, computed from the solve just finished.
     const double h = r.prm.t * r.prm.dtau, A = r.prm.A, dt = r.dt;
     const int k = S.md_step;
+    double kick = 0.0, drift = 0.0;
+    const int forces = md_schedule(r.prm.integrator, r.n_md, dt, k, &kick, &drift);
     if (k == 0)
         HB_TRY(launch_energy(S.N, S.m.pi, S.m.chi, S.m.x, S.nrhs, S.m.epart, &S.m.sc->H0, st));
-    double eps = (k == 0 || k == r.n_md) ? 0.5 * dt : dt;
-    HB_TRY(launch_force(S.geo, h, A, S.m.sigma, S.m.L64, S.m.x, S.nrhs, S.m.pi, eps, nullptr, st));
-    if (k < r.n_md) {
-        HB_TRY(launch_sigma_step(S.geo, A, dt, S.m.sigma, S.m.pi, S.m.L64, S.m.L32, st));
+    HB_TRY(launch_force(S.geo, h, A, S.m.sigma, S.m.L64, S.m.x, S.nrhs, S.m.pi, kick, nullptr, st));
+    if (k + 1 < forces) {
+        HB_TRY(launch_sigma_step(S.geo, A, drift, S.m.sigma, S.m.pi, S.m.L64, S.m.L32, st));
         S.md_step = k + 1;
         return start_solve(b, s);
     }

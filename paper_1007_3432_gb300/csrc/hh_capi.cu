@@ -357,6 +357,7 @@ void hh_default_params(hh_params *p)
     p->chain_id = 0;
     p->cheb_degree = 0;
     p->cheb_eps = 1e-3;
+    p->integrator = HH_LEAPFROG;
 }
 
 const char *hh_strerror(int code)
@@ -386,6 +387,7 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
     if (p->cheb_degree < 0 || p->cheb_degree > CHEB_MAX_DEGREE) return HH_EINVAL;
     if (p->cheb_degree > 0 && (p->precision != HH_FP64 || !(p->cheb_eps > 0.0 && p->cheb_eps < 1.0)))
         return HH_EINVAL;
+    if (p->integrator != HH_LEAPFROG && p->integrator != HH_OMELYAN) return HH_EINVAL;
     long long V = lat->d == 1 ? lat->nx : (long long)lat->nx * lat->nx * lat->nx;
     long long N = V * lat->ntau;
     if (N >= (1LL << 31) - 1024) return HH_EINVAL;
@@ -668,21 +670,20 @@ int leapfrog_enqueue(hh_ctx *c, double *pi, const double *chi, int n_rhs, int n_
     const double h = c->prm.t * c->prm.dtau, A = c->prm.A;
     int rc = make_plan(c, chi, c->xsol, n_rhs);
     if (rc) return rc;
-    rc = run_engine(c);
-    if (rc) return rc;
-    if (h0) HH_TRY(launch_energy(c->N, pi, chi, c->xsol, n_rhs, c->d_energy_part, h0, c->stream));
-    HH_TRY(launch_force(c->geo, h, A, c->sigma, c->L64, c->xsol, n_rhs, pi, 0.5 * dt, nullptr,
-                        c->stream));
-    for (int k = 1; k <= n_md; ++k) {
-        HH_TRY(launch_sigma_step(c->geo, A, dt, c->sigma, pi, c->L64, c->L32, c->stream));
+    double kick = 0.0, drift = 0.0;
+    const int forces = md_schedule(c->prm.integrator, n_md, dt, 0, &kick, &drift);
+    for (int j = 0; j < forces; ++j) {
+        md_schedule(c->prm.integrator, n_md, dt, j, &kick, &drift);
         rc = run_engine(c);
         if (rc) return rc;
-        double eps = (k == n_md) ? 0.5 * dt : dt;
-        HH_TRY(launch_force(c->geo, h, A, c->sigma, c->L64, c->xsol, n_rhs, pi, eps, nullptr,
-                            c->stream));
+        if (j == 0 && h0)
+            HH_TRY(launch_energy(c->N, pi, chi, c->xsol, n_rhs, c->d_energy_part, h0, c->stream));
+        HH_TRY(launch_force(c->geo, h, A, c->sigma, c->L64, c->xsol, n_rhs, pi, kick, nullptr, c->stream));
+        if (j + 1 < forces)
+            HH_TRY(launch_sigma_step(c->geo, A, drift, c->sigma, pi, c->L64, c->L32, c->stream));
     }
     if (h1) HH_TRY(launch_energy(c->N, pi, chi, c->xsol, n_rhs, c->d_energy_part, h1, c->stream));
-    c->n_launch += (h0 ? 2 : 0) + (h1 ? 2 : 0) + (n_md + 1) + n_md;
+    c->n_launch += (h0 ? 2 : 0) + (h1 ? 2 : 0) + forces + (forces - 1);
     return HH_OK;
 }
 

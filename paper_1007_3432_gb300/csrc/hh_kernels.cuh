@@ -3,6 +3,8 @@
 // return the launch's cudaError_t.
 #pragma once
 
+#include <cmath>
+
 #include "hh_device.cuh"
 
 namespace hh {
@@ -57,5 +59,33 @@ cudaError_t launch_metropolis(HmcScalars *sc, uint64_t seed, uint64_t traj, uint
 // If !sc->accepted: sigma = sigma0 and the links are recomputed.
 cudaError_t launch_restore(const Geo &g, double A, const HmcScalars *sc, double *sigma,
                            const double *sigma0, double *L64, float *L32, cudaStream_t st);
+
+// Molecular-dynamics schedule of one trajectory as a sequence of forces:
+// after force j (j = 0 .. forces - 1, each computed from a fresh solve at the
+// current sigma) the momenta take a kick pi -= kick F, then, except after the
+// last force, sigma drifts by drift * pi.  Leapfrog (Sec. 4.1): kicks dt/2,
+// dt, ..., dt, dt/2 and drifts dt (n_md + 1 forces).  Omelyan's second-order
+// minimum-norm scheme (Comput. Phys. Commun. 151 (2003) 272): kicks lambda dt,
+// (1 - 2 lambda) dt, 2 lambda dt, ..., (1 - 2 lambda) dt, lambda dt and drifts
+// dt/2 (2 n_md + 1 forces), lambda = 1/2 - c/12 + 1/(6c), c = (2 sqrt(326) +
+// 36)^(1/3).  Returns the number of forces.
+inline int md_schedule(int integrator, int n_md, double dt, int j, double *kick, double *drift)
+{
+    if (integrator == 1) {
+        const double c = cbrt(2.0 * sqrt(326.0) + 36.0);
+        const double lam = 0.5 - c / 12.0 + 1.0 / (6.0 * c);
+        const int forces = 2 * n_md + 1;
+        if (j == 0 || j == forces - 1)
+            *kick = lam * dt;
+        else
+            *kick = (j % 2 == 1) ? (1.0 - 2.0 * lam) * dt : 2.0 * lam * dt;
+        *drift = 0.5 * dt;
+        return forces;
+    }
+    const int forces = n_md + 1;
+    *kick = (j == 0 || j == forces - 1) ? 0.5 * dt : dt;
+    *drift = dt;
+    return forces;
+}
 
 }  // namespace hh

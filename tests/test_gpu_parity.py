@@ -412,3 +412,74 @@ def test_chebyshev_pcg_iteration_cap_reports_no_convergence(hh):
         rc, info = ctx.solve(dev(workloads.source(n, seed=32))[None, :], x, 1,
                              allow=(hh.binding.HH_ENOCONV,))
     assert rc == hh.binding.HH_ENOCONV and info["converged"] == 0 and info["iterations"] == 7
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_omelyan_trajectories_match_oracle(hh, precision):
+    """The second-order minimum-norm integrator (2 n_md + 1 forces): energies,
+    accept decisions and fields of the oracle's trajectories."""
+    wl = workloads.C0
+    lat = oracle.lattice(wl.d, wl.nx, wl.ntau)
+    n = wl.nsites
+    sigma = workloads.sigma_field(n, seed=wl.seed)
+    prm = oracle.params(seed=wl.seed, n_pf=2, integrator=1)
+    n_md, dt = 3, 0.1
+    s_ref = sigma.copy()
+    with hh.Context(wl.d, wl.nx, wl.ntau, seed=wl.seed, n_pf=2, precision=precision,
+                    integrator="omelyan") as ctx:
+        ctx.set_field(dev(sigma))
+        for traj in range(3):
+            info = ctx.trajectory(n_md, dt, traj)
+            s_ref, oinfo = oracle.trajectory(lat, prm, s_ref, n_md, dt, traj)
+            assert info["n_solves"] == 2 * (2 * n_md + 1)
+            assert info["max_true_relres"] <= 1e-10
+            assert info["u"] == oinfo["u"]
+            assert abs(info["H0"] - oinfo["H0"]) <= 1e-8 * abs(oinfo["H0"])
+            assert abs(info["dH"] - oinfo["dH"]) <= 1e-6, (info, oinfo)
+            if abs(oinfo["dH"] + np.log(oinfo["u"])) > 1e-5:
+                assert info["accepted"] == oinfo["accepted"]
+            if info["accepted"] != oinfo["accepted"]:
+                break
+            got = torch.empty(n, dtype=torch.float64, device="cuda")
+            ctx.get_field(got)
+            assert np.max(np.abs(got.cpu().numpy() - s_ref)) <= 1e-6
+
+
+def test_omelyan_reversible_on_gpu(hh):
+    d, nx, ntau = 1, 16, 24
+    n = nx * ntau
+    sigma = workloads.sigma_field(n, seed=91)
+    pi = workloads.unit_normal(n, seed=92, stream=1)
+    chi = np.stack([workloads.unit_normal(n, seed=93, stream=2 + a) for a in range(2)])
+    with hh.Context(d, nx, ntau, integrator="omelyan", cg_tol=1e-12) as ctx:
+        ctx.set_field(dev(sigma))
+        p = dev(pi)
+        ctx.leapfrog(p, dev(chi), 2, 6, 0.08)
+        mid = torch.empty(n, dtype=torch.float64, device="cuda")
+        ctx.get_field(mid)
+        p.neg_()
+        ctx.leapfrog(p, dev(chi), 2, 6, 0.08)
+        back = torch.empty(n, dtype=torch.float64, device="cuda")
+        ctx.get_field(back)
+    assert np.max(np.abs(mid.cpu().numpy() - sigma)) > 1e-3
+    assert np.max(np.abs(back.cpu().numpy() - sigma)) <= 1e-8
+    assert np.max(np.abs(p.cpu().numpy() + pi)) <= 1e-8
+
+
+def test_batched_omelyan_trajectory_matches_context(hh):
+    from paper_1007_3432_gb300 import binding as B
+    d, nx, nt, seed = 1, 16, 16, 95
+    n = nx * nt
+    sigma = workloads.sigma_field(n, seed=seed)
+    out = np.zeros(n)
+    batch = B.Batch(max_slots=2, hbm_budget_bytes=1 << 28, chunk_iters=32, tile_sites=1024)
+    req = B.make_request(B.HH_REQ_TRAJECTORY, d, nx, nt, sigma=sigma, out=out, n_md=3, dt=0.1, traj_index=4,
+                         precision="fp64", seed=seed, n_pf=2, integrator="omelyan")
+    batch.submit(req, keep=(sigma, out))
+    r = batch.run_until_idle()[0]
+    batch.close()
+    assert r["status"] == 0 and r["n_solves"] == 2 * 7
+    with hh.Context(d, nx, nt, seed=seed, n_pf=2, integrator="omelyan") as ctx:
+        ctx.set_field(dev(sigma))
+        info = ctx.trajectory(3, 0.1, 4)
+    assert abs(info["dH"] - r["dH"]) <= 1e-6 and info["u"] == r["u"]

@@ -341,6 +341,57 @@ def test_energy_violation_scales_as_dt_squared(orc):
 
 
 @pytest.mark.slow
+# --- Omelyan's second-order minimum-norm integrator ---------------------------
+
+
+def _omelyan_prm(orc, prm):
+    return orc.params(t=prm.t, dtau=prm.dtau, A=prm.A, cg_tol=prm.cg_tol, cg_maxit=prm.cg_maxit,
+                      n_pf=prm.n_pf, seed=prm.seed, chain=prm.chain, integrator=1)
+
+
+def test_omelyan_reversible_and_symplectic_order(orc):
+    """Reversible (momentum flip), and the energy violation falls as dt^2 with
+    a coefficient several times below leapfrog's at equal step size (the
+    scheme's minimum-norm property)."""
+    lat, prm, sigma, pi, chi = _md_setup(orc)
+    om = _omelyan_prm(orc, prm)
+    s1, p1, *_ = orc.leapfrog(lat, om, sigma, pi, chi, 10, 0.05)
+    s2, p2, *_ = orc.leapfrog(lat, om, s1, -p1, chi, 10, 0.05)
+    assert np.max(np.abs(s2 - sigma)) < 1e-9 and np.max(np.abs(p2 + pi)) < 1e-9
+    assert np.max(np.abs(s1 - sigma)) > 1e-2
+
+    lat, prm, sigma, pi, chi = _md_setup(orc, nx=4, ntau=6, seed=3)
+    om = _omelyan_prm(orc, prm)
+    pi = 0.5 * pi
+    H0 = _hamiltonian(orc, lat, prm, sigma, pi, chi)
+    steps = np.array([8, 16, 32])
+    dH_om, dH_lf = [], []
+    for n_md in steps:
+        s1, p1, *_ = orc.leapfrog(lat, om, sigma, pi, chi, int(n_md), 0.25 / n_md)
+        dH_om.append(abs(_hamiltonian(orc, lat, prm, s1, p1, chi) - H0))
+        s1, p1, *_ = orc.leapfrog(lat, prm, sigma, pi, chi, int(n_md), 0.25 / n_md)
+        dH_lf.append(abs(_hamiltonian(orc, lat, prm, s1, p1, chi) - H0))
+    slope = np.polyfit(np.log(0.25 / steps), np.log(dH_om), 1)[0]
+    assert 1.8 < slope < 2.2, (dH_om, slope)
+    assert all(o < 0.1 * l for o, l in zip(dH_om, dH_lf)), (dH_om, dH_lf)   # 0.046 measured
+
+
+def test_omelyan_step_sequence(orc):
+    """One Omelyan step on a quadratic action S = 0 (A = 0: the force
+    vanishes) is a free drift sigma += dt pi, and its 2 n_md + 1 forces are
+    counted in the trajectory's solves."""
+    lat = orc.lattice(1, 4, 4)
+    n = orc.nsites(lat)
+    prm = orc.params(A=0.0, integrator=1)
+    rng = np.random.default_rng(5)
+    sigma, pi = rng.uniform(-1, 1, n), rng.standard_normal(n)
+    chi = rng.standard_normal((2, n))
+    s1, p1, *_ = orc.leapfrog(lat, prm, sigma, pi, chi, 3, 0.1)
+    assert np.allclose(s1, sigma + 0.3 * pi, atol=1e-14) and np.allclose(p1, pi, atol=0)
+    _, info = orc.trajectory(lat, prm, sigma, 3, 0.1, 0)
+    assert info["n_solves"] == 2 * (2 * 3 + 1 + 2)
+
+
 def test_creutz_equality_mean_exp_minus_dH_is_one(orc):
     """<exp(-dH)> = 1 for an area-preserving, reversible integrator (Sec. 4.1:
     the Metropolis step makes HMC exact)."""
