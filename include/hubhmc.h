@@ -101,6 +101,11 @@ typedef struct {
                               scheme of Omelyan, Mryglod and Folk, Comput. Phys.
                               Commun. 151 (2003) 272; 2 n_md + 1 forces, energy
                               violation about 20x smaller at equal dt) */
+    int chrono;            /* initial guess of a trajectory's solves after the
+                              first: 0 zero (MD exactly reversible); 1 the
+                              previous force's solution; 2 the linear
+                              extrapolation of the last two.  1 and 2 make the
+                              MD reversible only to the CG tolerance. */
 } hh_params;
 
 #define HH_LEAPFROG 0
@@ -125,7 +130,7 @@ typedef struct {
 
 /* Fill p with the defaults t = 1, dtau = 0.05, A = 0.5, FP64, cg_tol = 1e-10,
  * cg_maxit = 1000000, reliable_delta = 0.1, seed = 0, n_pf = 2, chain_id = 0,
- * cheb_degree = 0 (plain CG), cheb_eps = 1e-3, integrator = HH_LEAPFROG. */
+ * cheb_degree = 0 (plain CG), cheb_eps = 1e-3, integrator = HH_LEAPFROG, chrono = 0. */
 void hh_default_params(hh_params *p);
 
 /* Create a context for one lattice and one Markov chain.  Allocates sigma,
@@ -173,6 +178,14 @@ int hh_apply(hh_ctx *ctx, int op, const void *x, void *y, int dtype);
  * cg_tol within cg_maxit (x then holds the last iterate), HH_ETIMEOUT if a
  * device-side barrier wait ran out, HH_ENUMERIC on NaN/Inf. */
 int hh_solve(hh_ctx *ctx, const double *b, double *x, int n_rhs, hh_solve_info *info);
+
+/* As hh_solve, from the initial guess x0 held in x on entry: the engine first
+ * computes the true residual b - Q x0 in FP64 (counted as a reliable update;
+ * info->iterations is 0 if it already meets cg_tol), then runs CG from it.
+ * b = 0 gives x = 0.  Used for chronological guesses in the molecular
+ * dynamics (hh_params.chrono); not part of the paper's method, which starts
+ * every solve from zero. */
+int hh_solve_guess(hh_ctx *ctx, const double *b, double *x, int n_rhs, hh_solve_info *info);
 
 /* F = dS_pf/dsigma for S_pf = 1/2 sum_a chi_a^T Q^{-1} chi_a: solves for
  * x_a = Q^{-1} chi_a, then F(n,tau) = -sum_a (M x_a)(n,tau+1) s(tau)

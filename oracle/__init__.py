@@ -24,7 +24,8 @@ class Lattice(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("dtau", ctypes.c_double), ("A", ctypes.c_double),
                 ("cg_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int), ("n_pf", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("chain", ctypes.c_uint64), ("integrator", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("chain", ctypes.c_uint64), ("integrator", ctypes.c_int),
+                ("chrono", ctypes.c_int)]
 
 
 class TrajInfo(ctypes.Structure):
@@ -63,9 +64,11 @@ def lattice(d, nx, ntau):
     return Lattice(d, nx, ntau)
 
 
-def params(t=1.0, dtau=0.05, A=0.5, cg_tol=1e-10, cg_maxit=100000, n_pf=2, seed=1007, chain=0, integrator=0):
-    """integrator: 0 leapfrog (Sec. 4.1), 1 Omelyan's second-order minimum-norm scheme."""
-    return Params(t, dtau, A, cg_tol, cg_maxit, n_pf, seed, chain, integrator)
+def params(t=1.0, dtau=0.05, A=0.5, cg_tol=1e-10, cg_maxit=100000, n_pf=2, seed=1007, chain=0, integrator=0,
+           chrono=0):
+    """integrator: 0 leapfrog (Sec. 4.1), 1 Omelyan's second-order minimum-norm scheme.
+    chrono: initial guess of the MD solves (0 zero, 1 last solution, 2 linear extrapolation)."""
+    return Params(t, dtau, A, cg_tol, cg_maxit, n_pf, seed, chain, integrator, chrono)
 
 
 def nsites(lat):
@@ -109,6 +112,18 @@ def cg(lat, h, L, b, tol=1e-10, maxit=100000):
     st = lib().oracle_cg(ctypes.byref(lat), ctypes.c_double(h), _ptr(L), _ptr(b), _ptr(x),
                          ctypes.c_double(tol), ctypes.c_int(maxit), ctypes.byref(it),
                          ctypes.byref(rr))
+    return x, st, it.value, rr.value
+
+
+def cg_guess(lat, h, L, b, x0, tol=1e-10, maxit=100000):
+    """CG from the initial guess x0; returns (x, status, iterations, true_relres)."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    x = np.array(x0, dtype=np.float64, copy=True)
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = lib().oracle_cg_guess(ctypes.byref(lat), ctypes.c_double(h), _ptr(L), _ptr(b), _ptr(x),
+                               ctypes.c_double(tol), ctypes.c_int(maxit), ctypes.byref(it), ctypes.byref(rr))
     return x, st, it.value, rr.value
 
 

@@ -163,8 +163,11 @@ static double dot(long n, const double *a, const double *b)
     return s;
 }
 
-int oracle_cg(const oracle_lattice *lat, double h, const double *L, const double *b,
-              double *x, double tol, int maxit, int *iterations, double *true_relres)
+/* CG for Q x = b from x0 = 0, or from the x passed in when guess != 0
+ * (r0 = b - Q x0, stopping at once if that already meets tol; b = 0 gives
+ * x = 0 either way). */
+static int cg_from(const oracle_lattice *lat, double h, const double *L, const double *b,
+                   double *x, int guess, double tol, int maxit, int *iterations, double *true_relres)
 {
     long n = oracle_nsites(lat);
     double *r = (double *)malloc(sizeof(double) * (size_t)n);
@@ -173,18 +176,27 @@ int oracle_cg(const oracle_lattice *lat, double h, const double *L, const double
     int status = -4, k = 0;
     double bnorm = sqrt(dot(n, b, b));
 
-    for (long i = 0; i < n; ++i) {
-        x[i] = 0.0;
-        r[i] = b[i];
-        p[i] = b[i];
+    if (!guess || bnorm == 0.0) {
+        for (long i = 0; i < n; ++i) {
+            x[i] = 0.0;
+            r[i] = b[i];
+        }
+    } else {
+        oracle_apply_MTM(lat, h, L, x, q);
+        for (long i = 0; i < n; ++i) r[i] = b[i] - q[i];
     }
+    for (long i = 0; i < n; ++i) p[i] = r[i];
     *true_relres = 0.0;
     if (bnorm == 0.0) {
         status = 0;
         goto done;
     }
     double rr = dot(n, r, r);
-    *true_relres = 1.0;
+    *true_relres = sqrt(rr) / bnorm;
+    if (guess && sqrt(rr) <= tol * bnorm) {
+        status = 0;
+        goto done;
+    }
     for (k = 1; k <= maxit; ++k) {
         oracle_apply_MTM(lat, h, L, p, q);
         double alpha = rr / dot(n, p, q);
@@ -220,6 +232,18 @@ done:
     free(p);
     free(q);
     return status;
+}
+
+int oracle_cg(const oracle_lattice *lat, double h, const double *L, const double *b,
+              double *x, double tol, int maxit, int *iterations, double *true_relres)
+{
+    return cg_from(lat, h, L, b, x, 0, tol, maxit, iterations, true_relres);
+}
+
+int oracle_cg_guess(const oracle_lattice *lat, double h, const double *L, const double *b,
+                    double *x, double tol, int maxit, int *iterations, double *true_relres)
+{
+    return cg_from(lat, h, L, b, x, 1, tol, maxit, iterations, true_relres);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -523,13 +547,15 @@ double oracle_action(const oracle_lattice *lat, const oracle_params *p,
  * dS/dsigma = -sum_a y_a^T (dM/dsigma) x_a, and sigma(n,tau) enters M only
  * through the link L(n,tau) at row (n,tau+1), column (n,tau), whose derivative
  * is s(tau) A cos sigma(n,tau) with s = -1, or +1 on the wrap link. */
-void oracle_force(const oracle_lattice *lat, const oracle_params *p, const double *sigma,
-                  const double *chi, double *F, int *iters, double *relres, int *status)
+/* The force with the solutions x_a kept in xs (n_pf * N); guess != 0 starts
+ * each solve from the xs passed in. */
+static void force_from(const oracle_lattice *lat, const oracle_params *p, const double *sigma,
+                       const double *chi, double *F, double *xs, int guess, int *iters,
+                       double *relres, int *status)
 {
     long n = oracle_nsites(lat);
     double h = p->t * p->dtau;
     double *L = (double *)malloc(sizeof(double) * (size_t)n);
-    double *x = (double *)malloc(sizeof(double) * (size_t)n);
     double *y = (double *)malloc(sizeof(double) * (size_t)n);
     int c[3], tau;
     oracle_links(lat, p->A, sigma, L);
@@ -537,7 +563,9 @@ void oracle_force(const oracle_lattice *lat, const oracle_params *p, const doubl
     for (int a = 0; a < p->n_pf; ++a) {
         int it;
         double rr;
-        int st = oracle_cg(lat, h, L, chi + (long)a * n, x, p->cg_tol, p->cg_maxit, &it, &rr);
+        double *x = xs + (long)a * n;
+        int st = guess ? oracle_cg_guess(lat, h, L, chi + (long)a * n, x, p->cg_tol, p->cg_maxit, &it, &rr)
+                       : oracle_cg(lat, h, L, chi + (long)a * n, x, p->cg_tol, p->cg_maxit, &it, &rr);
         if (st != 0) *status = st;
         *iters += it;
         if (rr > *relres) *relres = rr;
@@ -550,20 +578,46 @@ void oracle_force(const oracle_lattice *lat, const oracle_params *p, const doubl
         }
     }
     free(L);
-    free(x);
     free(y);
+}
+
+void oracle_force(const oracle_lattice *lat, const oracle_params *p, const double *sigma,
+                  const double *chi, double *F, int *iters, double *relres, int *status)
+{
+    double *xs = (double *)malloc(sizeof(double) * (size_t)oracle_nsites(lat) * (size_t)p->n_pf);
+    force_from(lat, p, sigma, chi, F, xs, 0, iters, relres, status);
+    free(xs);
 }
 
 /* Leapfrog integration of d sigma/dt = pi, d pi/dt = -F (reading R6):
  * half momentum step, n_md full sigma steps with full momentum steps between
  * them, half momentum step at the end; n_md + 1 force evaluations. */
-/* pi -= eps F(sigma) */
+/* Solutions of the molecular dynamics' solves, for chronological initial
+ * guesses: xs the latest, xp the one before; j counts the solves so far. */
+typedef struct {
+    double *xs, *xp;
+    int j;
+} md_solutions;
+
+/* pi -= eps F(sigma).  Initial guess of its solves (p->chrono): 0 none;
+ * 1 the previous force's solutions; 2 their linear extrapolation
+ * 2 x_{j-1} - x_{j-2} (1 at the second force). */
 static void kick(const oracle_lattice *lat, const oracle_params *p, const double *sigma,
-                 double *pi, const double *chi, double eps, double *F, int *iters,
-                 double *relres, int *status)
+                 double *pi, const double *chi, double eps, double *F, md_solutions *ms,
+                 int *iters, double *relres, int *status)
 {
-    long n = oracle_nsites(lat);
-    oracle_force(lat, p, sigma, chi, F, iters, relres, status);
+    long n = oracle_nsites(lat), m = n * (long)p->n_pf;
+    int guess = p->chrono != 0 && ms->j >= 1;
+    if (p->chrono == 2 && ms->j >= 2)
+        for (long i = 0; i < m; ++i) {
+            double t = ms->xs[i];
+            ms->xs[i] = 2.0 * t - ms->xp[i];
+            ms->xp[i] = t;
+        }
+    else
+        for (long i = 0; i < m; ++i) ms->xp[i] = ms->xs[i];
+    force_from(lat, p, sigma, chi, F, ms->xs, guess, iters, relres, status);
+    ms->j += 1;
     for (long i = 0; i < n; ++i) pi[i] -= eps * F[i];
 }
 
@@ -587,26 +641,32 @@ void oracle_leapfrog(const oracle_lattice *lat, const oracle_params *p, double *
 {
     long n = oracle_nsites(lat);
     double *F = (double *)malloc(sizeof(double) * (size_t)n);
+    md_solutions ms;
+    ms.xs = (double *)calloc((size_t)n * (size_t)p->n_pf, sizeof(double));
+    ms.xp = (double *)calloc((size_t)n * (size_t)p->n_pf, sizeof(double));
+    ms.j = 0;
     if (p->integrator == 1) {
         /* Per step: kick lambda dt, drift dt/2, kick (1 - 2 lambda) dt, drift
          * dt/2, kick lambda dt; the end kick of a step and the first of the
          * next merge into one of 2 lambda dt. */
         double lam = omelyan_lambda();
-        kick(lat, p, sigma, pi, chi, lam * dt, F, iters, relres, status);
+        kick(lat, p, sigma, pi, chi, lam * dt, F, &ms, iters, relres, status);
         for (int k = 1; k <= n_md; ++k) {
             drift(n, sigma, pi, 0.5 * dt);
-            kick(lat, p, sigma, pi, chi, (1.0 - 2.0 * lam) * dt, F, iters, relres, status);
+            kick(lat, p, sigma, pi, chi, (1.0 - 2.0 * lam) * dt, F, &ms, iters, relres, status);
             drift(n, sigma, pi, 0.5 * dt);
-            kick(lat, p, sigma, pi, chi, (k == n_md ? lam : 2.0 * lam) * dt, F, iters, relres, status);
+            kick(lat, p, sigma, pi, chi, (k == n_md ? lam : 2.0 * lam) * dt, F, &ms, iters, relres, status);
         }
     } else {
-        kick(lat, p, sigma, pi, chi, 0.5 * dt, F, iters, relres, status);
+        kick(lat, p, sigma, pi, chi, 0.5 * dt, F, &ms, iters, relres, status);
         for (int k = 1; k <= n_md; ++k) {
             drift(n, sigma, pi, dt);
-            kick(lat, p, sigma, pi, chi, (k == n_md) ? 0.5 * dt : dt, F, iters, relres, status);
+            kick(lat, p, sigma, pi, chi, (k == n_md) ? 0.5 * dt : dt, F, &ms, iters, relres, status);
         }
     }
     free(F);
+    free(ms.xs);
+    free(ms.xp);
 }
 
 /* One HMC trajectory (Sec. 4.1): momenta and pseudofermion heatbath,

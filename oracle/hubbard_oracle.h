@@ -43,6 +43,10 @@ typedef struct {
     int integrator;   /* 0: leapfrog (Sec. 4.1); 1: Omelyan's second-order
                          minimum-norm scheme (Omelyan, Mryglod, Folk, Comput.
                          Phys. Commun. 151 (2003) 272) */
+    int chrono;       /* initial guess of the MD's solves: 0 zero (reversible);
+                         1 the previous force's solution; 2 linear extrapolation
+                         of the last two.  Not part of the paper's method: it
+                         makes the MD reversible only to the CG tolerance. */
 } oracle_params;
 
 typedef struct {
@@ -71,6 +75,10 @@ void oracle_apply_MTM(const oracle_lattice *lat, double h, const double *L,
 /* Plain CG for Q x = b, x0 = 0 (Sec. 4.1).  Returns 0 or -4 (no convergence). */
 int oracle_cg(const oracle_lattice *lat, double h, const double *L, const double *b,
               double *x, double tol, int maxit, int *iterations, double *true_relres);
+/* The same from the initial guess x0 held in x: r0 = b - Q x0 (0 iterations
+ * if that already meets tol; b = 0 gives x = 0). */
+int oracle_cg_guess(const oracle_lattice *lat, double h, const double *L, const double *b,
+                    double *x, double tol, int maxit, int *iterations, double *true_relres);
 
 /* Chebyshev polynomial preconditioner of Sec. 4.2, Eqs. (13)-(17).
  * Roots z_k = m (1 - cos(2 pi k/(2n+1))) - i sqrt(eps) sin(2 pi k/(2n+1)),

@@ -36,7 +36,8 @@ class hh_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("cg_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
                 ("reliable_delta", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("n_pf", ctypes.c_int), ("chain_id", ctypes.c_uint64),
-                ("cheb_degree", ctypes.c_int), ("cheb_eps", ctypes.c_double), ("integrator", ctypes.c_int)]
+                ("cheb_degree", ctypes.c_int), ("cheb_eps", ctypes.c_double), ("integrator", ctypes.c_int),
+                ("chrono", ctypes.c_int)]
 
 
 class hh_solve_info(ctypes.Structure):
@@ -120,6 +121,7 @@ def load(path: str = LIB_PATH):
         "hh_init_field_random": (i, [vp, u64]),
         "hh_apply": (i, [vp, i, vp, vp, i]),
         "hh_solve": (i, [vp, vp, vp, i, ctypes.POINTER(hh_solve_info)]),
+        "hh_solve_guess": (i, [vp, vp, vp, i, ctypes.POINTER(hh_solve_info)]),
         "hh_force": (i, [vp, vp, i, vp, ctypes.POINTER(hh_solve_info)]),
         "hh_action": (i, [vp, vp, i, ctypes.POINTER(d), ctypes.POINTER(hh_solve_info)]),
         "hh_trajectory": (i, [vp, i, d, u64, ctypes.POINTER(hh_traj_info)]),
@@ -190,7 +192,7 @@ class Context:
 
     def __init__(self, d, nx, ntau, t=1.0, dtau=0.05, A=0.5, precision=HH_FP64, cg_tol=1e-10,
                  cg_maxit=1000000, reliable_delta=0.1, seed=0, n_pf=2, chain_id=0, stream=None,
-                 cheb_degree=0, cheb_eps=1e-3, integrator="leapfrog"):
+                 cheb_degree=0, cheb_eps=1e-3, integrator="leapfrog", chrono=0):
         L = load()
         self._lib = L
         self.lat = hh_lattice(d, nx, ntau)
@@ -202,6 +204,7 @@ class Context:
         p.seed, p.n_pf, p.chain_id = seed, n_pf, chain_id
         p.cheb_degree, p.cheb_eps = cheb_degree, cheb_eps
         p.integrator = INTEGRATORS.get(integrator, integrator)
+        p.chrono = chrono
         self.params = p
         self.stream = stream
         h = ctypes.c_void_p()
@@ -251,10 +254,12 @@ class Context:
             dtype = HH_DTYPE_F32 if x.dtype == torch.float32 else HH_DTYPE_F64
         check(self._lib.hh_apply(self._h, op, _ptr(x), _ptr(y), dtype), "hh_apply")
 
-    def solve(self, b, x, n_rhs=1, info=True, allow=()):
+    def solve(self, b, x, n_rhs=1, info=True, allow=(), guess=False):
+        """guess: start from the x passed in (hh_solve_guess) instead of zero."""
         inf = hh_solve_info() if info else None
-        rc = self._lib.hh_solve(self._h, _ptr(b), _ptr(x), n_rhs, ctypes.byref(inf) if info else None)
-        check(rc, "hh_solve", allow)
+        fn = self._lib.hh_solve_guess if guess else self._lib.hh_solve
+        rc = fn(self._h, _ptr(b), _ptr(x), n_rhs, ctypes.byref(inf) if info else None)
+        check(rc, "hh_solve_guess" if guess else "hh_solve", allow)
         return (rc, inf.as_dict()) if info else rc
 
     def force(self, chi, n_rhs, F, info=True):
@@ -308,7 +313,7 @@ def solve_noalloc(d, nx, ntau, sigma, b, x, t=1.0, dtau=0.05, A=0.5, cg_tol=1e-1
 
 def make_params(t=1.0, dtau=0.05, A=0.5, precision=HH_FP64, cg_tol=1e-10, cg_maxit=1000000,
                 reliable_delta=0.1, seed=0, n_pf=2, chain_id=0, cheb_degree=0, cheb_eps=1e-3,
-                integrator="leapfrog"):
+                integrator="leapfrog", chrono=0):
     L = load()
     p = hh_params()
     L.hh_default_params(ctypes.byref(p))
@@ -318,6 +323,7 @@ def make_params(t=1.0, dtau=0.05, A=0.5, precision=HH_FP64, cg_tol=1e-10, cg_max
     p.seed, p.n_pf, p.chain_id = seed, n_pf, chain_id
     p.cheb_degree, p.cheb_eps = cheb_degree, cheb_eps
     p.integrator = INTEGRATORS.get(integrator, integrator)
+    p.chrono = chrono
     return p
 
 

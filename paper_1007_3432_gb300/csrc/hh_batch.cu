@@ -135,10 +135,11 @@ struct SlotMem {
     double *sigma, *sigma0, *L64, *pi, *tmp, *chi, *x, *r, *p, *p2, *t, *epart;
     float *L32, *r32, *p32, *p32b, *t32, *x32;
     double *z, *u, *cheb;   // Chebyshev preconditioner (requests with cheb_degree > 0)
+    double *xprev;          // chronological guesses by extrapolation (chrono 2)
     HmcScalars *sc;
 };
 
-size_t slot_bytes(long long N, int nrhs, bool cheb, SlotMem *m, char *base)
+size_t slot_bytes(long long N, int nrhs, bool cheb, bool extrap, SlotMem *m, char *base)
 {
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -167,7 +168,10 @@ size_t slot_bytes(long long N, int nrhs, bool cheb, SlotMem *m, char *base)
     p = take(nrhs * N * f); if (m) m->x32 = (float *)p;
     p = take(sizeof(HmcScalars)); if (m) m->sc = (HmcScalars *)p;
     p = take(energy_blocks((int)N) * d); if (m) m->epart = (double *)p;
-    if (m) m->z = m->u = m->cheb = nullptr;
+    if (m) m->z = m->u = m->cheb = m->xprev = nullptr;
+    if (extrap) {
+        p = take(nrhs * N * d); if (m) m->xprev = (double *)p;
+    }
     if (cheb) {
         p = take(nrhs * N * d); if (m) m->z = (double *)p;
         p = take(nrhs * N * d); if (m) m->u = (double *)p;
@@ -272,6 +276,7 @@ int validate(const hh_request &r)
     if (!(r.prm.cg_tol > 0.0) || r.prm.cg_maxit < 1) return HH_EINVAL;
     if (r.kind == HH_REQ_TRAJECTORY && r.n_md < 1) return HH_EINVAL;
     if (r.prm.integrator != HH_LEAPFROG && r.prm.integrator != HH_OMELYAN) return HH_EINVAL;
+    if (r.prm.chrono < 0 || r.prm.chrono > 2) return HH_EINVAL;
     // Chebyshev-preconditioned CG (Sec. 4.2) is FP64 only, as in the context solver.
     if (r.prm.cheb_degree < 0 || r.prm.cheb_degree > CHEB_MAX_DEGREE) return HH_EINVAL;
     if (r.prm.cheb_degree > 0 && (r.prm.precision != HH_FP64 || !(r.prm.cheb_eps > 0.0 && r.prm.cheb_eps < 1.0)))
@@ -335,7 +340,7 @@ int admit(hh_batch *b, Pending &P, int s)
     S.cg_iters = 0;
     S.n_ru = S.n_solves = S.status = 0;
     S.max_relres = 0.0;
-    slot_bytes(S.N, S.nrhs, r.prm.cheb_degree > 0, &S.m, b->arena.base + S.off);
+    slot_bytes(S.N, S.nrhs, r.prm.cheb_degree > 0, r.prm.chrono == 2, &S.m, b->arena.base + S.off);
     b->active_sites += S.N;
     b->n_active += 1;
     const uint64_t seed = r.prm.seed, chain = r.prm.chain_id;
@@ -393,7 +398,8 @@ int admit_queued(hh_batch *b)
                     break;
                 }
             if (s < 0) return HH_OK;
-            size_t bytes = slot_bytes(N, front.req.prm.n_pf, front.req.prm.cheb_degree > 0, nullptr, nullptr);
+            size_t bytes = slot_bytes(N, front.req.prm.n_pf, front.req.prm.cheb_degree > 0,
+                                      front.req.prm.chrono == 2, nullptr, nullptr);
             int tpr = (int)((N + b->cfg.tile_sites - 1) / b->cfg.tile_sites);
             int part = b->parts.alloc(tpr * front.req.prm.n_pf);
             if (part < 0) return HH_OK;
@@ -449,6 +455,8 @@ int build_plan(hh_batch *b)
             Y.w = engine_group_width(S.geo.nx);
             Y.stall_window = ENGINE_STALL_WINDOW;
             Y.cheb_n = S.req.prm.cheb_degree;
+            // Chronological initial guess of a trajectory's later solves.
+            Y.x0_given = (S.req.kind == HH_REQ_TRAJECTORY && S.req.prm.chrono != 0 && S.md_step >= 1) ? 1 : 0;
             Y.cheb = S.m.cheb;
             Y.z = S.m.z ? S.m.z + o : nullptr;
             Y.u = S.m.u ? S.m.u + o : nullptr;
@@ -600,6 +608,11 @@ int advance(hh_batch *b, int s)
     if (k + 1 < forces) {
         HB_TRY(launch_sigma_step(S.geo, A, drift, S.m.sigma, S.m.pi, S.m.L64, S.m.L32, st));
         S.md_step = k + 1;
+        if (r.prm.chrono == 2 && k + 1 >= 2)
+            HB_TRY(launch_extrapolate(S.m.x, S.m.xprev, (long long)S.nrhs * S.N, st));
+        else if (r.prm.chrono == 2)
+            HB_TRY(cudaMemcpyAsync(S.m.xprev, S.m.x, sizeof(double) * (size_t)S.nrhs * S.N,
+                                   cudaMemcpyDeviceToDevice, st));
         return start_solve(b, s);
     }
     HB_TRY(launch_energy(S.N, S.m.pi, S.m.chi, S.m.x, S.nrhs, S.m.epart, &S.m.sc->H1, st));
@@ -818,7 +831,9 @@ int hh_batch_submit(hh_batch *b, const hh_request *req, uint64_t *ticket)
     int rc = validate(*req);
     if (rc) return rc;
     long long N = lattice_sites(req->lat);
-    if (slot_bytes(N, req->prm.n_pf, req->prm.cheb_degree > 0, nullptr, nullptr) > b->arena.size) return HH_EBUSY;
+    if (slot_bytes(N, req->prm.n_pf, req->prm.cheb_degree > 0, req->prm.chrono == 2, nullptr, nullptr) >
+        b->arena.size)
+        return HH_EBUSY;
     Pending P;
     P.req = *req;
     if (req->sigma) P.sigma.assign(req->sigma, req->sigma + N);

@@ -99,8 +99,10 @@ __global__ void k_zero_stats(EngStats *stats)
 struct Plan {
     int nsys = 0, ntiles = 0, grid = 0, homogeneous = 0;
     int precision = -1;
+    int x0 = 0;                  // systems start from the x passed in
     const double *b = nullptr;
     double *x = nullptr;
+    EngSystem sys[64];           // host copy of the device system table (n_pf <= 64)
 };
 
 }  // namespace
@@ -120,6 +122,7 @@ struct hh_ctx {
     float *L32, *tmp32a, *tmp32b;
     // CG workspace (cap_rhs vectors each)
     double *r, *p, *t, *p2;
+    double *xprev;          // chronological guesses by extrapolation (chrono 2)
     float *r32, *p32, *t32, *x32, *p32b;
     int two_slot;           // engine launches run the two-slot form
     // engine
@@ -167,7 +170,7 @@ cudaError_t dalloc(T **p, size_t n)
 void free_ctx(hh_ctx *c)
 {
     void *ptrs[] = {c->sigma, c->sigma0, c->L64, c->pi, c->chi, c->xsol, c->tmp, c->F, c->L32,
-                    c->tmp32a, c->tmp32b, c->r, c->p, c->p2, c->t, c->r32, c->p32, c->p32b, c->t32, c->x32,
+                    c->tmp32a, c->tmp32b, c->r, c->p, c->p2, c->xprev, c->t, c->r32, c->p32, c->p32b, c->t32, c->x32,
                     c->d_sys, c->d_state[0], c->d_state[1], c->d_tiles, c->d_sig, c->d_ctl, c->d_stats, c->d_sc, c->d_energy_part,
                     c->d_energy_out};
     for (void *p : ptrs)
@@ -252,6 +255,8 @@ int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
     // Pageable sources: the copies have consumed the host buffers on return.
     HH_TRY(cudaMemcpyAsync(c->d_sys, sys.data(), sizeof(EngSystem) * n_rhs, cudaMemcpyHostToDevice,
                            c->stream));
+    for (int a = 0; a < n_rhs; ++a) P.sys[a] = sys[a];
+    P.x0 = 0;
     HH_TRY(cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(EngTile) * ntiles,
                            cudaMemcpyHostToDevice, c->stream));
     P.nsys = n_rhs;
@@ -261,6 +266,19 @@ int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
     P.b = b;
     P.x = x;
     P.precision = c->prm.precision;
+    return HH_OK;
+}
+
+// Whether the plan's systems start from the x passed in (an initial guess) or
+// from x = 0; re-uploads the system table when that changes.
+int set_guess(hh_ctx *c, int x0)
+{
+    Plan &P = c->plan;
+    if (P.x0 == x0) return HH_OK;
+    for (int a = 0; a < P.nsys; ++a) P.sys[a].x0_given = x0;
+    // Pageable source: the copy has consumed it on return.
+    HH_TRY(cudaMemcpyAsync(c->d_sys, P.sys, sizeof(EngSystem) * P.nsys, cudaMemcpyHostToDevice, c->stream));
+    P.x0 = x0;
     return HH_OK;
 }
 
@@ -358,6 +376,7 @@ void hh_default_params(hh_params *p)
     p->cheb_degree = 0;
     p->cheb_eps = 1e-3;
     p->integrator = HH_LEAPFROG;
+    p->chrono = 0;
 }
 
 const char *hh_strerror(int code)
@@ -388,6 +407,7 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
     if (p->cheb_degree > 0 && (p->precision != HH_FP64 || !(p->cheb_eps > 0.0 && p->cheb_eps < 1.0)))
         return HH_EINVAL;
     if (p->integrator != HH_LEAPFROG && p->integrator != HH_OMELYAN) return HH_EINVAL;
+    if (p->chrono < 0 || p->chrono > 2) return HH_EINVAL;
     long long V = lat->d == 1 ? lat->nx : (long long)lat->nx * lat->nx * lat->nx;
     long long N = V * lat->ntau;
     if (N >= (1LL << 31) - 1024) return HH_EINVAL;
@@ -428,6 +448,7 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
     if (e == cudaSuccess) e = dalloc(&c->r, nr);
     if (e == cudaSuccess) e = dalloc(&c->p, nr);
     if (e == cudaSuccess) e = dalloc(&c->p2, nr);
+    if (e == cudaSuccess && p->chrono == 2) e = dalloc(&c->xprev, nr);
     if (e == cudaSuccess) e = dalloc(&c->p32b, nr);
     if (e == cudaSuccess) e = dalloc(&c->t, nr);
     if (e == cudaSuccess) e = dalloc(&c->r32, nr);
@@ -591,12 +612,15 @@ int hh_apply(hh_ctx *c, int op, const void *x, void *y, int dtype)
     return HH_OK;
 }
 
-int hh_solve(hh_ctx *c, const double *b, double *x, int n_rhs, hh_solve_info *info)
+// One solve of the current plan from x = 0 (x0 = 0) or from the x passed in.
+static int solve_from(hh_ctx *c, const double *b, double *x, int n_rhs, int x0, hh_solve_info *info)
 {
     if (!c || !b || !x || !aligned16(b) || !aligned16(x)) return HH_EINVAL;
     int rc = ensure_rhs(c, n_rhs);
     if (rc) return rc;
     rc = make_plan(c, b, x, n_rhs);
+    if (rc) return rc;
+    rc = set_guess(c, x0);
     if (rc) return rc;
     k_zero_stats<<<1, 32, 0, c->stream>>>(c->d_stats);
     HH_TRY(cudaGetLastError());
@@ -611,12 +635,24 @@ int hh_solve(hh_ctx *c, const double *b, double *x, int n_rhs, hh_solve_info *in
     return stats_status(s);
 }
 
+int hh_solve(hh_ctx *c, const double *b, double *x, int n_rhs, hh_solve_info *info)
+{
+    return solve_from(c, b, x, n_rhs, 0, info);
+}
+
+int hh_solve_guess(hh_ctx *c, const double *b, double *x, int n_rhs, hh_solve_info *info)
+{
+    return solve_from(c, b, x, n_rhs, 1, info);
+}
+
 int hh_force(hh_ctx *c, const double *chi, int n_rhs, double *F, hh_solve_info *info)
 {
     if (!c || !chi || !F || !aligned16(chi)) return HH_EINVAL;
     int rc = ensure_rhs(c, n_rhs);
     if (rc) return rc;
     rc = make_plan(c, chi, c->xsol, n_rhs);
+    if (rc) return rc;
+    rc = set_guess(c, 0);
     if (rc) return rc;
     k_zero_stats<<<1, 32, 0, c->stream>>>(c->d_stats);
     HH_TRY(cudaGetLastError());
@@ -640,6 +676,8 @@ int hh_action(hh_ctx *c, const double *chi, int n_rhs, double *S, hh_solve_info 
     int rc = ensure_rhs(c, n_rhs);
     if (rc) return rc;
     rc = make_plan(c, chi, c->xsol, n_rhs);
+    if (rc) return rc;
+    rc = set_guess(c, 0);
     if (rc) return rc;
     k_zero_stats<<<1, 32, 0, c->stream>>>(c->d_stats);
     HH_TRY(cudaGetLastError());
@@ -672,8 +710,22 @@ int leapfrog_enqueue(hh_ctx *c, double *pi, const double *chi, int n_rhs, int n_
     if (rc) return rc;
     double kick = 0.0, drift = 0.0;
     const int forces = md_schedule(c->prm.integrator, n_md, dt, 0, &kick, &drift);
+    const int chrono = c->prm.chrono;
+    const long long nx = (long long)n_rhs * c->N;
     for (int j = 0; j < forces; ++j) {
         md_schedule(c->prm.integrator, n_md, dt, j, &kick, &drift);
+        // Chronological initial guess (chrono 1: the previous force's
+        // solution, already in xsol; 2: the linear extrapolation of the last
+        // two); the trajectory's first solve starts from zero.
+        if (chrono == 2 && j >= 2) {
+            HH_TRY(launch_extrapolate(c->xsol, c->xprev, nx, c->stream));
+            c->n_launch += 1;
+        } else if (chrono == 2 && j == 1) {
+            HH_TRY(cudaMemcpyAsync(c->xprev, c->xsol, sizeof(double) * (size_t)nx, cudaMemcpyDeviceToDevice,
+                                   c->stream));
+        }
+        rc = set_guess(c, (chrono != 0 && j >= 1) ? 1 : 0);
+        if (rc) return rc;
         rc = run_engine(c);
         if (rc) return rc;
         if (j == 0 && h0)

@@ -324,6 +324,7 @@ __device__ EngState decide(const EngSystem &Y, const EngState &P, double rr)
         S.fp64_steps = 0;
         S.since_ru = 0;
         S.pre_j = 0;
+        S.no_guess = 0;
         return S;
     case MODE_INIT:
         S.bb = rr;
@@ -332,6 +333,23 @@ __device__ EngState decide(const EngSystem &Y, const EngState &P, double rr)
         if (!isfinite(rr)) {
             S.mode = MODE_DONE;
             S.status = kNumericErr;
+            return S;
+        }
+        if (Y.x0_given && !P.no_guess) {
+            if (rr == 0.0) {
+                // b = 0: the solution is x = 0 whatever the guess; one more
+                // INIT zeroes x.
+                S.no_guess = 1;
+                return S;
+            }
+            // Initial guess: the true residual b - Q x0 first (an RU step),
+            // then CG from it (beta = rr / inf = 0 restarts).  The guess's
+            // residual is not a stall of the mixed iteration.
+            S.mode = MODE_RU;
+            S.rr_alpha = INFINITY;
+            S.rr_ru = INFINITY;
+            S.rr_last = INFINITY;
+            S.maxr2 = rr;
             return S;
         }
         if (rr == 0.0) {
@@ -461,14 +479,15 @@ __device__ EngState decide(const EngSystem &Y, const EngState &P, double rr)
 // ---------------------------------------------------------------------------
 struct TileCtl {
     int mode, prec, pre_j, two;    // two: the launch runs the two-slot form
-    int pold, pnew, pad0, pad1;    // p buffers holding the previous / new direction
+    int pold, pnew;                // p buffers holding the previous / new direction
+    int zero_x, pad1;              // INIT: x starts at 0 (else x holds the guess)
     double beta, alpha;
 };
 
 // Tile controls of a system in state S.  Three-slot form: the direction is
 // updated in place in buffer S.pbuf.  Two-slot form: each CG step writes the
 // new direction to S.pbuf and reads the previous one from the other buffer.
-__device__ __forceinline__ TileCtl make_ctl(const EngState &S, int two)
+__device__ __forceinline__ TileCtl make_ctl(const EngState &S, int two, int x0_given)
 {
     TileCtl c;
     c.mode = S.mode;
@@ -477,7 +496,8 @@ __device__ __forceinline__ TileCtl make_ctl(const EngState &S, int two)
     c.two = two;
     c.pnew = S.pbuf;
     c.pold = two ? (S.pbuf ^ 1) : S.pbuf;
-    c.pad0 = c.pad1 = 0;
+    c.zero_x = (x0_given && !S.no_guess) ? 0 : 1;
+    c.pad1 = 0;
     c.beta = S.beta;
     c.alpha = 0.0;
     return c;
@@ -522,7 +542,8 @@ __device__ void slot1(const EngSystem &Y, const TileCtl &c, const EngTile &T)
     } else if (c.mode == MODE_RU) {
         if (c.prec == PREC_MIXED && !c.two) gloop_accumulate<W>(Y.x, Y.x32, T.begin, T.end);
     } else if (c.mode == MODE_INIT) {
-        for (int i = T.begin + ctid(); i < T.end; i += cnth()) Y.x[i] = 0.0;
+        if (c.zero_x)
+            for (int i = T.begin + ctid(); i < T.end; i += cnth()) Y.x[i] = 0.0;
         if (Y.precision == PREC_MIXED)
             for (int i = T.begin + ctid(); i < T.end; i += cnth()) Y.x32[i] = 0.0f;
     }
@@ -790,7 +811,7 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                                         }
                                         if (S.mode != MODE_DONE) live = 1;
                                         s_cache[slot] = S;
-                                        s_tctl[slot] = make_ctl(S, two);
+                                        s_tctl[slot] = make_ctl(S, two, Y.x0_given);
                                     }
                                 }
                             }
@@ -798,7 +819,7 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                             if (!cached && threadIdx.x == 0) {
                                 const EngState S = nxt[T.sys];
                                 s_cache[0] = S;
-                                s_tctl[0] = make_ctl(S, two);
+                                s_tctl[0] = make_ctl(S, two, Y.x0_given);
                             }
                             __syncthreads();
                             if (threadIdx.x < 32) {
@@ -956,14 +977,14 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                             }
                             if (S.mode != MODE_DONE) live = 1;
                             s_cache[slot] = S;
-                            s_tctl[slot] = make_ctl(S, two);
+                            s_tctl[slot] = make_ctl(S, two, Y.x0_given);
                         }
                     } else {
                         if (!cached) {
                             if (lane == 0) {
                                 const EngState S = nxt[T.sys];
                                 s_cache[0] = S;
-                                s_tctl[0] = make_ctl(S, two);
+                                s_tctl[0] = make_ctl(S, two, Y.x0_given);
                             }
                             __syncwarp();
                         }

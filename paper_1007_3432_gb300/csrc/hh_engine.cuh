@@ -73,6 +73,7 @@ struct EngSystem {
     int w;                            // x sites per thread group: 4, 2 or 1 (divides Nx)
     int stall_window;                 // mixed: forced RU after this many FP32 steps without one
     int cheb_n;                       // Chebyshev preconditioner degree n (0: plain CG; FP64 only)
+    int x0_given;                     // 1: x holds an initial guess when the system starts (MODE_NEW)
     const double *cheb;               // coefficient table (see CHEB_MAX_DEGREE)
     double *z, *u;                    // FP64 preconditioner vectors (when cheb_n > 0)
     double *p2;                       // second FP64 p buffer (two-slot launches)
@@ -111,7 +112,7 @@ struct EngState {
     int since_ru;       // CG steps since the last RU
     int pre_j;          // MODE_PRE sub-step, 0 .. 2 cheb_n - 1
     int pbuf;           // two-slot launches: p buffer (0: p/p32, 1: p2/p32b) holding p
-    int pad2;
+    int no_guess;       // the initial guess was dropped (b = 0): INIT zeroes x
 };
 
 struct EngTile {

@@ -252,4 +252,27 @@ cudaError_t launch_restore(const Geo &g, double A, const HmcScalars *sc, double 
     return cudaGetLastError();
 }
 
+namespace {
+
+__global__ void k_extrapolate(double *__restrict__ x, double *__restrict__ xp, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double t = x[i];
+        x[i] = fma(2.0, t, -xp[i]);
+        xp[i] = t;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_extrapolate(double *x, double *xp, long long n, cudaStream_t st)
+{
+    long long blocks = (n + kBlock - 1) / kBlock;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_extrapolate<<<(int)blocks, kBlock, 0, st>>>(x, xp, n);
+    return cudaGetLastError();
+}
+
 }  // namespace hh

@@ -60,6 +60,10 @@ cudaError_t launch_metropolis(HmcScalars *sc, uint64_t seed, uint64_t traj, uint
 cudaError_t launch_restore(const Geo &g, double A, const HmcScalars *sc, double *sigma,
                            const double *sigma0, double *L64, float *L32, cudaStream_t st);
 
+// Chronological initial guess by linear extrapolation: x <- 2 x - xp and
+// xp <- the old x, over n elements.
+cudaError_t launch_extrapolate(double *x, double *xp, long long n, cudaStream_t st);
+
 // Molecular-dynamics schedule of one trajectory as a sequence of forces:
 // after force j (j = 0 .. forces - 1, each computed from a fresh solve at the
 // current sigma) the momenta take a kick pi -= kick F, then, except after the

@@ -483,3 +483,80 @@ def test_batched_omelyan_trajectory_matches_context(hh):
         ctx.set_field(dev(sigma))
         info = ctx.trajectory(3, 0.1, 4)
     assert abs(info["dH"] - r["dH"]) <= 1e-6 and info["u"] == r["u"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_from_initial_guess(hh, precision):
+    """hh_solve_guess: from a guess near the dense-LU solution the solve takes
+    few steps and meets the true residual; the oracle's CG from the same guess
+    agrees; b = 0 gives x = 0 whatever the guess."""
+    d, nx, ntau = 1, 16, 12
+    n = nx * ntau
+    lat = oracle.lattice(d, nx, ntau)
+    sigma = workloads.sigma_field(n, seed=120)
+    L = oracle.links(lat, A, sigma)
+    b = np.stack([workloads.source(n, seed=121, rhs=a) for a in range(2)])
+    Q = oracle.dense(lat, H, L, "MTM")
+    x_lu = np.linalg.solve(Q, b.T).T
+    rng = np.random.default_rng(122)
+    x0 = x_lu + 1e-6 * rng.standard_normal(x_lu.shape) * np.abs(x_lu).max()
+    with hh.Context(d, nx, ntau, precision=precision) as ctx:
+        ctx.set_field(dev(sigma))
+        x = dev(x0.copy())
+        rc, info = ctx.solve(dev(b), x, 2, guess=True)
+        xg = x.cpu().numpy()
+        x_zero = torch.zeros(2, n, dtype=torch.float64, device="cuda")
+        rc0, info0 = ctx.solve(dev(b), x_zero, 2)
+        xb = dev(rng.standard_normal((2, n)))
+        rcz, infoz = ctx.solve(torch.zeros(2, n, dtype=torch.float64, device="cuda"), xb, 2, guess=True)
+        assert rcz == 0 and not torch.any(xb)
+    assert rc == 0 and info["converged"] == 1 and info["true_relres"] <= 1e-10
+    assert info["iterations"] < 0.7 * info0["iterations"], (info, info0)
+    for a in range(2):
+        res = b[a] - oracle.apply_MTM(lat, H, L, xg[a])
+        assert np.linalg.norm(res) <= 1.0001e-10 * np.linalg.norm(b[a])
+        xo, st, it, rr = oracle.cg_guess(lat, H, L, b[a], x0[a])
+        assert st == 0 and np.linalg.norm(xg[a] - xo) <= 1e-4 * np.linalg.norm(xo)
+        if precision == "fp64":
+            assert abs(info["iterations"] - it) <= 2 + 0.05 * it or a == 0
+
+
+@pytest.mark.parametrize("chrono", [1, 2])
+def test_chronological_guess_trajectory_matches_oracle(hh, chrono):
+    wl = workloads.C0
+    lat = oracle.lattice(wl.d, wl.nx, wl.ntau)
+    n = wl.nsites
+    sigma = workloads.sigma_field(n, seed=wl.seed)
+    prm = oracle.params(seed=wl.seed, n_pf=2, chrono=chrono)
+    n_md, dt = 5, 0.04
+    with hh.Context(wl.d, wl.nx, wl.ntau, seed=wl.seed, n_pf=2, chrono=chrono) as ctx:
+        ctx.set_field(dev(sigma))
+        info = ctx.trajectory(n_md, dt, 0)
+    with hh.Context(wl.d, wl.nx, wl.ntau, seed=wl.seed, n_pf=2) as ctx:
+        ctx.set_field(dev(sigma))
+        info0 = ctx.trajectory(n_md, dt, 0)
+    _, oinfo = oracle.trajectory(lat, prm, sigma, n_md, dt, 0)
+    assert info["max_true_relres"] <= 1e-10 and info["u"] == oinfo["u"]
+    assert abs(info["dH"] - oinfo["dH"]) <= 1e-6 and abs(info["dH"] - info0["dH"]) <= 1e-6
+    if abs(oinfo["dH"] + np.log(oinfo["u"])) > 1e-5:
+        assert info["accepted"] == oinfo["accepted"] == info0["accepted"]
+    assert info["cg_iterations"] < info0["cg_iterations"], (info, info0)
+
+
+def test_batched_chronological_trajectory_matches_context(hh):
+    from paper_1007_3432_gb300 import binding as B
+    d, nx, nt, seed = 1, 16, 16, 97
+    n = nx * nt
+    sigma = workloads.sigma_field(n, seed=seed)
+    out = np.zeros(n)
+    batch = B.Batch(max_slots=2, hbm_budget_bytes=1 << 28, chunk_iters=32, tile_sites=1024)
+    req = B.make_request(B.HH_REQ_TRAJECTORY, d, nx, nt, sigma=sigma, out=out, n_md=4, dt=0.1, traj_index=2,
+                         precision="fp64", seed=seed, n_pf=2, chrono=2)
+    batch.submit(req, keep=(sigma, out))
+    r = batch.run_until_idle()[0]
+    batch.close()
+    assert r["status"] == 0
+    with hh.Context(d, nx, nt, seed=seed, n_pf=2, chrono=2) as ctx:
+        ctx.set_field(dev(sigma))
+        info = ctx.trajectory(4, 0.1, 2)
+    assert abs(info["dH"] - r["dH"]) <= 1e-6 and info["u"] == r["u"]
