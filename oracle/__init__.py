@@ -25,7 +25,7 @@ class Params(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("dtau", ctypes.c_double), ("A", ctypes.c_double),
                 ("cg_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int), ("n_pf", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("chain", ctypes.c_uint64), ("integrator", ctypes.c_int),
-                ("chrono", ctypes.c_int)]
+                ("chrono", ctypes.c_int), ("link_order", ctypes.c_int)]
 
 
 class TrajInfo(ctypes.Structure):
@@ -65,10 +65,11 @@ def lattice(d, nx, ntau):
 
 
 def params(t=1.0, dtau=0.05, A=0.5, cg_tol=1e-10, cg_maxit=100000, n_pf=2, seed=1007, chain=0, integrator=0,
-           chrono=0):
+           chrono=0, link_order=0):
     """integrator: 0 leapfrog (Sec. 4.1), 1 Omelyan's second-order minimum-norm scheme.
-    chrono: initial guess of the MD solves (0 zero, 1 last solution, 2 linear extrapolation)."""
-    return Params(t, dtau, A, cg_tol, cg_maxit, n_pf, seed, chain, integrator, chrono)
+    chrono: initial guess of the MD solves (0 zero, 1 last solution, 2 linear extrapolation).
+    link_order: form of M (0 reading R1; 1, 2 the exact-block form expanded to that order)."""
+    return Params(t, dtau, A, cg_tol, cg_maxit, n_pf, seed, chain, integrator, chrono, link_order)
 
 
 def nsites(lat):
@@ -100,6 +101,39 @@ def apply_MT(lat, h, L, x):
 
 def apply_MTM(lat, h, L, x):
     return _apply(lib().oracle_apply_MTM, lat, h, L, x)
+
+
+def _apply_ex(fn, lat, h, L, order, x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    y = np.empty(nsites(lat))
+    fn(ctypes.byref(lat), ctypes.c_double(h), _ptr(L), ctypes.c_int(order), _ptr(x), _ptr(y))
+    return y
+
+
+def apply_M_ex(lat, h, L, order, x):
+    return _apply_ex(lib().oracle_apply_M_ex, lat, h, L, order, x)
+
+
+def apply_MT_ex(lat, h, L, order, x):
+    return _apply_ex(lib().oracle_apply_MT_ex, lat, h, L, order, x)
+
+
+def apply_MTM_ex(lat, h, L, order, x):
+    return _apply_ex(lib().oracle_apply_MTM_ex, lat, h, L, order, x)
+
+
+def cg_ex(lat, h, L, order, b, x0=None, tol=1e-10, maxit=100000):
+    """CG for the M of the given order, from zero or from x0."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    x = np.zeros(nsites(lat)) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = lib().oracle_cg_ex(ctypes.byref(lat), ctypes.c_double(h), _ptr(L), ctypes.c_int(order), _ptr(b), _ptr(x),
+                            ctypes.c_int(0 if x0 is None else 1), ctypes.c_double(tol), ctypes.c_int(maxit),
+                            ctypes.byref(it), ctypes.byref(rr))
+    return x, st, it.value, rr.value
 
 
 def cg(lat, h, L, b, tol=1e-10, maxit=100000):
@@ -236,10 +270,13 @@ def trajectory(lat, prm, sigma, n_md, dt, traj):
     return sigma, info.as_dict()
 
 
-def dense(lat, h, L, which="M"):
+def dense(lat, h, L, which="M", order=0):
     """Dense matrix of M, M^T or M^T M built column by column (small lattices only)."""
     n = nsites(lat)
     fn = {"M": apply_M, "MT": apply_MT, "MTM": apply_MTM}[which]
+    if order:
+        ex = {"M": apply_M_ex, "MT": apply_MT_ex, "MTM": apply_MTM_ex}[which]
+        fn = lambda lat_, h_, L_, x_: ex(lat_, h_, L_, order, x_)
     D = np.empty((n, n))
     e = np.zeros(n)
     for j in range(n):

@@ -152,6 +152,85 @@ void oracle_apply_MTM(const oracle_lattice *lat, double h, const double *L,
     free(tmp);
 }
 
+/* E v on every time slice: E = 1 + h H (order 1) or 1 + h H + h^2 H^2 / 2
+ * (order 2), (H v)(n,tau) the sum of v over the 2d spatial neighbours: the
+ * expansion of e^{-dtau K} = e^{h H} (K = -t H, Sec. 2, Eqs. (8)-(9)). */
+static void hop_factor(const oracle_lattice *lat, double h, int order, const double *v, double *out)
+{
+    long n = oracle_nsites(lat);
+    int c[3], tau;
+    double *hv = (double *)malloc(sizeof(double) * (size_t)n);
+    for (long i = 0; i < n; ++i) {
+        site_coords(lat, i, c, &tau);
+        hv[i] = neighbour_sum(lat, v, c, tau);
+    }
+    for (long i = 0; i < n; ++i) out[i] = v[i] + h * hv[i];
+    if (order == 2)
+        for (long i = 0; i < n; ++i) {
+            site_coords(lat, i, c, &tau);
+            out[i] += 0.5 * h * h * neighbour_sum(lat, hv, c, tau);
+        }
+    free(hv);
+}
+
+/* Exact-block form of M: the blocks of Eq. (7) with B = e^{-dtau K} e^{-dtau V},
+ * e^{-dtau K} expanded to order 1 or 2 (E above), e^{-dtau V} = 1 + A sin sigma
+ * (reading R2), and the diagonal blocks 1:
+ *   (M x)(n,tau) = x(n,tau) + [E w](n,tau-1),  w(m,tau') = L(m,tau') x(m,tau'),
+ * with L = -(1 + A sin sigma) and + on the wrap link as in oracle_links.
+ * order 0 is the form of oracle_apply_M (reading R1). */
+void oracle_apply_M_ex(const oracle_lattice *lat, double h, const double *L, int order,
+                       const double *x, double *y)
+{
+    if (order == 0) {
+        oracle_apply_M(lat, h, L, x, y);
+        return;
+    }
+    long n = oracle_nsites(lat);
+    int c[3], tau;
+    double *w = (double *)malloc(sizeof(double) * (size_t)n);
+    double *ew = (double *)malloc(sizeof(double) * (size_t)n);
+    for (long i = 0; i < n; ++i) w[i] = L[i] * x[i];
+    hop_factor(lat, h, order, w, ew);
+    for (long i = 0; i < n; ++i) {
+        site_coords(lat, i, c, &tau);
+        long iprev = site_index(lat, c, (tau + lat->ntau - 1) % lat->ntau);
+        y[i] = x[i] + ew[iprev];
+    }
+    free(w);
+    free(ew);
+}
+
+/* (M^T y)(m,tau) = y(m,tau) + L(m,tau) [E y](m,tau+1): E is symmetric. */
+void oracle_apply_MT_ex(const oracle_lattice *lat, double h, const double *L, int order,
+                        const double *x, double *y)
+{
+    if (order == 0) {
+        oracle_apply_MT(lat, h, L, x, y);
+        return;
+    }
+    long n = oracle_nsites(lat);
+    int c[3], tau;
+    double *ex = (double *)malloc(sizeof(double) * (size_t)n);
+    hop_factor(lat, h, order, x, ex);
+    for (long i = 0; i < n; ++i) {
+        site_coords(lat, i, c, &tau);
+        long inext = site_index(lat, c, (tau + 1) % lat->ntau);
+        y[i] = x[i] + L[i] * ex[inext];
+    }
+    free(ex);
+}
+
+void oracle_apply_MTM_ex(const oracle_lattice *lat, double h, const double *L, int order,
+                         const double *x, double *y)
+{
+    long n = oracle_nsites(lat);
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)n);
+    oracle_apply_M_ex(lat, h, L, order, x, tmp);
+    oracle_apply_MT_ex(lat, h, L, order, tmp, y);
+    free(tmp);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Conjugate gradient for Q x = b (Sec. 4.1).                               */
 /* ------------------------------------------------------------------------ */
@@ -166,7 +245,7 @@ static double dot(long n, const double *a, const double *b)
 /* CG for Q x = b from x0 = 0, or from the x passed in when guess != 0
  * (r0 = b - Q x0, stopping at once if that already meets tol; b = 0 gives
  * x = 0 either way). */
-static int cg_from(const oracle_lattice *lat, double h, const double *L, const double *b,
+static int cg_from(const oracle_lattice *lat, double h, const double *L, int order, const double *b,
                    double *x, int guess, double tol, int maxit, int *iterations, double *true_relres)
 {
     long n = oracle_nsites(lat);
@@ -182,7 +261,7 @@ static int cg_from(const oracle_lattice *lat, double h, const double *L, const d
             r[i] = b[i];
         }
     } else {
-        oracle_apply_MTM(lat, h, L, x, q);
+        oracle_apply_MTM_ex(lat, h, L, order, x, q);
         for (long i = 0; i < n; ++i) r[i] = b[i] - q[i];
     }
     for (long i = 0; i < n; ++i) p[i] = r[i];
@@ -198,7 +277,7 @@ static int cg_from(const oracle_lattice *lat, double h, const double *L, const d
         goto done;
     }
     for (k = 1; k <= maxit; ++k) {
-        oracle_apply_MTM(lat, h, L, p, q);
+        oracle_apply_MTM_ex(lat, h, L, order, p, q);
         double alpha = rr / dot(n, p, q);
         for (long i = 0; i < n; ++i) {
             x[i] += alpha * p[i];
@@ -207,7 +286,7 @@ static int cg_from(const oracle_lattice *lat, double h, const double *L, const d
         double rr_new = dot(n, r, r);
         if (sqrt(rr_new) <= tol * bnorm) {
             /* Confirm with the true residual b - Q x (reading R5). */
-            oracle_apply_MTM(lat, h, L, x, q);
+            oracle_apply_MTM_ex(lat, h, L, order, x, q);
             for (long i = 0; i < n; ++i) r[i] = b[i] - q[i];
             rr_new = dot(n, r, r);
             *true_relres = sqrt(rr_new) / bnorm;
@@ -221,7 +300,7 @@ static int cg_from(const oracle_lattice *lat, double h, const double *L, const d
         for (long i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
     }
     if (status != 0) {
-        oracle_apply_MTM(lat, h, L, x, q);
+        oracle_apply_MTM_ex(lat, h, L, order, x, q);
         for (long i = 0; i < n; ++i) r[i] = b[i] - q[i];
         *true_relres = sqrt(dot(n, r, r)) / bnorm;
         k = maxit;
@@ -237,13 +316,19 @@ done:
 int oracle_cg(const oracle_lattice *lat, double h, const double *L, const double *b,
               double *x, double tol, int maxit, int *iterations, double *true_relres)
 {
-    return cg_from(lat, h, L, b, x, 0, tol, maxit, iterations, true_relres);
+    return cg_from(lat, h, L, 0, b, x, 0, tol, maxit, iterations, true_relres);
 }
 
 int oracle_cg_guess(const oracle_lattice *lat, double h, const double *L, const double *b,
                     double *x, double tol, int maxit, int *iterations, double *true_relres)
 {
-    return cg_from(lat, h, L, b, x, 1, tol, maxit, iterations, true_relres);
+    return cg_from(lat, h, L, 0, b, x, 1, tol, maxit, iterations, true_relres);
+}
+
+int oracle_cg_ex(const oracle_lattice *lat, double h, const double *L, int order, const double *b,
+                 double *x, int guess, double tol, int maxit, int *iterations, double *true_relres)
+{
+    return cg_from(lat, h, L, order, b, x, guess, tol, maxit, iterations, true_relres);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -512,7 +597,7 @@ void oracle_heatbath(const oracle_lattice *lat, const oracle_params *p,
     oracle_links(lat, p->A, sigma, L);
     for (int a = 0; a < p->n_pf; ++a) {
         oracle_gaussian(p->seed, 2, a, traj, p->chain, n, xi);
-        oracle_apply_MT(lat, p->t * p->dtau, L, xi, chi + (long)a * n);
+        oracle_apply_MT_ex(lat, p->t * p->dtau, L, p->link_order, xi, chi + (long)a * n);
     }
     free(L);
     free(xi);
@@ -532,7 +617,8 @@ double oracle_action(const oracle_lattice *lat, const oracle_params *p,
     for (int a = 0; a < p->n_pf; ++a) {
         int it;
         double rr;
-        int st = oracle_cg(lat, h, L, chi + (long)a * n, x, p->cg_tol, p->cg_maxit, &it, &rr);
+        int st = oracle_cg_ex(lat, h, L, p->link_order, chi + (long)a * n, x, 0, p->cg_tol, p->cg_maxit,
+                              &it, &rr);
         if (st != 0) *status = st;
         *iters += it;
         if (rr > *relres) *relres = rr;
@@ -557,6 +643,7 @@ static void force_from(const oracle_lattice *lat, const oracle_params *p, const 
     double h = p->t * p->dtau;
     double *L = (double *)malloc(sizeof(double) * (size_t)n);
     double *y = (double *)malloc(sizeof(double) * (size_t)n);
+    double *ey = (double *)malloc(sizeof(double) * (size_t)n);
     int c[3], tau;
     oracle_links(lat, p->A, sigma, L);
     for (long i = 0; i < n; ++i) F[i] = 0.0;
@@ -564,12 +651,18 @@ static void force_from(const oracle_lattice *lat, const oracle_params *p, const 
         int it;
         double rr;
         double *x = xs + (long)a * n;
-        int st = guess ? oracle_cg_guess(lat, h, L, chi + (long)a * n, x, p->cg_tol, p->cg_maxit, &it, &rr)
-                       : oracle_cg(lat, h, L, chi + (long)a * n, x, p->cg_tol, p->cg_maxit, &it, &rr);
+        int st = oracle_cg_ex(lat, h, L, p->link_order, chi + (long)a * n, x, guess, p->cg_tol, p->cg_maxit,
+                              &it, &rr);
         if (st != 0) *status = st;
         *iters += it;
         if (rr > *relres) *relres = rr;
-        oracle_apply_M(lat, h, L, x, y);
+        oracle_apply_M_ex(lat, h, L, p->link_order, x, y);
+        /* Exact-block form: sigma(n,tau) enters through w(n,tau) = L x, seen by
+         * row (., tau+1) through E, so the factor of y is (E y)(n, tau+1). */
+        if (p->link_order != 0) {
+            hop_factor(lat, h, p->link_order, y, ey);
+            for (long i = 0; i < n; ++i) y[i] = ey[i];
+        }
         for (long i = 0; i < n; ++i) {
             site_coords(lat, i, c, &tau);
             long inext = site_index(lat, c, (tau + 1) % lat->ntau);
@@ -579,6 +672,7 @@ static void force_from(const oracle_lattice *lat, const oracle_params *p, const 
     }
     free(L);
     free(y);
+    free(ey);
 }
 
 void oracle_force(const oracle_lattice *lat, const oracle_params *p, const double *sigma,

@@ -47,6 +47,8 @@ typedef struct {
                          1 the previous force's solution; 2 linear extrapolation
                          of the last two.  Not part of the paper's method: it
                          makes the MD reversible only to the CG tolerance. */
+    int link_order;   /* form of M: 0 reading R1 (oracle_apply_M); 1, 2 the
+                         exact-block form (oracle_apply_M_ex) */
 } oracle_params;
 
 typedef struct {
@@ -72,6 +74,17 @@ void oracle_apply_MT(const oracle_lattice *lat, double h, const double *L,
 void oracle_apply_MTM(const oracle_lattice *lat, double h, const double *L,
                       const double *x, double *y);
 
+/* Exact-block form of M (Eq. (7) with B = e^{-dtau K} e^{-dtau V}, the hopping
+ * factor expanded to order 1 or 2 in dtau K; order 0 is the R1 form above):
+ * (M x)(n,tau) = x(n,tau) + [E (L x)](n,tau-1), E = 1 + h H (+ h^2 H^2 / 2),
+ * H the sum over the 2d spatial neighbours; M^T and M^T M likewise. */
+void oracle_apply_M_ex(const oracle_lattice *lat, double h, const double *L, int order,
+                       const double *x, double *y);
+void oracle_apply_MT_ex(const oracle_lattice *lat, double h, const double *L, int order,
+                        const double *x, double *y);
+void oracle_apply_MTM_ex(const oracle_lattice *lat, double h, const double *L, int order,
+                         const double *x, double *y);
+
 /* Plain CG for Q x = b, x0 = 0 (Sec. 4.1).  Returns 0 or -4 (no convergence). */
 int oracle_cg(const oracle_lattice *lat, double h, const double *L, const double *b,
               double *x, double tol, int maxit, int *iterations, double *true_relres);
@@ -79,6 +92,9 @@ int oracle_cg(const oracle_lattice *lat, double h, const double *L, const double
  * if that already meets tol; b = 0 gives x = 0). */
 int oracle_cg_guess(const oracle_lattice *lat, double h, const double *L, const double *b,
                     double *x, double tol, int maxit, int *iterations, double *true_relres);
+/* CG for the M of the given order, from zero or (guess != 0) from x. */
+int oracle_cg_ex(const oracle_lattice *lat, double h, const double *L, int order, const double *b,
+                 double *x, int guess, double tol, int maxit, int *iterations, double *true_relres);
 
 /* Chebyshev polynomial preconditioner of Sec. 4.2, Eqs. (13)-(17).
  * Roots z_k = m (1 - cos(2 pi k/(2n+1))) - i sqrt(eps) sin(2 pi k/(2n+1)),

@@ -626,3 +626,97 @@ def test_pcg_matches_dense_lu(orc, d, nx, ntau):
     assert np.linalg.norm(x - x_lu) <= 2 * np.linalg.cond(Q) * 1e-10 * np.linalg.norm(x_lu)
     x0, st0, it0, _ = orc.cg(lat, H, L, b)
     assert it < it0   # each PCG step applies Q 2n+1 times: far fewer steps
+
+
+# --- Exact-block form of M (Eq. (7) with B = e^{-dtau K} e^{-dtau V}) ---------
+
+
+def _free_block_eigenvalues(d, nx, ntau, h, order):
+    """A = 0: plane waves with lattice momenta k_j = 2 pi m_j / N_x and
+    antiperiodic frequencies w = pi (2m + 1) / N_tau are eigenvectors, with
+    lambda = 1 - B_k e^{-i w}, B_k = 1 + h e_k (+ (h e_k)^2 / 2), e_k = sum_j
+    2 cos k_j the eigenvalue of the neighbour sum."""
+    ks = np.array(np.meshgrid(*[2 * np.pi * np.arange(nx) / nx] * d, indexing="ij")).reshape(d, -1)
+    ek = 2 * np.cos(ks).sum(axis=0)
+    B = 1 + h * ek + (0.5 * (h * ek) ** 2 if order == 2 else 0.0)
+    w = np.pi * (2 * np.arange(ntau) + 1) / ntau
+    return (1 - B[:, None] * np.exp(-1j * w[None, :])).ravel(), B
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("d,nx,ntau", [(1, 6, 8), (3, 3, 4)])
+def test_exact_block_free_field_spectrum_and_determinant(orc, order, d, nx, ntau):
+    """Free field: the singular values of M are |lambda| (M is normal), and
+    det M = prod_k (1 + B_k^{N_tau}) (the block-cyclic determinant of Eq. (7)
+    with the antiperiodic corner)."""
+    lat = orc.lattice(d, nx, ntau)
+    n = orc.nsites(lat)
+    h = 0.3
+    L = orc.links(lat, 0.0, np.zeros(n))
+    M = orc.dense(lat, h, L, "M", order=order)
+    lam, B = _free_block_eigenvalues(d, nx, ntau, h, order)
+    sv = np.sort(np.linalg.svd(M, compute_uv=False))
+    assert np.allclose(sv, np.sort(np.abs(lam)), rtol=1e-12, atol=1e-12)
+    sign, logdet = np.linalg.slogdet(M)
+    ref = 1 + B ** ntau
+    assert np.isclose(logdet, np.sum(np.log(np.abs(ref))), rtol=1e-12)
+    assert sign == np.prod(np.sign(ref))
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_exact_block_structure(orc, order):
+    """M^T is the transpose of M; A = 0 and h -> 0 recover the R1 form with
+    h = 0; a row of M couples its site, the same site one slice earlier and,
+    at order 1, its 2d spatial neighbours there (order 2: distance 2 too)."""
+    lat = orc.lattice(1, 7, 5)
+    n = orc.nsites(lat)
+    rng = np.random.default_rng(4)
+    L = orc.links(lat, 0.5, rng.uniform(-np.pi, np.pi, n))
+    M = orc.dense(lat, 0.2, L, "M", order=order)
+    MT = orc.dense(lat, 0.2, L, "MT", order=order)
+    # entries agree to rounding (order 2 sums the same products in another order)
+    assert np.allclose(MT, M.T, rtol=1e-15, atol=1e-17)
+    assert np.allclose(orc.dense(lat, 0.0, L, "M", order=order), orc.dense(lat, 0.0, L, "M"), atol=0)
+    row = 7 * 2 + 3                 # x = 3, tau = 2
+    cols = set(np.nonzero(M[row])[0])
+    expect = {row, 7 * 1 + 3, 7 * 1 + 2, 7 * 1 + 4}
+    if order == 2:
+        expect |= {7 * 1 + 1, 7 * 1 + 5}
+    assert cols == expect
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("d,nx,ntau", [(1, 4, 6), (3, 2, 3)])
+def test_exact_block_force_and_cg(orc, order, d, nx, ntau):
+    """Force against central differences of the dense-LU action of the same M,
+    CG against dense LU, and the heatbath identity S = |xi|^2 / 2."""
+    lat = orc.lattice(d, nx, ntau)
+    n = orc.nsites(lat)
+    prm = orc.params(cg_tol=1e-13, seed=78, link_order=order)
+    rng = np.random.default_rng(9)
+    sigma = rng.uniform(-np.pi, np.pi, n)
+    chi = rng.standard_normal((prm.n_pf, n))
+    h = prm.t * prm.dtau
+
+    def dense_action(s):
+        M = orc.dense(lat, h, orc.links(lat, prm.A, s), "M", order=order)
+        Q = M.T @ M
+        return 0.5 * sum(c @ np.linalg.solve(Q, c) for c in chi)
+
+    F, it, rr, st = orc.force(lat, prm, sigma, chi)
+    assert st == 0
+    eps = 1e-5
+    for i in rng.choice(n, size=min(n, 8), replace=False):
+        sp, sm = sigma.copy(), sigma.copy()
+        sp[i] += eps
+        sm[i] -= eps
+        fd = (dense_action(sp) - dense_action(sm)) / (2 * eps)
+        assert abs(F[i] - fd) <= 1e-6 * max(1.0, abs(fd))
+    L = orc.links(lat, prm.A, sigma)
+    Q = orc.dense(lat, h, L, "MTM", order=order)
+    x, st, it, rr = orc.cg_ex(lat, h, L, order, chi[0])
+    assert st == 0 and np.linalg.norm(x - np.linalg.solve(Q, chi[0])) <= 1e-6 * np.linalg.norm(x)
+    xi_chi = orc.heatbath(lat, prm, sigma, traj=3)
+    S, *_ = orc.action(lat, prm, sigma, xi_chi)
+    Minv_chi = [np.linalg.solve(orc.dense(lat, h, L, "MT", order=order), c) for c in xi_chi]
+    assert abs(S - 0.5 * sum(v @ v for v in Minv_chi)) <= 1e-9 * S
