@@ -106,6 +106,15 @@ typedef struct {
                               previous force's solution; 2 the linear
                               extrapolation of the last two.  1 and 2 make the
                               MD reversible only to the CG tolerance. */
+    int link_order;        /* form of M.  0: reading R1, diagonal blocks 1 - h H
+                              (H: sum over the 2d spatial neighbours) and links
+                              L = -(1 + A sin sigma).  1, 2: the exact-block form
+                              of Eq. (7), B = e^{-dtau K} e^{-dtau V} with
+                              e^{-dtau K} = e^{h H} expanded to that order:
+                              (M x)(n,tau) = x(n,tau) + [E (L x)](n,tau-1),
+                              E = 1 + h H (+ h^2 H^2 / 2).  Contexts only (not
+                              batch requests or hh_solve_noalloc); no Chebyshev
+                              preconditioner; scalar kernels. */
 } hh_params;
 
 #define HH_LEAPFROG 0
@@ -130,7 +139,8 @@ typedef struct {
 
 /* Fill p with the defaults t = 1, dtau = 0.05, A = 0.5, FP64, cg_tol = 1e-10,
  * cg_maxit = 1000000, reliable_delta = 0.1, seed = 0, n_pf = 2, chain_id = 0,
- * cheb_degree = 0 (plain CG), cheb_eps = 1e-3, integrator = HH_LEAPFROG, chrono = 0. */
+ * cheb_degree = 0 (plain CG), cheb_eps = 1e-3, integrator = HH_LEAPFROG, chrono = 0,
+ * link_order = 0. */
 void hh_default_params(hh_params *p);
 
 /* Create a context for one lattice and one Markov chain.  Allocates sigma,

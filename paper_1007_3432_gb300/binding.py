@@ -37,7 +37,7 @@ class hh_params(ctypes.Structure):
                 ("reliable_delta", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("n_pf", ctypes.c_int), ("chain_id", ctypes.c_uint64),
                 ("cheb_degree", ctypes.c_int), ("cheb_eps", ctypes.c_double), ("integrator", ctypes.c_int),
-                ("chrono", ctypes.c_int)]
+                ("chrono", ctypes.c_int), ("link_order", ctypes.c_int)]
 
 
 class hh_solve_info(ctypes.Structure):
@@ -192,7 +192,7 @@ class Context:
 
     def __init__(self, d, nx, ntau, t=1.0, dtau=0.05, A=0.5, precision=HH_FP64, cg_tol=1e-10,
                  cg_maxit=1000000, reliable_delta=0.1, seed=0, n_pf=2, chain_id=0, stream=None,
-                 cheb_degree=0, cheb_eps=1e-3, integrator="leapfrog", chrono=0):
+                 cheb_degree=0, cheb_eps=1e-3, integrator="leapfrog", chrono=0, link_order=0):
         L = load()
         self._lib = L
         self.lat = hh_lattice(d, nx, ntau)
@@ -205,6 +205,7 @@ class Context:
         p.cheb_degree, p.cheb_eps = cheb_degree, cheb_eps
         p.integrator = INTEGRATORS.get(integrator, integrator)
         p.chrono = chrono
+        p.link_order = link_order
         self.params = p
         self.stream = stream
         h = ctypes.c_void_p()
@@ -313,7 +314,7 @@ def solve_noalloc(d, nx, ntau, sigma, b, x, t=1.0, dtau=0.05, A=0.5, cg_tol=1e-1
 
 def make_params(t=1.0, dtau=0.05, A=0.5, precision=HH_FP64, cg_tol=1e-10, cg_maxit=1000000,
                 reliable_delta=0.1, seed=0, n_pf=2, chain_id=0, cheb_degree=0, cheb_eps=1e-3,
-                integrator="leapfrog", chrono=0):
+                integrator="leapfrog", chrono=0, link_order=0):
     L = load()
     p = hh_params()
     L.hh_default_params(ctypes.byref(p))
@@ -324,6 +325,7 @@ def make_params(t=1.0, dtau=0.05, A=0.5, precision=HH_FP64, cg_tol=1e-10, cg_max
     p.cheb_degree, p.cheb_eps = cheb_degree, cheb_eps
     p.integrator = INTEGRATORS.get(integrator, integrator)
     p.chrono = chrono
+    p.link_order = link_order
     return p
 
 

@@ -277,6 +277,7 @@ int validate(const hh_request &r)
     if (r.kind == HH_REQ_TRAJECTORY && r.n_md < 1) return HH_EINVAL;
     if (r.prm.integrator != HH_LEAPFROG && r.prm.integrator != HH_OMELYAN) return HH_EINVAL;
     if (r.prm.chrono < 0 || r.prm.chrono > 2) return HH_EINVAL;
+    if (r.prm.link_order != 0) return HH_EINVAL;   // the exact-block form runs in contexts only
     // Chebyshev-preconditioned CG (Sec. 4.2) is FP64 only, as in the context solver.
     if (r.prm.cheb_degree < 0 || r.prm.cheb_degree > CHEB_MAX_DEGREE) return HH_EINVAL;
     if (r.prm.cheb_degree > 0 && (r.prm.precision != HH_FP64 || !(r.prm.cheb_eps > 0.0 && r.prm.cheb_eps < 1.0)))

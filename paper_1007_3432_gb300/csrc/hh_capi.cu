@@ -248,6 +248,7 @@ int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
         Y.stall_window = ENGINE_STALL_WINDOW;
         Y.cheb_n = c->prm.cheb_degree;
         Y.cheb = c->d_cheb;
+        Y.link_order = c->prm.link_order;
         Y.z = c->z ? c->z + off : nullptr;
         Y.u = c->u ? c->u + off : nullptr;
     }
@@ -279,6 +280,22 @@ int set_guess(hh_ctx *c, int x0)
     // Pageable source: the copy has consumed it on return.
     HH_TRY(cudaMemcpyAsync(c->d_sys, P.sys, sizeof(EngSystem) * P.nsys, cudaMemcpyHostToDevice, c->stream));
     P.x0 = x0;
+    return HH_OK;
+}
+
+// The force from the solutions in xsol (n_rhs right-hand sides): pi -= eps F
+// (pi may be NULL) and F_out (may be NULL); returns the launches added.
+int ctx_force(hh_ctx *c, int n_rhs, double *pi, double eps, double *F_out, int *launches)
+{
+    const double h = c->prm.t * c->prm.dtau, A = c->prm.A;
+    if (c->prm.link_order == 0) {
+        HH_TRY(launch_force(c->geo, h, A, c->sigma, c->L64, c->xsol, n_rhs, pi, eps, F_out, c->stream));
+        *launches = 1;
+    } else {
+        HH_TRY(launch_force_ex(c->geo, h, A, c->prm.link_order, c->sigma, c->L64, c->xsol, n_rhs, c->tmp, c->F,
+                               pi, eps, F_out, c->stream));
+        *launches = 2 * n_rhs;
+    }
     return HH_OK;
 }
 
@@ -377,6 +394,7 @@ void hh_default_params(hh_params *p)
     p->cheb_eps = 1e-3;
     p->integrator = HH_LEAPFROG;
     p->chrono = 0;
+    p->link_order = 0;
 }
 
 const char *hh_strerror(int code)
@@ -408,6 +426,9 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
         return HH_EINVAL;
     if (p->integrator != HH_LEAPFROG && p->integrator != HH_OMELYAN) return HH_EINVAL;
     if (p->chrono < 0 || p->chrono > 2) return HH_EINVAL;
+    if (p->link_order < 0 || p->link_order > 2) return HH_EINVAL;
+    // The Chebyshev normalisation bound is that of the R1 form.
+    if (p->link_order != 0 && p->cheb_degree != 0) return HH_EINVAL;
     long long V = lat->d == 1 ? lat->nx : (long long)lat->nx * lat->nx * lat->nx;
     long long N = V * lat->ntau;
     if (N >= (1LL << 31) - 1024) return HH_EINVAL;
@@ -422,8 +443,9 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
     c->N = (int)N;
     c->cap_rhs = p->n_pf > 4 ? p->n_pf : 4;
     c->timeout_ns = 5LL * 1000 * 1000 * 1000;
-    c->kind = lat->d == 1 ? ENGINE_D1 : ENGINE_D3;
-    c->two_slot = engine_two_slot(c->kind);
+    // The exact-block form of M runs in its own kernel.
+    c->kind = p->link_order != 0 ? ENGINE_EXBLOCK : (lat->d == 1 ? ENGINE_D1 : ENGINE_D3);
+    c->two_slot = p->link_order == 0 ? engine_two_slot(c->kind) : 0;
     int max_grid = engine_default_grid(c->kind);
     if (max_grid <= 0) {
         delete c;
@@ -560,9 +582,36 @@ int hh_apply(hh_ctx *c, int op, const void *x, void *y, int dtype)
     if (!c || !x || !y || x == y) return HH_EINVAL;
     if (op != HH_OP_M && op != HH_OP_MT && op != HH_OP_MTM) return HH_EINVAL;
     const double h = c->prm.t * c->prm.dtau;
+    const int order = c->prm.link_order;
+    int launches = 0;
+    if (order != 0) {
+        // Exact-block form: the scalar kernels.
+        if (dtype == HH_DTYPE_F64) {
+            const double *xd = (const double *)x;
+            double *yd = (double *)y;
+            if (op == HH_OP_MTM) {
+                HH_TRY(launch_apply_f64(c->geo, 0, h, c->L64, xd, c->tmp, c->stream, order));
+                HH_TRY(launch_apply_f64(c->geo, 1, h, c->L64, c->tmp, yd, c->stream, order));
+            } else {
+                HH_TRY(launch_apply_f64(c->geo, op, h, c->L64, xd, yd, c->stream, order));
+            }
+        } else if (dtype == HH_DTYPE_F32) {
+            const float *xf = (const float *)x;
+            float *yf = (float *)y;
+            if (op == HH_OP_MTM) {
+                HH_TRY(launch_apply_f32(c->geo, 0, (float)h, c->L32, xf, c->tmp32a, c->stream, order));
+                HH_TRY(launch_apply_f32(c->geo, 1, (float)h, c->L32, c->tmp32a, yf, c->stream, order));
+            } else {
+                HH_TRY(launch_apply_f32(c->geo, op, (float)h, c->L32, xf, yf, c->stream, order));
+            }
+        } else {
+            return HH_EINVAL;
+        }
+        c->n_launch += op == HH_OP_MTM ? 2 : 1;
+        return HH_OK;
+    }
     // Vector sweeps need 16-byte aligned x and y; the scalar kernels take any.
     const bool vec = aligned16(x) && aligned16(y);
-    int launches = 0;
     if (dtype == HH_DTYPE_F64) {
         const double *xd = (const double *)x;
         double *yd = (double *)y;
@@ -659,9 +708,10 @@ int hh_force(hh_ctx *c, const double *chi, int n_rhs, double *F, hh_solve_info *
     c->n_launch += 1;
     rc = run_engine(c);
     if (rc) return rc;
-    HH_TRY(launch_force(c->geo, c->prm.t * c->prm.dtau, c->prm.A, c->sigma, c->L64, c->xsol, n_rhs,
-                        nullptr, 0.0, F, c->stream));
-    c->n_launch += 1;
+    int nl = 0;
+    rc = ctx_force(c, n_rhs, nullptr, 0.0, F, &nl);
+    if (rc) return rc;
+    c->n_launch += nl;
     if (!info) return HH_OK;
     EngStats s;
     rc = read_stats(c, &s);
@@ -730,7 +780,10 @@ int leapfrog_enqueue(hh_ctx *c, double *pi, const double *chi, int n_rhs, int n_
         if (rc) return rc;
         if (j == 0 && h0)
             HH_TRY(launch_energy(c->N, pi, chi, c->xsol, n_rhs, c->d_energy_part, h0, c->stream));
-        HH_TRY(launch_force(c->geo, h, A, c->sigma, c->L64, c->xsol, n_rhs, pi, kick, nullptr, c->stream));
+        int nl = 0;
+        rc = ctx_force(c, n_rhs, pi, kick, nullptr, &nl);
+        if (rc) return rc;
+        c->n_launch += nl - 1;
         if (j + 1 < forces)
             HH_TRY(launch_sigma_step(c->geo, A, drift, c->sigma, pi, c->L64, c->L32, c->stream));
     }
@@ -775,7 +828,8 @@ int hh_trajectory(hh_ctx *c, int n_md, double dt, uint64_t traj, hh_traj_info *i
     HH_TRY(launch_gaussian(c->pi, c->N, seed, 1, 0, traj, chain, c->stream));
     for (int a = 0; a < npf; ++a) {
         HH_TRY(launch_gaussian(c->tmp, c->N, seed, 2, a, traj, chain, c->stream));
-        HH_TRY(launch_apply_f64(c->geo, 1, h, c->L64, c->tmp, c->chi + (size_t)a * c->N, c->stream));
+        HH_TRY(launch_apply_f64(c->geo, 1, h, c->L64, c->tmp, c->chi + (size_t)a * c->N, c->stream,
+                                c->prm.link_order));
     }
     HH_TRY(cudaMemcpyAsync(c->sigma0, c->sigma, (size_t)c->N * sizeof(double),
                            cudaMemcpyDeviceToDevice, c->stream));

@@ -121,6 +121,58 @@ __device__ __forceinline__ T stencil_MT(const Geo &g, T h, const T *__restrict__
     return fma(__ldg(L + i), v[nb.next], acc);
 }
 
+// Exact-block form of M (the blocks of Eq. (7) with B = e^{-dtau K} e^{-dtau V},
+// e^{-dtau K} = e^{h H} expanded to order 1 or 2): E = 1 + h H (+ h^2 H^2 / 2)
+// applied at site p of one time slice to w = L v (WL) or to v, with H the
+// sum over the 2d spatial neighbours, summed in the neighbour order of
+// hop_sum (the H^2 term as a sum over neighbours of neighbour sums).
+template <typename T, bool WL>
+__device__ __forceinline__ T e_factor(const Geo &g, T h, const T *__restrict__ L, const T *v, int p,
+                                      int order)
+{
+    Nbr nb;
+    neighbours(g, p, nb);
+    const int nn = 2 * g.d;
+    T s1 = T(0), s2 = T(0);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        if (a >= nn) break;
+        const int q = nb.sp[a];
+        s1 += WL ? __ldg(L + q) * v[q] : v[q];
+        if (order == 2) {
+            Nbr nq;
+            neighbours(g, q, nq);
+            T t = T(0);
+#pragma unroll
+            for (int b = 0; b < 6; ++b) {
+                if (b >= nn) break;
+                const int r = nq.sp[b];
+                t += WL ? __ldg(L + r) * v[r] : v[r];
+            }
+            s2 += t;
+        }
+    }
+    T e = fma(h, s1, WL ? __ldg(L + p) * v[p] : v[p]);
+    if (order == 2) e = fma(T(0.5) * h * h, s2, e);
+    return e;
+}
+
+// Exact-block form: (M v)_i = v_i + [E (L v)](prev)
+template <typename T>
+__device__ __forceinline__ T stencil_M_ex(const Geo &g, T h, const T *__restrict__ L, const T *v, int i,
+                                          const Nbr &nb, int order)
+{
+    return v[i] + e_factor<T, true>(g, h, L, v, nb.prev, order);
+}
+
+// Exact-block form: (M^T v)_i = v_i + L(i) [E v](next)
+template <typename T>
+__device__ __forceinline__ T stencil_MT_ex(const Geo &g, T h, const T *__restrict__ L, const T *v, int i,
+                                           const Nbr &nb, int order)
+{
+    return fma(__ldg(L + i), e_factor<T, false>(g, h, L, v, nb.next, order), v[i]);
+}
+
 // ---------------------------------------------------------------------------
 // Short vectors of W consecutive elements (W = 1, 2, 4), loaded and stored
 // with 8- or 16-byte accesses.  The address must be aligned to the access.

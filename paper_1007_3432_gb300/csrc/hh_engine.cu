@@ -174,6 +174,58 @@ __device__ double gloop_cheb_z(const Geo g, const double h, const double *__rest
     return acc;
 }
 
+// Exact-block form of M (link_order 1, 2): scalar site loops with the stencils
+// of hh_device.cuh.  t = M p, acc += t^2.
+template <typename T>
+__device__ double gloop_M_ex(const Geo g, const T h, const T *__restrict__ L, const T *v, T *t, int order,
+                             int b, int e)
+{
+    T acc = T(0);
+    Nbr nb;
+    for (int i = b + ctid(); i < e; i += cnth()) {
+        neighbours(g, i, nb);
+        const T y = stencil_M_ex<T>(g, h, L, v, i, nb, order);
+        t[i] = y;
+        acc = fma(y, y, acc);
+    }
+    return (double)acc;
+}
+
+// q = M^T t, x += alpha p, r -= alpha q; acc += r^2.
+template <typename T>
+__device__ double gloop_update_ex(const Geo g, const T h, const T *__restrict__ L, const T *t, T *x,
+                                  const T *p, T *r, const T alpha, int order, int b, int e)
+{
+    T acc = T(0);
+    Nbr nb;
+    for (int i = b + ctid(); i < e; i += cnth()) {
+        neighbours(g, i, nb);
+        const T q = stencil_MT_ex<T>(g, h, L, t, i, nb, order);
+        x[i] = fma(alpha, p[i], x[i]);
+        const T rv = fma(-alpha, q, r[i]);
+        r[i] = rv;
+        acc = fma(rv, rv, acc);
+    }
+    return (double)acc;
+}
+
+// res = b - M^T t64 in FP64; r64 = res, r32 = (float)res (mixed); acc += res^2.
+__device__ double gloop_residual_ex(const Geo g, const double h, const double *__restrict__ L,
+                                    const double *t, const double *__restrict__ bvec, double *r, float *r32,
+                                    int order, int b, int e)
+{
+    double acc = 0.0;
+    Nbr nb;
+    for (int i = b + ctid(); i < e; i += cnth()) {
+        neighbours(g, i, nb);
+        const double res = __ldg(bvec + i) - stencil_MT_ex<double>(g, h, L, t, i, nb, order);
+        r[i] = res;
+        if (r32) r32[i] = (float)res;
+        acc = fma(res, res, acc);
+    }
+    return acc;
+}
+
 // Two-slot CG step: p_new = src + beta p_old on the tile's sites (stored), and
 // t = M p_new with p_new recomputed at the neighbour sites from src and p_old,
 // which are final there; acc += t^2.  The recomputed values are bitwise the
@@ -596,6 +648,35 @@ __device__ double slot3(const EngSystem &Y, const TileCtl &c, const EngTile &T)
     return 0.0;
 }
 
+// Slots 2 and 3 of a system with the exact-block form of M (three-slot
+// form; CG, RU and INIT modes).
+__device__ double slot2_ex(const EngSystem &Y, const TileCtl &c, const EngTile &T)
+{
+    if (c.mode == MODE_CG) {
+        if (c.prec == PREC_FP64)
+            return gloop_M_ex<double>(Y.g, Y.h, Y.L64, pbuf64(Y, c.pnew), Y.t, Y.link_order, T.begin, T.end);
+        return gloop_M_ex<float>(Y.g, (float)Y.h, Y.L32, pbuf32(Y, c.pnew), Y.t32, Y.link_order, T.begin, T.end);
+    }
+    if (c.mode == MODE_RU) gloop_M_ex<double>(Y.g, Y.h, Y.L64, Y.x, Y.t, Y.link_order, T.begin, T.end);
+    return 0.0;
+}
+
+__device__ double slot3_ex(const EngSystem &Y, const TileCtl &c, const EngTile &T)
+{
+    if (c.mode == MODE_CG) {
+        if (c.prec == PREC_FP64)
+            return gloop_update_ex<double>(Y.g, Y.h, Y.L64, Y.t, Y.x, pbuf64(Y, c.pnew), Y.r, c.alpha,
+                                           Y.link_order, T.begin, T.end);
+        return gloop_update_ex<float>(Y.g, (float)Y.h, Y.L32, Y.t32, Y.x32, pbuf32(Y, c.pnew), Y.r32,
+                                      (float)c.alpha, Y.link_order, T.begin, T.end);
+    }
+    if (c.mode == MODE_RU)
+        return gloop_residual_ex(Y.g, Y.h, Y.L64, Y.t, Y.b, Y.r, Y.precision == PREC_MIXED ? Y.r32 : nullptr,
+                                 Y.link_order, T.begin, T.end);
+    if (c.mode == MODE_INIT) return init_residual(Y, T);
+    return 0.0;
+}
+
 // Two-slot first slot: slot 1 folded into slot 2.  Returns this thread's
 // |t|^2 partial for a CG step (0 otherwise).
 template <int D, int W>
@@ -634,6 +715,16 @@ __device__ double slotA(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 template <int SLOT, int FD>
 __device__ double run_slot(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 {
+    if (FD == 4) {
+        // Exact-block form: scalar loops, three-slot form (ENGINE_EXBLOCK).
+        if (SLOT == 1) {
+            slot1<1, 1>(Y, c, T);
+            return 0.0;
+        }
+        if (SLOT == 2) return slot2_ex(Y, c, T);
+        if (SLOT == 3) return slot3_ex(Y, c, T);
+        return 0.0;
+    }
 #define HH_SLOT_CALL(D, W)                                   \
     if (SLOT == 1) {                                         \
         slot1<D, W>(Y, c, T);                                \
@@ -1046,15 +1137,16 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
 
 }  // namespace
 
-// The kernels: generic (any mix of dimensions) and the dimension-specialised
-// ones, each launched with one 512-thread block per SM (measured on GB300:
-// two blocks per SM, at 64 registers, was slower than one block with fewer
-// grid-barrier arrivals).
+// The kernels: generic (any mix of dimensions), the dimension-specialised
+// ones and the exact-block one, each launched with one 512-thread block per SM
+// (measured on GB300: two blocks per SM, at 64 registers, was slower than one
+// block with fewer arrivals per synchronisation).
 const void *kernel_of(int kind)
 {
     switch (kind) {
     case ENGINE_D1: return (const void *)engine_kernel<1, 1>;
     case ENGINE_D3: return (const void *)engine_kernel<3, 1>;
+    case ENGINE_EXBLOCK: return (const void *)engine_kernel<4, 1>;
     default: return (const void *)engine_kernel<0, 1>;
     }
 }

@@ -74,6 +74,8 @@ struct EngSystem {
     int stall_window;                 // mixed: forced RU after this many FP32 steps without one
     int cheb_n;                       // Chebyshev preconditioner degree n (0: plain CG; FP64 only)
     int x0_given;                     // 1: x holds an initial guess when the system starts (MODE_NEW)
+    int link_order;                   // form of M: 0 reading R1; 1, 2 exact-block (three-slot form,
+                                      // no preconditioner, scalar site loops)
     const double *cheb;               // coefficient table (see CHEB_MAX_DEGREE)
     double *z, *u;                    // FP64 preconditioner vectors (when cheb_n > 0)
     double *p2;                       // second FP64 p buffer (two-slot launches)
@@ -149,7 +151,10 @@ __host__ __device__ constexpr size_t engine_sig_count(int parts)
 // Engine kernels: ENGINE_GENERIC handles systems of both dimensions in one
 // launch; ENGINE_D1 / ENGINE_D3 require every system of the launch to have
 // that dimension and are compiled for it.
-enum EngKind : int { ENGINE_GENERIC = 0, ENGINE_D1 = 1, ENGINE_D3 = 3 };
+// ENGINE_EXBLOCK runs systems with the exact-block form of M (link_order 1,
+// 2) only, with scalar site loops, kept apart so that the other kernels do
+// not carry its code.
+enum EngKind : int { ENGINE_GENERIC = 0, ENGINE_D1 = 1, ENGINE_D3 = 3, ENGINE_EXBLOCK = 4 };
 
 // Host launcher: runs the engine with a cooperative launch of 'grid' blocks.
 // The barrier counter ctl->count must be zero when the launch starts.

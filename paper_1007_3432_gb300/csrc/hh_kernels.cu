@@ -49,12 +49,16 @@ __global__ void k_sigma_step(Geo g, double A, double dt, double *__restrict__ si
 
 template <typename T>
 __global__ void k_apply(Geo g, int op, T h, const T *__restrict__ L, const T *__restrict__ x,
-                        T *__restrict__ y)
+                        T *__restrict__ y, int order)
 {
     Nbr nb;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += gridDim.x * blockDim.x) {
         neighbours(g, i, nb);
-        y[i] = (op == 0) ? stencil_M<T>(g, h, L, x, i, nb) : stencil_MT<T>(g, h, L, x, i, nb);
+        if (order == 0)
+            y[i] = (op == 0) ? stencil_M<T>(g, h, L, x, i, nb) : stencil_MT<T>(g, h, L, x, i, nb);
+        else
+            y[i] = (op == 0) ? stencil_M_ex<T>(g, h, L, x, i, nb, order)
+                             : stencil_MT_ex<T>(g, h, L, x, i, nb, order);
     }
 }
 
@@ -114,6 +118,32 @@ __global__ void k_force(Geo g, double h, double A, const double *__restrict__ si
         }
         if (F_out) F_out[i] = F;
         if (pi) pi[i] = fma(-eps, F, pi[i]);
+    }
+}
+
+// Exact-block form: sigma(n,tau) enters through w = L x at (n,tau), which row
+// (., tau+1) sees through E, so y's factor is (E y)(n, tau+1) with y = M x_a
+// (ya, precomputed).  Accumulates over right-hand sides in Facc; the last one
+// writes F_out and updates pi.
+__global__ void k_force_ex(Geo g, double h, double A, int order, const double *__restrict__ sigma,
+                           const double *__restrict__ L64, const double *__restrict__ xa,
+                           const double *__restrict__ ya, double *__restrict__ Facc, int first, int last,
+                           double *__restrict__ pi, double eps, double *__restrict__ F_out)
+{
+    Nbr nb;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += gridDim.x * blockDim.x) {
+        neighbours(g, i, nb);
+        uint32_t tau = fd_div((uint32_t)i, g.f_V);
+        double s = ((int)tau == g.ntau - 1) ? 1.0 : -1.0;
+        double coef = s * A * cos(sigma[i]);
+        double e = e_factor<double, false>(g, h, L64, ya, nb.next, order);
+        double F = (first ? 0.0 : Facc[i]) - e * coef * xa[i];
+        if (last) {
+            if (F_out) F_out[i] = F;
+            if (pi) pi[i] = fma(-eps, F, pi[i]);
+        } else {
+            Facc[i] = F;
+        }
     }
 }
 
@@ -184,16 +214,16 @@ cudaError_t launch_sigma_step(const Geo &g, double A, double dt, double *sigma, 
 }
 
 cudaError_t launch_apply_f64(const Geo &g, int op, double h, const double *L, const double *x,
-                             double *y, cudaStream_t st)
+                             double *y, cudaStream_t st, int order)
 {
-    k_apply<double><<<grid_for(g.N), kBlock, 0, st>>>(g, op, h, L, x, y);
+    k_apply<double><<<grid_for(g.N), kBlock, 0, st>>>(g, op, h, L, x, y, order);
     return cudaGetLastError();
 }
 
 cudaError_t launch_apply_f32(const Geo &g, int op, float h, const float *L, const float *x, float *y,
-                             cudaStream_t st)
+                             cudaStream_t st, int order)
 {
-    k_apply<float><<<grid_for(g.N), kBlock, 0, st>>>(g, op, h, L, x, y);
+    k_apply<float><<<grid_for(g.N), kBlock, 0, st>>>(g, op, h, L, x, y, order);
     return cudaGetLastError();
 }
 
@@ -217,6 +247,22 @@ cudaError_t launch_force(const Geo &g, double h, double A, const double *sigma, 
 {
     k_force<<<grid_for(g.N), kBlock, 0, st>>>(g, h, A, sigma, L64, x, n_rhs, pi, eps, F_out);
     return cudaGetLastError();
+}
+
+cudaError_t launch_force_ex(const Geo &g, double h, double A, int order, const double *sigma,
+                            const double *L64, const double *x, int n_rhs, double *ytmp, double *Facc,
+                            double *pi, double eps, double *F_out, cudaStream_t st)
+{
+    for (int a = 0; a < n_rhs; ++a) {
+        const double *xa = x + (size_t)a * g.N;
+        cudaError_t e = launch_apply_f64(g, 0, h, L64, xa, ytmp, st, order);
+        if (e != cudaSuccess) return e;
+        k_force_ex<<<grid_for(g.N), kBlock, 0, st>>>(g, h, A, order, sigma, L64, xa, ytmp, Facc, a == 0,
+                                                      a == n_rhs - 1, pi, eps, F_out);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 int energy_blocks(int n)

@@ -27,11 +27,12 @@ cudaError_t launch_links(const Geo &g, double A, const double *sigma, double *L6
 cudaError_t launch_sigma_step(const Geo &g, double A, double dt, double *sigma, const double *pi,
                               double *L64, float *L32, cudaStream_t st);
 
-// y = M x or y = M^T x (op 0 / 1), FP64 or FP32.
+// y = M x or y = M^T x (op 0 / 1), FP64 or FP32; order 0 is the form of
+// reading R1, 1 and 2 the exact-block form (stencil_M_ex).
 cudaError_t launch_apply_f64(const Geo &g, int op, double h, const double *L, const double *x,
-                             double *y, cudaStream_t st);
+                             double *y, cudaStream_t st, int order = 0);
 cudaError_t launch_apply_f32(const Geo &g, int op, float h, const float *L, const float *x, float *y,
-                             cudaStream_t st);
+                             cudaStream_t st, int order = 0);
 
 // out[i] = N(0,1) Philox/Box-Muller draw for element i (tag, a, traj, chain).
 cudaError_t launch_gaussian(double *out, int n, uint64_t seed, int tag, int a, uint64_t traj,
@@ -63,6 +64,13 @@ cudaError_t launch_restore(const Geo &g, double A, const HmcScalars *sc, double 
 // Chronological initial guess by linear extrapolation: x <- 2 x - xp and
 // xp <- the old x, over n elements.
 cudaError_t launch_extrapolate(double *x, double *xp, long long n, cudaStream_t st);
+
+// The force of the exact-block form of M (order 1 or 2): per right-hand side
+// y = M x_a into ytmp, then F accumulated in Facc (N doubles); pi -= eps F and
+// F_out (may be NULL) as launch_force.  2 n_rhs launches.
+cudaError_t launch_force_ex(const Geo &g, double h, double A, int order, const double *sigma,
+                            const double *L64, const double *x, int n_rhs, double *ytmp, double *Facc,
+                            double *pi, double eps, double *F_out, cudaStream_t st);
 
 // Molecular-dynamics schedule of one trajectory as a sequence of forces:
 // after force j (j = 0 .. forces - 1, each computed from a fresh solve at the

@@ -142,6 +142,7 @@ extern "C" int hh_solve_noalloc(const hh_lattice *lat, const hh_params *p, const
     if (lat->d != 1 && lat->d != 3) return HH_EINVAL;
     if (lat->nx < 2 || lat->ntau < 2) return HH_EINVAL;
     if (p->precision != HH_FP64 || !(p->cg_tol > 0.0) || p->cg_maxit < 1) return HH_EINVAL;
+    if (p->link_order != 0 || p->cheb_degree != 0) return HH_EINVAL;
     long long V = lat->d == 1 ? lat->nx : (long long)lat->nx * lat->nx * lat->nx;
     long long N = V * lat->ntau;
     if (N > kMaxSites) return HH_ESIZE;
