@@ -226,8 +226,9 @@ def run_reference(args, wl, world, rank):
 def config_of(args, wl):
     return {"workload": wl.name, "d": wl.d, "nx": wl.nx, "ntau": wl.ntau, "sites": wl.nsites,
             "t": workloads.T_HOP, "dtau": workloads.DTAU, "A": workloads.A_HS, "seed": wl.seed,
-            "n_md": args.n_md, "dt": 1.0 / args.n_md, "n_pf": 2, "cg_tol": 1e-10,
+            "n_md": args.n_md, "dt": args.dt, "n_pf": 2, "cg_tol": 1e-10,
             "precision": args.precision, "step": "one HMC trajectory", "integrator": args.integrator,
+            "cg": ("Chebyshev-preconditioned, n=%d eps=%g" % (args.cheb, args.cheb_eps)) if args.cheb else "plain",
             "l2": "flushed between steps (512 MiB write, then 512 MiB read)", "parallelism": "replicas%d" % args.gpus}
 
 
@@ -468,7 +469,7 @@ def run_serve(args, world, rank, local, dev, stream):
                                      traj_index=r.rid, **prm)
             else:
                 req = B.make_request(HH_REQ_TRAJECTORY, r.d, r.nx, r.ntau, sigma=sigma, seed=r.seed, n_pf=2,
-                                     n_md=args.serve_n_md, dt=1.0 / args.serve_n_md, traj_index=r.rid, **prm)
+                                     n_md=args.serve_n_md, dt=args.serve_dt, traj_index=r.rid, **prm)
             keep.append(sigma)
             batch.submit(req)
             got += batch.poll()
@@ -498,7 +499,8 @@ def run_serve(args, world, rank, local, dev, stream):
             "data": "synthetic",
             "config": {"workload": "serve_poisson", "seed": workloads.SERVE_SEED, "requests_per_rate": args.requests,
                        "d1": {"nx": [64, 2048], "ntau": [64, 512]}, "d3": {"nx": [8, 24], "ntau": [40, 256]},
-                       "trajectory_n_md": args.serve_n_md, "hbm_budget_gb": args.budget_gb,
+                       "trajectory_n_md": args.serve_n_md, "trajectory_dt": args.serve_dt,
+                       "hbm_budget_gb": args.budget_gb,
                        "precision": "mixed; FP64 + Chebyshev n=8 eps=1e-4 for d=1 with N_tau >= 256",
                        "mode": "serve", "parallelism": "replicas%d" % world},
             "per_rate": per_rate, "e2e": None, "gpu_launches": None}
@@ -519,17 +521,21 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--mode", default="trajectory", choices=["trajectory", "solve", "apply", "batch", "serve"])
     ap.add_argument("--cg-maxit", type=int, default=1000000)
-    ap.add_argument("--cheb", type=int, default=0, help="solve mode: Chebyshev preconditioner degree n (FP64)")
+    ap.add_argument("--cheb", type=int, default=0, help="Chebyshev preconditioner degree n (FP64; solve and trajectory)")
     ap.add_argument("--integrator", default="leapfrog", choices=["leapfrog", "omelyan"])
     ap.add_argument("--cheb-eps", type=float, default=1e-4)
     ap.add_argument("--rates", default="10,100,1000")
     ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--serve-n-md", type=int, default=4)
+    ap.add_argument("--serve-dt", type=float, default=0.002)
+    ap.add_argument("--dt", type=float, default=None, help="MD step (default: the workload's)")
     ap.add_argument("--budget-gb", type=float, default=150.0)
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.n_md is None:
         args.n_md = wl.n_md
+    if args.dt is None:
+        args.dt = wl.dt if wl.dt > 0 else 1.0 / args.n_md
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, wl, world, rank)
@@ -554,9 +560,10 @@ def main():
     n = wl.nsites
     sigma_h = workloads.sigma_field(n, seed=wl.seed, chain=rank)
     ctx = Context(wl.d, wl.nx, wl.ntau, seed=wl.seed, n_pf=2, chain_id=rank, precision=args.precision,
-                  cg_maxit=args.cg_maxit, stream=stream, integrator=args.integrator)
+                  cg_maxit=args.cg_maxit, stream=stream, integrator=args.integrator,
+                  cheb_degree=args.cheb, cheb_eps=args.cheb_eps)
     flush = L2Flush(dev)
-    dt = 1.0 / args.n_md
+    dt = args.dt
 
     def step(traj, timed):
         flush(float(traj))
@@ -568,7 +575,7 @@ def main():
         e0.record(stream)
         ctx.set_field(sigma_h)              # host -> device (the step's input)
         e1.record(stream)
-        info = ctx.trajectory(args.n_md, dt, traj, info=False)
+        info = ctx.trajectory(args.n_md, dt, traj)
         e2.record(stream)
         ctx.get_field(sigma_h)              # device -> host (the step's output)
         w1 = time.perf_counter()
@@ -582,17 +589,21 @@ def main():
     ctx.counters_reset(profile_engine=True)
     clocks = ClockSampler(local)
     clocks.start()
-    dev_ms, wall_ms = [], []
+    dev_ms, wall_ms, infos = [], [], []
     for k in range(args.steps):
-        a, b, _ = step(args.warmup + k, True)
+        a, b, inf = step(args.warmup + k, True)
         dev_ms.append(a)
         wall_ms.append(b)
+        infos.append(inf)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     barrier(world)
     cnt = ctx.counters()
 
-    applies = cnt["cg_steps"] + cnt["ru_steps"]
+    # Every CG step and true-residual check applies Q once per right-hand
+    # side; with the Chebyshev preconditioner each is followed by 2n more.
+    q_per_step = 2 * args.cheb + 1
+    applies = (cnt["cg_steps"] + cnt["ru_steps"]) * q_per_step
     t_dev = max_over_ranks(world, sum(dev_ms) / 1000.0)
     t_wall = max_over_ranks(world, sum(wall_ms) / 1000.0)
     tot_applies = sum_over_ranks(world, float(applies))
@@ -608,6 +619,9 @@ def main():
     per_launch = eng_s / max(1, cnt["engine_launches"])
     if args.precision == "fp64":
         flops = n * (cnt["cg_steps"] * f_cg + cnt["ru_steps"] * f_ru)
+        # preconditioner sub-steps: one Q apply with its vector update each,
+        # counted at the flops of a CG step
+        flops += n * (cnt["cg_steps"] + cnt["ru_steps"]) * (q_per_step - 1) * f_cg
         achieved = flops / eng_s / 1e12 if eng_s > 0 else 0.0
         peak = fp64_peak_tflops()
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -631,6 +645,10 @@ def main():
         "data": "synthetic", "config": config_of(args, wl),
         "solves_per_s": tot_solves / t_dev, "trajectories_per_s": world * args.steps / t_dev,
         "cg_steps_per_solve": cnt["cg_steps"] / max(1, cnt["solves"]),
+        "q_applies_per_solve": applies / max(1, cnt["solves"]),
+        "acceptance": float(np.mean([i["accepted"] for i in infos])),
+        "dH": [i["dH"] for i in infos],
+        "max_true_relres": max(i["max_true_relres"] for i in infos),
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
         "gpu_launches": int(cnt["kernel_launches"]),
         "clocks": clk, "roofline": roof,

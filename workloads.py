@@ -28,6 +28,7 @@ class Workload:
     ntau: int
     seed: int
     n_md: int = 10
+    dt: float = 0.0     # MD step; 0: 1 / n_md (trajectory length 1)
     notes: str = ""
 
     @property
@@ -39,8 +40,10 @@ class Workload:
 # trajectories in seconds; C1 and C2 are the at-scale d=1 and d=3 lattices.
 C0 = Workload("d1_nx32_nt64", 1, 32, 64, 1007, n_md=10,
               notes="d=1, Nx=32, Ntau=64: one 10-step trajectory, FP64")
-C1 = Workload("d1_nx1024_nt512", 1, 1024, 512, 1008, n_md=20,
-              notes="d=1, Nx=1024, Ntau=512: HMC trajectories of 20 leapfrog steps, FP64")
+C1 = Workload("d1_nx1024_nt512", 1, 1024, 512, 1008, n_md=20, dt=0.002,
+              notes="d=1, Nx=1024, Ntau=512: HMC trajectories of 20 leapfrog steps, FP64; from the "
+                    "uniform (hot) field the forces reach 1.5e6 and dH is 5e20 at dt = 0.05, 9e7 at "
+                    "0.01 and 1.2 at 0.002 (measured), hence dt = 0.002")
 C2 = Workload("d3_nx32_nt128", 3, 32, 128, 1009, n_md=10,
               notes="d=3, Nx=32^3, Ntau=128: FP64 CG vs FP32-inner CG")
 BATCH_SEED = 1010
