@@ -68,6 +68,25 @@ def bytes_per_site(kind, precision):
     return 8 * 8 + (12 if precision == "mixed" else 0)
 
 
+# DRAM bytes per engine iteration (two right-hand sides) of the engine kernel
+# as it stands, from one ncu --set full capture each (dram__bytes_read.sum +
+# dram__bytes_write.sum over a 202-iteration launch; profiles/engine_kernel_*).
+# A launch's traffic scales with its iterations.
+ENGINE_DRAM_PER_ITER = {("d1_nx1024_nt512", "fp64"): (12.720384e6 + 95.198208e6) / 202,
+                        ("d3_nx32_nt128", "mixed"): (33.617242e9 + 27.067933e9) / 202}
+
+
+def engine_traffic(wl, precision, cheb, cnt):
+    """Estimated DRAM bytes per engine launch, or None without a capture."""
+    per_iter = ENGINE_DRAM_PER_ITER.get((wl.name, precision))
+    if per_iter is None or cheb or cnt["engine_launches"] == 0:
+        return None
+    # both right-hand sides advance together: one INIT iteration, then the CG
+    # steps and true-residual checks of one system
+    iters = (cnt["cg_steps"] + cnt["ru_steps"]) / 2.0 / cnt["engine_launches"] + 1.0
+    return per_iter * iters
+
+
 def fp64_peak_tflops():
     """FP64 peak of GB300 from unit counts and clocks: 152 SMs x 2 DFMA per
     clock per SM x 2 flops x 2.07 GHz (maximum SM clock) = 1.26 TFLOP/s, the
@@ -316,12 +335,14 @@ def run_part(args, wl, world, rank, local, dev, stream):
             flops += n * (cnt["cg_steps"] + cnt["ru_steps"]) * (q_per_step - 1) * flops_per_site(wl.d, "cg", "fp64")
             ach = flops / eng_s / 1e12
             roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak_tflops(), "unit": "TFLOP/s",
-                    "frac": ach / fp64_peak_tflops(), "traffic": None, "kernel": "engine_kernel (FP64 CG)"}
+                    "frac": ach / fp64_peak_tflops(), "traffic": engine_traffic(wl, args.precision, args.cheb, cnt),
+                    "kernel": "engine_kernel (FP64 CG)"}
         else:
             byts = n * (cnt["cg_steps"] * bytes_per_site("cg", "mixed") + cnt["ru_steps"] * bytes_per_site("ru", "mixed"))
             ach = byts / eng_s / 1e9
             roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "engine_kernel (FP32-inner CG)"}
+                    "frac": ach / peaks["hbm_gbs"], "traffic": engine_traffic(wl, args.precision, args.cheb, cnt),
+                    "kernel": "engine_kernel (FP32-inner CG)"}
         extra = {"cg_steps_per_solve": cnt["cg_steps"] / max(1, cnt["solves"]),
                  "q_applies_per_solve": (cnt["cg_steps"] + cnt["ru_steps"]) * q_per_step / max(1, cnt["solves"]),
                  "ru_steps": cnt["ru_steps"], "fp64_steps": cnt["fp64_steps"], "cheb_degree": args.cheb}
@@ -332,7 +353,9 @@ def run_part(args, wl, world, rank, local, dev, stream):
         bps = 12 if args.precision == "mixed" else 24
         ach = units / world * n * bps / t_dev / 1e9 * world
         roof = {"bound": "hbm", "achieved": ach / world, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / world / peaks["hbm_gbs"], "traffic": None,
+                "frac": ach / world / peaks["hbm_gbs"],
+                # one ncu --set full capture of the fused kernel (profiles/mtm_fused_d3_nx32_nt128_fp32.md)
+                "traffic": (33.58e6 + 0.01e6) if (wl.name == "d3_nx32_nt128" and args.precision == "mixed") else None,
                 "kernel": "M^T M apply (%s)" % ("FP32" if args.precision == "mixed" else "FP64"),
                 "algorithmic_bytes_per_site": bps}
         extra = {"median_apply_us": 1000.0 * float(np.median(dev_ms))}
@@ -625,7 +648,7 @@ def main():
         achieved = flops / eng_s / 1e12 if eng_s > 0 else 0.0
         peak = fp64_peak_tflops()
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": engine_traffic(wl, args.precision, args.cheb, cnt),
                 "kernel": "engine_kernel (persistent FP64 CG)",
                 "peak_source": "FP64 from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz)",
                 "launch_ms": per_launch * 1000.0}
