@@ -186,7 +186,7 @@ int hh_apply(hh_ctx *ctx, int op, const void *x, void *y, int dtype);
  * b, x: device pointers to n_rhs * N doubles.  info may be NULL (then the call
  * does not synchronise).  Returns HH_ENOCONV if a right-hand side missed
  * cg_tol within cg_maxit (x then holds the last iterate), HH_ETIMEOUT if a
- * device-side barrier wait ran out, HH_ENUMERIC on NaN/Inf. */
+ * bounded device-side wait ran out, HH_ENUMERIC on NaN/Inf. */
 int hh_solve(hh_ctx *ctx, const double *b, double *x, int n_rhs, hh_solve_info *info);
 
 /* As hh_solve, from the initial guess x0 held in x on entry: the engine first

@@ -23,7 +23,7 @@ struct EngStats {
     int n_solves;
     int n_ru;
     int worst_status;       // most severe status among systems
-    int error;              // barrier / launch error
+    int error;              // device-side wait / launch error
     int pad;
     double max_relres;
 };

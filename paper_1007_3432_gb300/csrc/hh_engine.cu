@@ -786,6 +786,21 @@ __device__ __forceinline__ void named_arrive(int id, unsigned n)
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
+// The engine kernel.  One block per SM owns fixed tiles; every engine
+// iteration runs the slots of each of its tiles' systems, each slot of a system
+// starting once every tile of that system has published the previous one
+// (signal slots, see EngCtl).  Two forms:
+//  * flat (L.ctl_warp = 0): all 16 warps compute; the block waits, decides and
+//    publishes between tiles;
+//  * control warp (L.ctl_warp = 1): warp 0 waits, decides, sums and publishes
+//    while warps 1-15 run the tasks it posts (one slot of one tile), so that a
+//    task's waits and the previous task's publication overlap the compute of
+//    the current one.  A publication is held back past the next task's
+//    preparation only when that cannot close a cycle of waits: the next task
+//    is of another system at the same phase (level), or the launch is
+//    homogeneous (every block holds one tile of each system, in the same
+//    order), where a preparation needs only publications of tasks two or more
+//    places back.  A block leaves once all its systems are done.
 template <int FD, int MINB>
 __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
 {

@@ -170,7 +170,7 @@ int engine_max_grid(int block, int kind);
 constexpr int ENGINE_BLOCK = 512;
 constexpr int ENGINE_MIN_TILE = 512;   // sites per tile, at least one per thread
 
-// Default grid: one block per SM (fewer arrivals per grid barrier), capped
+// Default grid: one block per SM (fewer blocks per wait), capped
 // by co-residency.
 // HH_ENGINE_BLOCKS_PER_SM overrides the blocks per SM.
 int engine_default_grid(int kind);

@@ -7,7 +7,7 @@
 // must not take the allocator's locks.  hh_solve_noalloc serves them: the
 // caller passes the field sigma, the right-hand side b and the output x, and
 // every other buffer the FP64 CG needs (links, CG vectors, the system table,
-// tiles, per-tile partials, the barrier word) lives in one file-scope
+// tiles, signal slots, the control block) lives in one file-scope
 // __device__ array of fixed size, reserved on every device that loads the
 // library for as long as the process lives.
 //
