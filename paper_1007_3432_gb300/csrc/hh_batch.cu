@@ -781,10 +781,7 @@ int hh_batch_create(hh_batch **out, const hh_batch_config *cfg, void *cuda_strea
     b->grid_of[ENGINE_D1] = engine_default_grid(ENGINE_D1);
     b->grid_of[ENGINE_D3] = engine_default_grid(ENGINE_D3);
     for (int k : {ENGINE_GENERIC, ENGINE_D1, ENGINE_D3}) b->two_slot_of[k] = engine_two_slot(k);
-    {
-        const char *env = getenv("HH_BATCH_CTL_WARP");
-        b->ctl_warp = env ? (atoi(env) != 0) : 1;
-    }
+    b->ctl_warp = engine_ctl_warps(1);
     cudaError_t e = (b->grid_of[0] > 0 && b->grid_of[1] > 0 && b->grid_of[3] > 0) ? cudaSuccess
                                                                                  : cudaErrorUnknown;
     if (e == cudaSuccess) e = b->arena.init(cfg->hbm_budget_bytes);

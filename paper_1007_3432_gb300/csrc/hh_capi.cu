@@ -313,7 +313,7 @@ int run_engine(hh_ctx *c)
     L.tiles = c->d_tiles;
     L.sig = c->d_sig;
     L.sig_stride = c->max_tiles;
-    L.ctl_warp = P.homogeneous;
+    L.ctl_warp = engine_ctl_warps(P.homogeneous ? 1 : 0);
     L.ctl = c->d_ctl;
     L.nsys = P.nsys;
     L.ntiles = P.ntiles;

@@ -770,6 +770,13 @@ struct TaskMsg {
     int pad;
 };
 
+// Where the publishing control warp stores a task's partial.
+struct PubMsg {
+    unsigned long long *now, *next;
+    int part;
+    int pad;
+};
+
 // Named barriers of the control / compute hand-off (0 is __syncthreads):
 // kBarReady + b: a task is posted in s_task[b]; kBarDone + b: the compute
 // warps have ended it and written their partials to s_part[b].
@@ -792,7 +799,8 @@ __device__ __forceinline__ void named_arrive(int id, unsigned n)
 // (signal slots, see EngCtl).  Two forms:
 //  * flat (L.ctl_warp = 0): all 16 warps compute; the block waits, decides and
 //    publishes between tiles;
-//  * control warp (L.ctl_warp = 1): warp 0 waits, decides, sums and publishes
+//  * control warp (L.ctl_warp = 1; 2: warp 0 prepares and posts, warp 1 ends
+//    tasks and publishes): warp 0 waits, decides, sums and publishes
 //    while warps 1-15 run the tasks it posts (one slot of one tile), so that a
 //    task's waits and the previous task's publication overlap the compute of
 //    the current one.  A publication is held back past the next task's
@@ -806,6 +814,11 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
 {
     __shared__ TaskMsg s_task[2];
     __shared__ double s_part[2][ENGINE_BLOCK / 32];
+    // Two control warps: the preparing warp posts tasks (s_posted counts them,
+    // s_pub says where each publishes); the publishing warp ends them
+    // (s_published counts them).
+    __shared__ PubMsg s_pub[2];
+    __shared__ int s_posted, s_published, s_end, s_failed;
     __shared__ double s_red[ENGINE_BLOCK / 32];
     __shared__ int s_flag;
     __shared__ EngState s_cache[kCacheSys];
@@ -980,13 +993,20 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
         return;
     }
 
-    if (threadIdx.x == 0) s_ctl_threads = kCtlThreads;
+    // Control warps: 1, or 2 (warp 0 prepares and posts, warp 1 publishes).
+    const int nctl = L.ctl_warp >= 2 ? 2 : 1;
+    // Threads of each hand-off barrier: the compute warps and one control warp.
+    const unsigned nbar = blockDim.x - 32u * (unsigned)(nctl - 1);
+    if (threadIdx.x == 0) {
+        s_ctl_threads = kCtlThreads * nctl;
+        s_posted = s_published = s_end = s_failed = 0;
+    }
     __syncthreads();
-    if (threadIdx.x >= kCtlThreads) {
+    if (threadIdx.x >= kCtlThreads * nctl) {
         // ---- compute warps: run the tasks the control warp posts ----
-        const int warp = ((int)threadIdx.x >> 5) - 1;
+        const int warp = ((int)threadIdx.x >> 5) - nctl;
         for (int buf = 0;; buf ^= 1) {
-            named_sync(kBarReady + buf, blockDim.x);
+            named_sync(kBarReady + buf, nbar);
             const TaskMsg m = s_task[buf];
             if (m.exit) return;
             const EngTile T = cached ? s_tiles[m.j] : L.tiles[m.tile];
@@ -1004,13 +1024,64 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
             // after the last preconditioner sub-step, else 0.
             v = warp_sum(v);
             if ((threadIdx.x & 31u) == 0) s_part[buf][warp] = v;
-            named_arrive(kBarDone + buf, blockDim.x);
+            named_arrive(kBarDone + buf, nbar);
         }
     }
 
-    // ---- control warp: waits, decisions, partial sums and signals ----
+    const int ncw = (int)(blockDim.x >> 5) - nctl;   // compute warps
+    // Bounded spin on a shared counter written by the other control warp.
+    auto wait_count = [&](volatile int *cnt, int target) -> bool {
+        uint64_t t0 = 0;
+        unsigned spins = 0;
+        while (*cnt < target) {
+            if ((++spins & 255u) == 0) {
+                if (t0 == 0) t0 = global_ns();
+                if ((long long)(global_ns() - t0) > 3 * ctl->timeout_ns) {
+                    atomicCAS(&ctl->error, 0, -6);
+                    return false;
+                }
+            }
+        }
+        return true;
+    };
+    if (nctl == 2 && threadIdx.x >= kCtlThreads) {
+        // ---- publishing warp: ends posted tasks in order, publishes their
+        //      partials (sum of the per-warp partials in warp order) ----
+        const int lane = (int)threadIdx.x & 31;
+        for (int t = 0;; ++t) {
+            // the next posted task, or the end
+            uint64_t t0 = 0;
+            unsigned spins = 0;
+            bool ok = true;
+            while (*(volatile int *)&s_posted <= t && !*(volatile int *)&s_end) {
+                if ((++spins & 255u) == 0) {
+                    if (t0 == 0) t0 = global_ns();
+                    if ((long long)(global_ns() - t0) > 3 * ctl->timeout_ns) {
+                        ok = false;
+                        break;
+                    }
+                }
+            }
+            if (!ok || *(volatile int *)&s_posted <= t) break;
+            __threadfence_block();
+            const int b = t & 1;
+            named_sync(kBarDone + b, nbar);
+            if (lane == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < ncw; ++w) tot += s_part[b][w];
+                const PubMsg pm = s_pub[b];
+                if (!*(volatile int *)&s_failed) sig_publish(pm.now + pm.part, pm.next + pm.part, tot);
+                __threadfence_block();
+                *(volatile int *)&s_published = t + 1;
+            }
+            __syncwarp();
+        }
+        return;
+    }
+
+    // ---- control warp (with two: the preparing warp): waits, decisions,
+    //      partial sums and signals ----
     const int lane = (int)threadIdx.x;
-    const int ncw = (int)(blockDim.x >> 5) - 1;   // compute warps
     const int two = L.two_slot;
     const int nph = two ? 2 : 3;
     const size_t stride = (size_t)L.sig_stride;
@@ -1020,14 +1091,21 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
     int pend_buf = 0, pend_part = 0, pend_sys = -1;
     long long pend_level = 0;
     unsigned long long *pend_now = nullptr, *pend_next = nullptr;
+    int posted = 0;
     // Waits for the compute warps to end the pending task, then publishes its
-    // partial (the sum of the per-warp partials in warp order).
+    // partial (the sum of the per-warp partials in warp order); with two
+    // control warps, waits until the publishing warp has done so.
     auto finish = [&]() {
-        named_sync(kBarDone + pend_buf, blockDim.x);
-        if (lane == 0) {
-            double tot = 0.0;
-            for (int w = 0; w < ncw; ++w) tot += s_part[pend_buf][w];
-            if (!failed) sig_publish(pend_now + pend_part, pend_next + pend_part, tot);
+        if (nctl == 1) {
+            named_sync(kBarDone + pend_buf, nbar);
+            if (lane == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < ncw; ++w) tot += s_part[pend_buf][w];
+                if (!failed) sig_publish(pend_now + pend_part, pend_next + pend_part, tot);
+            }
+            __syncwarp();
+        } else if (!wait_count(&s_published, posted)) {
+            failed = true;
         }
         __syncwarp();
         pend = false;
@@ -1109,6 +1187,12 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                 }
                 const TileCtl c = s_tctl[slot];
                 if (c.mode == MODE_DONE) continue;
+                // The compute warps have read this buffer's previous task (two
+                // back) once it is published.
+                if (nctl == 2 && !wait_count(&s_published, posted - 1)) {
+                    failed = true;
+                    break;
+                }
                 if (lane == 0) {
                     TaskMsg &m = s_task[buf];
                     m.c = c;
@@ -1117,10 +1201,21 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                     m.slot = slot;
                     m.tile = tile;
                     m.exit = 0;
+                    if (nctl == 2) {
+                        PubMsg &pm = s_pub[buf];
+                        pm.now = sig_now;
+                        pm.next = sig_next;
+                        pm.part = T.part;
+                    }
                 }
                 __syncwarp();
-                named_arrive(kBarReady + buf, blockDim.x);
-                if (pend) finish();
+                named_arrive(kBarReady + buf, nbar);
+                ++posted;
+                if (nctl == 2 && lane == 0) {
+                    __threadfence_block();
+                    *(volatile int *)&s_posted = posted;
+                }
+                if (nctl == 1 && pend) finish();
                 pend = true;
                 pend_buf = buf;
                 pend_part = T.part;
@@ -1141,13 +1236,18 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
             }
         }
     }
+    if (nctl == 2 && failed && lane == 0) *(volatile int *)&s_failed = 1;
     if (pend) finish();
     if (lane == 0) {
         s_task[buf].exit = 1;
         if (!stop && !failed) atomicMax((long long *)&ctl->k_end, k);
+        if (nctl == 2) {
+            __threadfence_block();
+            *(volatile int *)&s_end = 1;
+        }
     }
     __syncwarp();
-    named_arrive(kBarReady + buf, blockDim.x);
+    named_arrive(kBarReady + buf, nbar);
 }
 
 }  // namespace
@@ -1240,6 +1340,14 @@ void engine_cheb_table(int d, double h, double A, int n, double eps, double *tab
         tab[3 + 3 * j] = b * b;
         tab[4 + 3 * j] = 1.0 / ((m - a) * (m - a) + b * b);
     }
+}
+
+int engine_ctl_warps(int dflt)
+{
+    const char *env = getenv("HH_ENGINE_CTL_WARPS");
+    if (!env) return dflt;
+    const int v = atoi(env);
+    return v < 0 ? 0 : (v > 2 ? 2 : v);
 }
 
 bool engine_overlap(int nsys, long long sites, bool mixed)

@@ -133,7 +133,7 @@ struct EngLaunch {
     // slots must be empty (kSigEmpty) when it enters as MODE_NEW.
     unsigned long long *sig;
     int sig_stride;
-    int ctl_warp;           // 1: warp 0 is a control warp (see the kernel); 0: flat
+    int ctl_warp;           // control warps (see the kernel): 0 flat, 1 warp 0, 2 warps 0 and 1
     EngCtl *ctl;
     int nsys, ntiles;
     long long max_iters;    // engine iterations this launch may run
@@ -184,6 +184,10 @@ int engine_two_slot(int kind);
 // CHEB_MAX_DEGREE) for the lattice dimension d, hop h = t dtau and coupling A:
 // writes 2 + 3 CHEB_MAX_DEGREE doubles.
 void engine_cheb_table(int d, double h, double A, int n, double eps, double *tab);
+
+// Control warps of an engine launch: 'dflt', unless HH_ENGINE_CTL_WARPS (0, 1
+// or 2) overrides it.
+int engine_ctl_warps(int dflt);
 
 // Whether a launch of nsys systems of 'sites' sites each uses the overlapped
 // layout (see EngLaunch::homogeneous); HH_ENGINE_OVERLAP=0 or 1 forces it.
