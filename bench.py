@@ -72,8 +72,8 @@ def bytes_per_site(kind, precision):
 # as it stands, from one ncu --set full capture each (dram__bytes_read.sum +
 # dram__bytes_write.sum over a 202-iteration launch; profiles/engine_kernel_*).
 # A launch's traffic scales with its iterations.
-ENGINE_DRAM_PER_ITER = {("d1_nx1024_nt512", "fp64"): (12.720384e6 + 95.198208e6) / 202,
-                        ("d3_nx32_nt128", "mixed"): (33.617242e9 + 27.067933e9) / 202}
+ENGINE_DRAM_PER_ITER = {("d1_nx1024_nt512", "fp64"): (12.7232e6 + 455.225344e6) / 202,
+                        ("d3_nx32_nt128", "mixed"): (35.046802e9 + 27.076187e9) / 202}
 
 
 def engine_traffic(wl, precision, cheb, cnt):

@@ -205,6 +205,11 @@ int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
     int ntiles = tl.tiles * n_rhs;
     if (ntiles > c->max_tiles) return HH_EINVAL;
     const int grid = overlap ? tl.tiles : (ntiles < c->max_grid ? ntiles : c->max_grid);
+    // Bytes the CG iteration streams per site: x, r, p, t, b, the links and
+    // the second p buffer in FP64 (and z, u with the preconditioner); r, p,
+    // t, x, links, p' in FP32 (mixed).
+    const long long site_bytes = c->prm.precision == HH_MIXED ? 24 : (c->prm.cheb_degree > 0 ? 72 : 56);
+    const int pf = engine_prefetch(site_bytes * (long long)c->N * n_rhs, c->lat.d);
     std::vector<EngSystem> sys(n_rhs);
     std::vector<EngTile> tiles;
     tiles.reserve(ntiles);
@@ -245,6 +250,7 @@ int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
         Y.delta2 = c->prm.reliable_delta * c->prm.reliable_delta;
         Y.maxit = c->prm.cg_maxit;
         Y.w = engine_group_width(c->lat.nx);
+        Y.pf = pf;
         Y.stall_window = ENGINE_STALL_WINDOW;
         Y.cheb_n = c->prm.cheb_degree;
         Y.cheb = c->d_cheb;

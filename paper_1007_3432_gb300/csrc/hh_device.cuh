@@ -184,6 +184,23 @@ struct Vec {
     T a[W];
 };
 
+// Hint to bring the line holding *p into L2 ahead of a demand load.  p must
+// point into an allocation (callers keep it inside the vector they stream).
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Site j shifted one slice earlier / later (cyclic in tau).
+__device__ __forceinline__ int row_prev(const Geo &g, int j)
+{
+    return j >= g.V ? j - g.V : j + (g.ntau - 1) * g.V;
+}
+__device__ __forceinline__ int row_next(const Geo &g, int j)
+{
+    return j < g.N - g.V ? j + g.V : j - (g.ntau - 1) * g.V;
+}
+
 template <typename T, int W>
 __device__ __forceinline__ Vec<T, W> vld(const T *p)
 {

@@ -40,10 +40,17 @@ __device__ __forceinline__ int cnth()
 
 template <int D, typename T, int W>
 __device__ double gloop_M(const Geo g, const T h, const T *__restrict__ L, const T *v, T *t, int b,
-                          int e)
+                          int e, int pf = 0)
 {
     T acc = T(0);
-    for (int i = b + W * ctid(); i < e; i += W * cnth()) {
+    const int step = W * cnth(), ahead = pf * step;
+    for (int i = b + W * ctid(); i < e; i += step) {
+        if (ahead && i + ahead < e) {
+            const int j = i + ahead, jp = row_prev(g, j);
+            prefetch_l2(v + j);
+            prefetch_l2(v + jp);
+            prefetch_l2(L + jp);
+        }
         GroupNbr nb;
         group_nbrs<D, W>(g, i, nb);
         Vec<T, W> self = vld<T, W>(v + i);
@@ -64,10 +71,20 @@ __device__ double gloop_M(const Geo g, const T h, const T *__restrict__ L, const
 // CG slot 3: q = M^T t, x += alpha p, r -= alpha q; acc += r^2.
 template <int D, typename T, int W>
 __device__ double gloop_update(const Geo g, const T h, const T *__restrict__ L, const T *t, T *x,
-                               const T *p, T *r, const T alpha, int b, int e)
+                               const T *p, T *r, const T alpha, int b, int e, int pf = 0)
 {
     T acc = T(0);
-    for (int i = b + W * ctid(); i < e; i += W * cnth()) {
+    const int step = W * cnth(), ahead = pf * step;
+    for (int i = b + W * ctid(); i < e; i += step) {
+        if (ahead && i + ahead < e) {
+            const int j = i + ahead;
+            prefetch_l2(t + j);
+            prefetch_l2(t + row_next(g, j));
+            prefetch_l2(L + j);
+            prefetch_l2(x + j);
+            prefetch_l2(p + j);
+            prefetch_l2(r + j);
+        }
         GroupNbr nb;
         group_nbrs<D, W>(g, i, nb);
         Vec<T, W> self = vld<T, W>(t + i);
@@ -123,9 +140,18 @@ __device__ double gloop_residual(const Geo g, const double h, const double *__re
 // Preconditioner sub-step of an even index: u = (Q/lam) z - a z, from t = M z.
 template <int D, int W>
 __device__ void gloop_cheb_u(const Geo g, const double h, const double *__restrict__ L, const double *t,
-                             const double *z, double *u, const double invlam, const double a, int b, int e)
+                             const double *z, double *u, const double invlam, const double a, int b, int e,
+                             int pf = 0)
 {
-    for (int i = b + W * ctid(); i < e; i += W * cnth()) {
+    const int step = W * cnth(), ahead = pf * step;
+    for (int i = b + W * ctid(); i < e; i += step) {
+        if (ahead && i + ahead < e) {
+            const int j = i + ahead;
+            prefetch_l2(t + j);
+            prefetch_l2(t + row_next(g, j));
+            prefetch_l2(L + j);
+            prefetch_l2(z + j);
+        }
         GroupNbr nb;
         group_nbrs<D, W>(g, i, nb);
         Vec<double, W> self = vld<double, W>(t + i);
@@ -148,10 +174,20 @@ template <int D, int W>
 __device__ double gloop_cheb_z(const Geo g, const double h, const double *__restrict__ L, const double *t,
                                const double *u, double *z, const double *r, const double invlam,
                                const double a, const double b2, const double invq, const double scale,
-                               bool dot, int b, int e)
+                               bool dot, int b, int e, int pf = 0)
 {
     double acc = 0.0;
-    for (int i = b + W * ctid(); i < e; i += W * cnth()) {
+    const int step = W * cnth(), ahead = pf * step;
+    for (int i = b + W * ctid(); i < e; i += step) {
+        if (ahead && i + ahead < e) {
+            const int j = i + ahead;
+            prefetch_l2(t + j);
+            prefetch_l2(t + row_next(g, j));
+            prefetch_l2(L + j);
+            prefetch_l2(u + j);
+            prefetch_l2(z + j);
+            if (dot) prefetch_l2(r + j);
+        }
         GroupNbr nb;
         group_nbrs<D, W>(g, i, nb);
         Vec<double, W> self = vld<double, W>(t + i);
@@ -232,10 +268,21 @@ __device__ double gloop_residual_ex(const Geo g, const double h, const double *_
 // ones their owners store (the same fma on the same inputs).
 template <int D, typename T, int W>
 __device__ double gloop_pM(const Geo g, const T h, const T *__restrict__ L, const T *src, const T *pold,
-                           T *pnew, T *t, const T beta, bool restart, int b, int e)
+                           T *pnew, T *t, const T beta, bool restart, int b, int e, int pf = 0)
 {
     T acc = T(0);
-    for (int i = b + W * ctid(); i < e; i += W * cnth()) {
+    const int step = W * cnth(), ahead = pf * step;
+    for (int i = b + W * ctid(); i < e; i += step) {
+        if (ahead && i + ahead < e) {
+            const int j = i + ahead, jp = row_prev(g, j);
+            prefetch_l2(src + j);
+            prefetch_l2(src + jp);
+            prefetch_l2(L + jp);
+            if (!restart) {
+                prefetch_l2(pold + j);
+                prefetch_l2(pold + jp);
+            }
+        }
         GroupNbr nb;
         group_nbrs<D, W>(g, i, nb);
         auto pn_at = [&](int j) -> T {
@@ -321,9 +368,14 @@ __device__ void gloop_accM(const Geo g, const double h, const double *__restrict
 
 // p = r + beta p (restart: p = r).
 template <typename T, int W>
-__device__ void gloop_direction(const T *r, T *p, const T beta, bool restart, int b, int e)
+__device__ void gloop_direction(const T *r, T *p, const T beta, bool restart, int b, int e, int pf = 0)
 {
-    for (int i = b + W * ctid(); i < e; i += W * cnth()) {
+    const int step = W * cnth(), ahead = pf * step;
+    for (int i = b + W * ctid(); i < e; i += step) {
+        if (ahead && i + ahead < e) {
+            prefetch_l2(r + i + ahead);
+            if (!restart) prefetch_l2(p + i + ahead);
+        }
         Vec<T, W> rv = vld<T, W>(r + i);
         if (!restart) {
             Vec<T, W> pv = vld<T, W>(p + i);
@@ -578,19 +630,20 @@ __device__ double init_residual(const EngSystem &Y, const EngTile &T)
     return acc;
 }
 
-template <int D, int W>
+template <int D, int W, bool PF = true>
 __device__ void slot1(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 {
+    const int pf = PF ? Y.pf : 0;
     if (c.mode == MODE_PRE) {
         if (c.pre_j == 0) gloop_direction<double, W>(Y.r, Y.z, 0.0, true, T.begin, T.end);
     } else if (c.mode == MODE_CG) {
         bool restart = (c.beta == 0.0);
         if (Y.cheb_n > 0)
-            gloop_direction<double, W>(Y.z, pbuf64(Y, c.pnew), c.beta, restart, T.begin, T.end);
+            gloop_direction<double, W>(Y.z, pbuf64(Y, c.pnew), c.beta, restart, T.begin, T.end, pf);
         else if (c.prec == PREC_FP64)
-            gloop_direction<double, W>(Y.r, pbuf64(Y, c.pnew), c.beta, restart, T.begin, T.end);
+            gloop_direction<double, W>(Y.r, pbuf64(Y, c.pnew), c.beta, restart, T.begin, T.end, pf);
         else
-            gloop_direction<float, W>(Y.r32, pbuf32(Y, c.pnew), (float)c.beta, restart, T.begin, T.end);
+            gloop_direction<float, W>(Y.r32, pbuf32(Y, c.pnew), (float)c.beta, restart, T.begin, T.end, pf);
     } else if (c.mode == MODE_RU) {
         if (c.prec == PREC_MIXED && !c.two) gloop_accumulate<W>(Y.x, Y.x32, T.begin, T.end);
     } else if (c.mode == MODE_INIT) {
@@ -601,29 +654,31 @@ __device__ void slot1(const EngSystem &Y, const TileCtl &c, const EngTile &T)
     }
 }
 
-template <int D, int W>
+template <int D, int W, bool PF = true>
 __device__ double slot2(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 {
+    const int pf = PF ? Y.pf : 0;
     if (c.mode == MODE_CG) {
         if (c.prec == PREC_FP64)
-            return gloop_M<D, double, W>(Y.g, Y.h, Y.L64, pbuf64(Y, c.pnew), Y.t, T.begin, T.end);
-        return gloop_M<D, float, W>(Y.g, (float)Y.h, Y.L32, pbuf32(Y, c.pnew), Y.t32, T.begin, T.end);
+            return gloop_M<D, double, W>(Y.g, Y.h, Y.L64, pbuf64(Y, c.pnew), Y.t, T.begin, T.end, pf);
+        return gloop_M<D, float, W>(Y.g, (float)Y.h, Y.L32, pbuf32(Y, c.pnew), Y.t32, T.begin, T.end, pf);
     }
     if (c.mode == MODE_RU) gloop_M<D, double, W>(Y.g, Y.h, Y.L64, Y.x, Y.t, T.begin, T.end);
     if (c.mode == MODE_PRE)
-        gloop_M<D, double, W>(Y.g, Y.h, Y.L64, (c.pre_j & 1) ? Y.u : Y.z, Y.t, T.begin, T.end);
+        gloop_M<D, double, W>(Y.g, Y.h, Y.L64, (c.pre_j & 1) ? Y.u : Y.z, Y.t, T.begin, T.end, pf);
     return 0.0;
 }
 
-template <int D, int W>
+template <int D, int W, bool PF = true>
 __device__ double slot3(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 {
+    const int pf = PF ? Y.pf : 0;
     if (c.mode == MODE_CG) {
         if (c.prec == PREC_FP64)
             return gloop_update<D, double, W>(Y.g, Y.h, Y.L64, Y.t, Y.x, pbuf64(Y, c.pnew), Y.r, c.alpha,
-                                              T.begin, T.end);
+                                              T.begin, T.end, pf);
         return gloop_update<D, float, W>(Y.g, (float)Y.h, Y.L32, Y.t32, Y.x32, pbuf32(Y, c.pnew), Y.r32,
-                                         (float)c.alpha, T.begin, T.end);
+                                         (float)c.alpha, T.begin, T.end, pf);
     }
     if (c.mode == MODE_RU) {
         // Two-slot form: the mixed reliable update accumulates here, after
@@ -636,13 +691,13 @@ __device__ double slot3(const EngSystem &Y, const TileCtl &c, const EngTile &T)
         const int k = c.pre_j >> 1;
         const double invlam = __ldg(Y.cheb), a = __ldg(Y.cheb + 2 + 3 * k);
         if ((c.pre_j & 1) == 0) {
-            gloop_cheb_u<D, W>(Y.g, Y.h, Y.L64, Y.t, Y.z, Y.u, invlam, a, T.begin, T.end);
+            gloop_cheb_u<D, W>(Y.g, Y.h, Y.L64, Y.t, Y.z, Y.u, invlam, a, T.begin, T.end, pf);
             return 0.0;
         }
         const bool last = (c.pre_j == 2 * Y.cheb_n - 1);
         const double b2 = __ldg(Y.cheb + 3 + 3 * k), invq = __ldg(Y.cheb + 4 + 3 * k);
         return gloop_cheb_z<D, W>(Y.g, Y.h, Y.L64, Y.t, Y.u, Y.z, Y.r, invlam, a, b2, invq,
-                                  last ? __ldg(Y.cheb + 1) : 1.0, last, T.begin, T.end);
+                                  last ? __ldg(Y.cheb + 1) : 1.0, last, T.begin, T.end, pf);
     }
     if (c.mode == MODE_INIT) return init_residual(Y, T);
     return 0.0;
@@ -679,19 +734,20 @@ __device__ double slot3_ex(const EngSystem &Y, const TileCtl &c, const EngTile &
 
 // Two-slot first slot: slot 1 folded into slot 2.  Returns this thread's
 // |t|^2 partial for a CG step (0 otherwise).
-template <int D, int W>
+template <int D, int W, bool PF = true>
 __device__ double slotA(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 {
+    const int pf = PF ? Y.pf : 0;
     if (c.mode == MODE_CG) {
         const bool restart = (c.beta == 0.0);
         if (Y.cheb_n > 0)
             return gloop_pM<D, double, W>(Y.g, Y.h, Y.L64, Y.z, pbuf64(Y, c.pold), pbuf64(Y, c.pnew), Y.t,
-                                          c.beta, restart, T.begin, T.end);
+                                          c.beta, restart, T.begin, T.end, pf);
         if (c.prec == PREC_FP64)
             return gloop_pM<D, double, W>(Y.g, Y.h, Y.L64, Y.r, pbuf64(Y, c.pold), pbuf64(Y, c.pnew), Y.t,
-                                          c.beta, restart, T.begin, T.end);
+                                          c.beta, restart, T.begin, T.end, pf);
         return gloop_pM<D, float, W>(Y.g, (float)Y.h, Y.L32, Y.r32, pbuf32(Y, c.pold), pbuf32(Y, c.pnew),
-                                     Y.t32, (float)c.beta, restart, T.begin, T.end);
+                                     Y.t32, (float)c.beta, restart, T.begin, T.end, pf);
     }
     if (c.mode == MODE_RU) {
         if (c.prec == PREC_MIXED)
@@ -702,12 +758,12 @@ __device__ double slotA(const EngSystem &Y, const TileCtl &c, const EngTile &T)
     }
     if (c.mode == MODE_PRE) {
         if (c.pre_j == 0)
-            gloop_pM<D, double, W>(Y.g, Y.h, Y.L64, Y.r, Y.r, Y.z, Y.t, 0.0, true, T.begin, T.end);
+            gloop_pM<D, double, W>(Y.g, Y.h, Y.L64, Y.r, Y.r, Y.z, Y.t, 0.0, true, T.begin, T.end, pf);
         else
-            gloop_M<D, double, W>(Y.g, Y.h, Y.L64, (c.pre_j & 1) ? Y.u : Y.z, Y.t, T.begin, T.end);
+            gloop_M<D, double, W>(Y.g, Y.h, Y.L64, (c.pre_j & 1) ? Y.u : Y.z, Y.t, T.begin, T.end, pf);
         return 0.0;
     }
-    if (c.mode == MODE_INIT) slot1<D, W>(Y, c, T);
+    if (c.mode == MODE_INIT) slot1<D, W, PF>(Y, c, T);
     return 0.0;
 }
 
@@ -725,16 +781,18 @@ __device__ double run_slot(const EngSystem &Y, const TileCtl &c, const EngTile &
         if (SLOT == 3) return slot3_ex(Y, c, T);
         return 0.0;
     }
+    // The generic kernel (FD = 0) carries both dimensions' loops; it is
+    // compiled without the prefetches to stay within its registers.
 #define HH_SLOT_CALL(D, W)                                   \
     if (SLOT == 1) {                                         \
-        slot1<D, W>(Y, c, T);                                \
+        slot1<D, W, FD != 0>(Y, c, T);                       \
         return 0.0;                                          \
     } else if (SLOT == 2) {                                  \
-        return slot2<D, W>(Y, c, T);                         \
+        return slot2<D, W, FD != 0>(Y, c, T);                \
     } else if (SLOT == 4) {                                  \
-        return slotA<D, W>(Y, c, T);                         \
+        return slotA<D, W, FD != 0>(Y, c, T);                \
     } else {                                                 \
-        return slot3<D, W>(Y, c, T);                         \
+        return slot3<D, W, FD != 0>(Y, c, T);                \
     }
     const int w = Y.w;
     if (FD == 3 || (FD == 0 && Y.g.d == 3)) {
@@ -1348,6 +1406,13 @@ int engine_ctl_warps(int dflt)
     if (!env) return dflt;
     const int v = atoi(env);
     return v < 0 ? 0 : (v > 2 ? 2 : v);
+}
+
+int engine_prefetch(long long bytes, int d)
+{
+    int pf = (d == 3 && bytes > (64LL << 20)) ? 1 : 0;
+    if (const char *env = getenv("HH_ENGINE_PREFETCH")) pf = atoi(env);
+    return pf < 0 ? 0 : (pf > 8 ? 8 : pf);
 }
 
 bool engine_overlap(int nsys, long long sites, bool mixed)

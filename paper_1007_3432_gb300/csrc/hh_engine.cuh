@@ -71,6 +71,8 @@ struct EngSystem {
     double delta2;                    // reliable_delta^2 (mixed)
     int maxit;
     int w;                            // x sites per thread group: 4, 2 or 1 (divides Nx)
+    int pf;                           // CG site loops prefetch into L2 this many rounds of the
+                                      // loop ahead (0: none; see engine_prefetch)
     int stall_window;                 // mixed: forced RU after this many FP32 steps without one
     int cheb_n;                       // Chebyshev preconditioner degree n (0: plain CG; FP64 only)
     int x0_given;                     // 1: x holds an initial guess when the system starts (MODE_NEW)
@@ -192,6 +194,14 @@ int engine_ctl_warps(int dflt);
 // Whether a launch of nsys systems of 'sites' sites each uses the overlapped
 // layout (see EngLaunch::homogeneous); HH_ENGINE_OVERLAP=0 or 1 forces it.
 bool engine_overlap(int nsys, long long sites, bool mixed);
+
+// L2 prefetch distance (EngSystem::pf) of a system of dimension d in a
+// launch whose CG vectors take 'bytes' in all: one round of the site loop
+// ahead for d = 3 when they overflow about half of the L2 (the loops then wait
+// on DRAM, one round trip per round; measured on GB300: 13% less time per
+// mixed iteration on 32^3 x 128), else none (d = 1 loops run 2-9% slower with
+// it).  HH_ENGINE_PREFETCH sets the distance.
+int engine_prefetch(long long bytes, int d);
 
 // Tiles of one system: 'tiles' contiguous ranges of 'chunk' sites (the last
 // one shorter), enough to give every block of the grid a tile when 'nsys'
