@@ -354,8 +354,8 @@ def run_part(args, wl, world, rank, local, dev, stream):
         ach = units / world * n * bps / t_dev / 1e9 * world
         roof = {"bound": "hbm", "achieved": ach / world, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / world / peaks["hbm_gbs"],
-                # one ncu --set full capture of the fused kernel (profiles/mtm_fused_d3_nx32_nt128_fp32.md)
-                "traffic": (33.58e6 + 0.01e6) if (wl.name == "d3_nx32_nt128" and args.precision == "mixed") else None,
+                # one ncu capture of the apply's two sweeps (profiles/mtm_sweeps_d3_nx32_nt128_fp32.md)
+                "traffic": (33557760 + 344320 + 88320 + 6871040) if (wl.name == "d3_nx32_nt128" and args.precision == "mixed") else None,
                 "kernel": "M^T M apply (%s)" % ("FP32" if args.precision == "mixed" else "FP64"),
                 "algorithmic_bytes_per_site": bps}
         extra = {"median_apply_us": 1000.0 * float(np.median(dev_ms))}

@@ -10,6 +10,8 @@
 // slab.  The slices are brought in by 1-D TMA bulk copies that complete on
 // mbarriers, two slices ahead of use, so HBM is read once per site (halo
 // re-reads hit L2) and q is written once: 12 bytes per site in FP32.
+#include <cstdlib>
+
 #include "hh_apply.cuh"
 
 namespace hh {
@@ -23,6 +25,13 @@ template <int D, typename T, int W, bool TRANS>
 __global__ void __launch_bounds__(256) k_apply_group(const Geo g, const T h, const T *__restrict__ L,
                                                      const T *__restrict__ x, T *__restrict__ y)
 {
+    // Programmatic dependent launch: a sweep launched after this one with
+    // programmatic stream serialization may start its blocks once every block
+    // here has started; it waits below, until this grid has completed and
+    // its writes are visible, before reading.  Without that launch attribute
+    // both instructions return at once.
+    asm volatile("griddepcontrol.launch_dependents;");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int stride = W * gridDim.x * blockDim.x;
     for (int i = W * (blockIdx.x * blockDim.x + threadIdx.x); i < g.N; i += stride) {
         GroupNbr nb;
@@ -38,15 +47,41 @@ __global__ void __launch_bounds__(256) k_apply_group(const Geo g, const T h, con
     }
 }
 
+template <typename K, typename T>
+cudaError_t launch_group_kernel(K kern, int blocks, bool pdl, cudaStream_t st, const Geo &g, T h, const T *L,
+                                const T *x, T *y)
+{
+    if (!pdl) {
+        kern<<<blocks, 256, 0, st>>>(g, h, L, x, y);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, g, h, L, x, y);
+}
+
 template <typename T, bool TRANS>
-cudaError_t launch_sweep(const Geo &g, T h, const T *L, const T *x, T *y, cudaStream_t st)
+cudaError_t launch_sweep(const Geo &g, T h, const T *L, const T *x, T *y, cudaStream_t st, bool pdl)
 {
     const int w = engine_group_width(g.nx);
     long long groups = g.N / w;
     int blocks = (int)((groups + 255) / 256);
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    static const int cap = [] {
+        const char *env = getenv("HH_APPLY_SWEEP_BLOCKS");
+        return env ? atoi(env) : 152 * 16;
+    }();
+    if (cap > 0 && blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-#define HH_SWEEP(D, W) k_apply_group<D, T, W, TRANS><<<blocks, 256, 0, st>>>(g, h, L, x, y)
+#define HH_SWEEP(D, W) \
+    return launch_group_kernel(k_apply_group<D, T, W, TRANS>, blocks, pdl, st, g, h, L, x, y)
     if (g.d == 3) {
         if (w == 4) HH_SWEEP(3, 4);
         else if (w == 2) HH_SWEEP(3, 2);
@@ -409,15 +444,17 @@ cudaError_t launch_mtm_fused_f32(const Geo &g, float h, const float *L, const fl
 }
 
 cudaError_t launch_sweep_f64(const Geo &g, bool trans, double h, const double *L, const double *x, double *y,
-                             cudaStream_t st)
+                             cudaStream_t st, bool pdl)
 {
-    return trans ? launch_sweep<double, true>(g, h, L, x, y, st) : launch_sweep<double, false>(g, h, L, x, y, st);
+    return trans ? launch_sweep<double, true>(g, h, L, x, y, st, pdl)
+                 : launch_sweep<double, false>(g, h, L, x, y, st, pdl);
 }
 
 cudaError_t launch_sweep_f32(const Geo &g, bool trans, float h, const float *L, const float *x, float *y,
-                             cudaStream_t st)
+                             cudaStream_t st, bool pdl)
 {
-    return trans ? launch_sweep<float, true>(g, h, L, x, y, st) : launch_sweep<float, false>(g, h, L, x, y, st);
+    return trans ? launch_sweep<float, true>(g, h, L, x, y, st, pdl)
+                 : launch_sweep<float, false>(g, h, L, x, y, st, pdl);
 }
 
 }  // namespace hh

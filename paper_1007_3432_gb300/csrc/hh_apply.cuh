@@ -7,11 +7,14 @@
 namespace hh {
 
 // y = M x (trans = false) or y = M^T x (trans = true): one sweep in x groups
-// of W sites with 16-byte accesses (x, y, L 16-byte aligned).
+// of W sites with 16-byte accesses (x, y, L 16-byte aligned).  pdl: launch
+// with programmatic stream serialization, so that the sweep's blocks start
+// while the previous sweep on the stream finishes (they wait for its
+// completion before reading).
 cudaError_t launch_sweep_f64(const Geo &g, bool trans, double h, const double *L, const double *x, double *y,
-                             cudaStream_t st);
+                             cudaStream_t st, bool pdl = false);
 cudaError_t launch_sweep_f32(const Geo &g, bool trans, float h, const float *L, const float *x, float *y,
-                             cudaStream_t st);
+                             cudaStream_t st, bool pdl = false);
 
 // Whether the fused FP32 d=3 Q kernel applies to this lattice and these
 // pointers (x-y plane fits in shared memory, 16-byte alignment).

@@ -147,6 +147,9 @@ struct hh_ctx {
     void *h_pinned;         // host readback buffer
     int *d_apply_err;       // set by a fused apply whose bounded wait ran out
     int nsm;
+    int mtm_path;           // Q apply path (HH_APPLY_MTM): 0 by size (see hh_apply), 1 two
+                            // sweeps, 2 two sweeps with programmatic dependent launch, 3 the
+                            // fused FP32 d = 3 kernel where it applies
     double *z, *u;          // Chebyshev preconditioner vectors (cap_rhs each), or null
     double *d_cheb;         // its coefficient table
 };
@@ -520,6 +523,7 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (const char *env = getenv("HH_APPLY_MTM")) c->mtm_path = atoi(env);
     }
     if (e == cudaSuccess) e = launch_links(c->geo, p->A, c->sigma, c->L64, c->L32, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -624,7 +628,7 @@ int hh_apply(hh_ctx *c, int op, const void *x, void *y, int dtype)
         if (op == HH_OP_MTM) {
             if (vec) {
                 HH_TRY(launch_sweep_f64(c->geo, false, h, c->L64, xd, c->tmp, c->stream));
-                HH_TRY(launch_sweep_f64(c->geo, true, h, c->L64, c->tmp, yd, c->stream));
+                HH_TRY(launch_sweep_f64(c->geo, true, h, c->L64, c->tmp, yd, c->stream, c->mtm_path != 1));
             } else {
                 HH_TRY(launch_apply_f64(c->geo, 0, h, c->L64, xd, c->tmp, c->stream));
                 HH_TRY(launch_apply_f64(c->geo, 1, h, c->L64, c->tmp, yd, c->stream));
@@ -641,12 +645,19 @@ int hh_apply(hh_ctx *c, int op, const void *x, void *y, int dtype)
         const float *xf = (const float *)x;
         float *yf = (float *)y;
         if (op == HH_OP_MTM) {
-            if (vec && fused_mtm_ok(c->geo, c->L32, xf, yf)) {
+            // Two sweeps with t = M x kept in L2 while x, t, y and the links fit
+            // in it (measured on GB300 at 4.2M sites: 26 us cold against 31 us
+            // for the fused kernel); the fused kernel, which keeps t in shared
+            // memory, beyond that.
+            const bool big = (long long)c->N * 16 > (96LL << 20);
+            const bool fused = c->mtm_path == 3 || (c->mtm_path == 0 && big);
+            if (vec && fused && fused_mtm_ok(c->geo, c->L32, xf, yf)) {
                 HH_TRY(launch_mtm_fused_f32(c->geo, (float)h, c->L32, xf, yf, c->d_apply_err, c->nsm, c->stream));
                 launches = 1;
             } else if (vec) {
                 HH_TRY(launch_sweep_f32(c->geo, false, (float)h, c->L32, xf, c->tmp32a, c->stream));
-                HH_TRY(launch_sweep_f32(c->geo, true, (float)h, c->L32, c->tmp32a, yf, c->stream));
+                HH_TRY(launch_sweep_f32(c->geo, true, (float)h, c->L32, c->tmp32a, yf, c->stream,
+                                        c->mtm_path != 1));
                 launches = 2;
             } else {
                 HH_TRY(launch_apply_f32(c->geo, 0, (float)h, c->L32, xf, c->tmp32a, c->stream));

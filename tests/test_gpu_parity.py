@@ -77,9 +77,15 @@ FP32_SHAPES = [(1, 32, 64), (3, 8, 12), (3, 5, 7), (3, 4, 3), (3, 6, 5), (3, 12,
                (3, 10, 40)]
 
 
+# Q apply paths (HH_APPLY_MTM): by size (two sweeps with programmatic
+# dependent launch here), plain two sweeps, the fused FP32 d = 3 kernel.
+MTM_PATHS = ["0", "1", "3"]
+
+
 @pytest.mark.parametrize("d,nx,ntau", FP32_SHAPES)
-@pytest.mark.parametrize("op", ["M", "MT", "MTM"])
-def test_apply_fp32_per_element(hh, d, nx, ntau, op):
+@pytest.mark.parametrize("op,path", [("M", "0"), ("MT", "0")] + [("MTM", p) for p in MTM_PATHS])
+def test_apply_fp32_per_element(hh, monkeypatch, d, nx, ntau, op, path):
+    monkeypatch.setenv("HH_APPLY_MTM", path)
     lat = oracle.lattice(d, nx, ntau)
     n = oracle.nsites(lat)
     sigma = workloads.sigma_field(n, seed=300 + nx)
@@ -97,9 +103,12 @@ def test_apply_fp32_per_element(hh, d, nx, ntau, op):
     assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
 
 
-def test_fused_mtm_fp32_full_size_lattice(hh):
-    """Q x on the d=3, 32^3 x 128 lattice (4.2M sites) in the launch
-    configuration the benchmark times, every element against the oracle."""
+@pytest.mark.parametrize("path", MTM_PATHS)
+def test_mtm_fp32_full_size_lattice(hh, monkeypatch, path):
+    """Q x on the d=3, 32^3 x 128 lattice (4.2M sites) on every Q apply path,
+    the default one being the launch configuration the benchmark times; every
+    element against the oracle."""
+    monkeypatch.setenv("HH_APPLY_MTM", path)
     wl = workloads.C2
     lat = oracle.lattice(wl.d, wl.nx, wl.ntau)
     n = wl.nsites
