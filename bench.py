@@ -194,10 +194,12 @@ def sum_over_ranks(world, value):
     return float(t.item())
 
 
-def cpu_baseline(wl, seconds=15.0):
-    """The oracle, as it stands, on this host: CG iterations on the same
-    lattice and field for about `seconds`, as M^T M applies per second."""
+def _oracle_cg_rate(name, seconds):
+    """M^T M applies per second of the oracle's FP64 CG on workload `name`,
+    run for about `seconds` (one thread); returns (applies/s, iterations,
+    applies, seconds)."""
     import oracle
+    wl = {w.name: w for w in WORKLOADS.values()}[name]
     lat = oracle.lattice(wl.d, wl.nx, wl.ntau)
     n = wl.nsites
     sigma = workloads.sigma_field(n, seed=wl.seed)
@@ -212,9 +214,29 @@ def cpu_baseline(wl, seconds=15.0):
     _, st, it, rr = oracle.cg(lat, h, L, b, 1e-10, iters)
     dt = time.perf_counter() - t0
     applies = it + 1  # it CG steps + one final true-residual apply
-    return {"value": applies / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "oracle FP64 CG on the %s lattice (seed %d): %d CG iterations (%d M^T M applies) in %.1f s, single thread"
-                      % (wl.name, wl.seed, it, applies, dt)}
+    return applies / dt, it, applies, dt
+
+
+def cpu_baseline(wl, seconds=15.0, all_cores=True):
+    """The oracle, as it stands, on this host: CG iterations on the same
+    lattice and field for about `seconds`, as M^T M applies per second, on
+    one thread; with all_cores, also one copy of that run per host core at
+    once (spawned processes, the oracle unchanged) and their summed rate."""
+    rate, it, applies, dt = _oracle_cg_rate(wl.name, seconds)
+    out = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "oracle FP64 CG on the %s lattice (seed %d): %d CG iterations (%d M^T M applies) in %.1f s, single thread"
+                     % (wl.name, wl.seed, it, applies, dt)}
+    if all_cores:
+        import multiprocessing as mp
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        ctx = mp.get_context("spawn")   # the parent has used the GPU: no fork
+        with ctx.Pool(cores) as pool:
+            res = pool.starmap(_oracle_cg_rate, [(wl.name, seconds)] * cores)
+        out["all_cores"] = {"value": float(sum(r[0] for r in res)), "unit": UNIT, "cores": cores,
+                            "kind": "oracle",
+                            "sample": "%d concurrent copies of the single-thread run, one per host core, rates summed"
+                                      % cores}
+    return out
 
 
 def run_reference(args, wl, world, rank):
@@ -223,11 +245,11 @@ def run_reference(args, wl, world, rank):
         return
     per_step = max(2.0, 40.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        cpu_baseline(wl, seconds=min(per_step, 3.0))
+        cpu_baseline(wl, seconds=min(per_step, 3.0), all_cores=False)
     vals, samples = [], []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        r = cpu_baseline(wl, seconds=per_step)
+        r = cpu_baseline(wl, seconds=per_step, all_cores=False)
         vals.append(r["value"])
         samples.append(r["sample"])
     wall = time.perf_counter() - t0
@@ -671,6 +693,7 @@ def main():
         "q_applies_per_solve": applies / max(1, cnt["solves"]),
         "acceptance": float(np.mean([i["accepted"] for i in infos])),
         "dH": [i["dH"] for i in infos],
+        "exp_minus_dH_mean": float(np.mean([np.exp(-i["dH"]) for i in infos])),
         "max_true_relres": max(i["max_true_relres"] for i in infos),
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
         "gpu_launches": int(cnt["kernel_launches"]),
