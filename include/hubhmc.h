@@ -216,6 +216,38 @@ int hh_action(hh_ctx *ctx, const double *chi, int n_rhs, double *S, hh_solve_inf
  * Errors: HH_EINVAL (n_md < 1), solver errors as in hh_solve. */
 int hh_trajectory(hh_ctx *ctx, int n_md, double dt, uint64_t traj_index, hh_traj_info *info);
 
+/* Observables: noise estimators of the diagonal of M^{-1}.  For the block
+ * form of Eq. (7) (link_order 1, 2) the diagonal blocks of M^{-1} are the
+ * equal-time Green's functions (1 + B_tau ... B_{tau+1})^{-1}, so 1 -
+ * M^{-1}_ii is the occupation of one spin state at site i and slice tau; for
+ * reading R1 (link_order 0, M = e^{dtau K} times that form to first order)
+ * the diagonal carries an O(dtau) admixture of the nearest-neighbour Green's
+ * function.  The paper names no observables; these are the standard
+ * stochastic estimators.
+ *
+ * n_noise (even, 2..64) Z2 vectors eta_k: element i is +1 when the top bit of
+ * word i & 3 of Philox block i >> 2 (tag 6, a = k, trajectory traj, the
+ * context's chain) is set, else -1.  y_k = M^{-1} eta_k = Q^{-1} M^T eta_k by
+ * the context's solver (precision, preconditioner as set), in groups of at
+ * most max(n_pf, 4) right-hand sides.  The field is the context's current
+ * sigma.  Synchronises.  Errors: HH_EINVAL (out NULL, n_noise odd or out of
+ * range), HH_ENOMEM, solver errors as in hh_solve. */
+typedef struct {
+    double trace_Minv;      /* mean over k of (1/N) eta_k . y_k: unbiased for (1/N) tr M^{-1} */
+    double trace_err;       /* its standard error (sample deviation / sqrt(n_noise)) */
+    double one_minus_g_sq;  /* (1/N) sum_i (1 - gA_i)(1 - gB_i), gA and gB the means of
+                               eta_k(i) y_k(i) over the first and second half of the
+                               vectors: unbiased for (1/N) sum_i (1 - M^{-1}_ii)^2, the
+                               double occupancy when 1 - M^{-1}_ii is the occupation */
+    double mean_sin;        /* (1/N) sum_i sin sigma_i */
+    double mean_sin2;       /* (1/N) sum_i sin^2 sigma_i */
+    int n_noise;
+    int cg_iterations;      /* largest CG iteration count over the solve groups */
+    double max_true_relres; /* largest true relative residual of the solves */
+} hh_obs_info;
+
+int hh_observables(hh_ctx *ctx, int n_noise, uint64_t traj, hh_obs_info *out);
+
 /* Leapfrog only, on caller-owned fields: integrates (sigma_ctx, pi) for n_md
  * steps of size dt at fixed chi (device, n_rhs * N), updating the context's
  * sigma and the device array pi (N doubles) in place.  No Metropolis step. */
@@ -247,8 +279,8 @@ int hh_counters_get(hh_ctx *ctx, hh_counters *out);
 
 /* ---- Batched multi-chain engine and serving loop ---------------------------
  * Many independent Markov chains and solves, of different lattices, share one
- * persistent CG launch (the a12/a13 patterns of the build: not in the paper,
- * whose Sec. 5 runs one lattice at a time).  Requests are admitted into slots
+ * persistent CG launch (an extension: the paper's Sec. 5 runs one lattice at
+ * a time).  Requests are admitted into slots
  * while the HBM budget and the active-site window allow, each slot's state
  * stays resident on the device, and the engine advances every active system
  * by 'chunk_iters' CG iterations per launch (a CUDA-graph replay).  Between

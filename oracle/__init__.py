@@ -270,6 +270,27 @@ def trajectory(lat, prm, sigma, n_md, dt, traj):
     return sigma, info.as_dict()
 
 
+def z2_noise(seed, k, traj, chain, n):
+    """Z2 noise vector k of the observables (Philox tag 6)."""
+    out = np.empty(n)
+    lib().oracle_z2_noise(ctypes.c_uint64(seed), ctypes.c_int(k), ctypes.c_uint64(traj), ctypes.c_uint64(chain),
+                          ctypes.c_long(n), _ptr(out))
+    return out
+
+
+def observables(lat, prm, sigma, n_noise, traj):
+    """Noise estimators (reading R13); returns a dict with trace_Minv (mean of
+    (1/N) eta_k . M^{-1} eta_k), trace_err, one_minus_g_sq, mean_sin,
+    mean_sin2, cg_iterations, max_relres, status."""
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    out = np.zeros(5)
+    it, rr = ctypes.c_int(0), ctypes.c_double(0.0)
+    st = lib().oracle_observables(ctypes.byref(lat), ctypes.byref(prm), _ptr(sigma), ctypes.c_int(n_noise),
+                                  ctypes.c_uint64(traj), _ptr(out), ctypes.byref(it), ctypes.byref(rr))
+    return {"trace_Minv": out[0], "trace_err": out[1], "one_minus_g_sq": out[2], "mean_sin": out[3],
+            "mean_sin2": out[4], "cg_iterations": it.value, "max_relres": rr.value, "status": st}
+
+
 def dense(lat, h, L, which="M", order=0):
     """Dense matrix of M, M^T or M^T M built column by column (small lattices only)."""
     n = nsites(lat)

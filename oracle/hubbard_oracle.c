@@ -30,7 +30,11 @@
  *      u < exp(-dH).
  *   R7 (random numbers, not specified by the paper): Philox4x64-10 with
  *      counter (block, tag | a<<8, traj, chain) and key (seed, 0);
- *      tags 0 sigma init, 1 momenta, 2 pseudofermion sources, 3 Metropolis.
+ *      tags 0 sigma init, 1 momenta, 2 pseudofermion sources, 3 Metropolis,
+ *      6 observable noise.
+ *   R13 (observables, none named by the paper): noise estimators of
+ *      diag(M^{-1}), whose diagonal blocks are the equal-time Green's
+ *      functions (1 + B_tau ... B_{tau+1})^{-1} of the block form of Eq. (7).
  */
 #include "hubbard_oracle.h"
 
@@ -800,5 +804,81 @@ int oracle_trajectory(const oracle_lattice *lat, const oracle_params *p, double 
     free(pi);
     free(chi);
     free(sigma0);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Observables (reading R13).                                                */
+/* ------------------------------------------------------------------------ */
+
+/* Z2 noise vector k: element i is +1 if the top bit of word i & 3 of Philox
+ * block i >> 2 (tag 6, a = k) is set, else -1. */
+void oracle_z2_noise(uint64_t seed, int k, uint64_t traj, uint64_t chain, long n, double *eta)
+{
+    for (long i = 0; i < n; ++i) {
+        uint64_t w[4];
+        philox_block(seed, 6, k, traj, chain, (uint64_t)i >> 2, w);
+        eta[i] = (w[i & 3] >> 63) ? 1.0 : -1.0;
+    }
+}
+
+/* With n_noise Z2 vectors eta_k and y_k = M^{-1} eta_k = Q^{-1} (M^T eta_k)
+ * (a CG solve on Q, the form of M given by p->link_order):
+ *   t_k = (1/N) eta_k . y_k  estimates (1/N) tr M^{-1} without bias;
+ *   g_A(i), g_B(i) = the means of eta_k(i) y_k(i) over the first and the
+ *   second half of the vectors estimate M^{-1}_ii independently, so
+ *   (1/N) sum_i (1 - g_A(i)) (1 - g_B(i)) estimates (1/N) sum_i (1 - M^{-1}_ii)^2.
+ * out[0] = mean of t_k, out[1] = its standard error (sample deviation over
+ * sqrt(n_noise)), out[2] = the product estimate, out[3] = (1/N) sum sin sigma,
+ * out[4] = (1/N) sum sin^2 sigma.  n_noise must be even and >= 2. */
+int oracle_observables(const oracle_lattice *lat, const oracle_params *p, const double *sigma,
+                       int n_noise, uint64_t traj, double *out, int *iters, double *relres)
+{
+    long n = oracle_nsites(lat);
+    int half = n_noise / 2, status = 0;
+    double h = p->t * p->dtau;
+    double *L = (double *)malloc(sizeof(double) * (size_t)n);
+    double *eta = (double *)malloc(sizeof(double) * (size_t)n);
+    double *rhs = (double *)malloc(sizeof(double) * (size_t)n);
+    double *y = (double *)malloc(sizeof(double) * (size_t)n);
+    double *gA = (double *)calloc((size_t)n, sizeof(double));
+    double *gB = (double *)calloc((size_t)n, sizeof(double));
+    double *t = (double *)malloc(sizeof(double) * (size_t)n_noise);
+    oracle_links(lat, p->A, sigma, L);
+    for (int k = 0; k < n_noise; ++k) {
+        int it;
+        double rr;
+        oracle_z2_noise(p->seed, k, traj, p->chain, n, eta);
+        oracle_apply_MT_ex(lat, h, L, p->link_order, eta, rhs);
+        int st = oracle_cg_ex(lat, h, L, p->link_order, rhs, y, 0, p->cg_tol, p->cg_maxit, &it, &rr);
+        if (st != 0) status = st;
+        *iters += it;
+        if (rr > *relres) *relres = rr;
+        t[k] = dot(n, eta, y) / (double)n;
+        double *g = k < half ? gA : gB;
+        for (long i = 0; i < n; ++i) g[i] += eta[i] * y[i] / (double)half;
+    }
+    double mean = 0.0, var = 0.0, prod = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int k = 0; k < n_noise; ++k) mean += t[k];
+    mean /= (double)n_noise;
+    for (int k = 0; k < n_noise; ++k) var += (t[k] - mean) * (t[k] - mean);
+    var /= (double)(n_noise - 1);
+    for (long i = 0; i < n; ++i) {
+        prod += (1.0 - gA[i]) * (1.0 - gB[i]);
+        s1 += sin(sigma[i]);
+        s2 += sin(sigma[i]) * sin(sigma[i]);
+    }
+    out[0] = mean;
+    out[1] = sqrt(var / (double)n_noise);
+    out[2] = prod / (double)n;
+    out[3] = s1 / (double)n;
+    out[4] = s2 / (double)n;
+    free(L);
+    free(eta);
+    free(rhs);
+    free(y);
+    free(gA);
+    free(gB);
+    free(t);
     return status;
 }

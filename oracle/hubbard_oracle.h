@@ -133,6 +133,12 @@ void oracle_leapfrog(const oracle_lattice *lat, const oracle_params *p, double *
 int oracle_trajectory(const oracle_lattice *lat, const oracle_params *p, double *sigma,
                       int n_md, double dt, uint64_t traj, oracle_traj_info *info);
 
+/* Z2 noise vector k (Philox tag 6) and the noise estimators of (1/N) tr M^{-1}
+ * and (1/N) sum_i (1 - M^{-1}_ii)^2 with the field moments (reading R13). */
+void oracle_z2_noise(uint64_t seed, int k, uint64_t traj, uint64_t chain, long n, double *eta);
+int oracle_observables(const oracle_lattice *lat, const oracle_params *p, const double *sigma,
+                       int n_noise, uint64_t traj, double *out, int *iters, double *relres);
+
 #ifdef __cplusplus
 }
 #endif

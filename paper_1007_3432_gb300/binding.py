@@ -57,6 +57,16 @@ class hh_traj_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class hh_obs_info(ctypes.Structure):
+    _fields_ = [("trace_Minv", ctypes.c_double), ("trace_err", ctypes.c_double),
+                ("one_minus_g_sq", ctypes.c_double), ("mean_sin", ctypes.c_double),
+                ("mean_sin2", ctypes.c_double), ("n_noise", ctypes.c_int), ("cg_iterations", ctypes.c_int),
+                ("max_true_relres", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class hh_counters(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_longlong), ("engine_launches", ctypes.c_longlong),
                 ("engine_ms", ctypes.c_double), ("cg_steps", ctypes.c_longlong),
@@ -125,6 +135,7 @@ def load(path: str = LIB_PATH):
         "hh_force": (i, [vp, vp, i, vp, ctypes.POINTER(hh_solve_info)]),
         "hh_action": (i, [vp, vp, i, ctypes.POINTER(d), ctypes.POINTER(hh_solve_info)]),
         "hh_trajectory": (i, [vp, i, d, u64, ctypes.POINTER(hh_traj_info)]),
+        "hh_observables": (i, [vp, i, u64, ctypes.POINTER(hh_obs_info)]),
         "hh_leapfrog": (i, [vp, vp, vp, i, i, d, ctypes.POINTER(hh_solve_info)]),
         "hh_counters_reset": (i, [vp, i]),
         "hh_counters_get": (i, [vp, ctypes.POINTER(hh_counters)]),
@@ -287,6 +298,12 @@ class Context:
         rc = self._lib.hh_trajectory(self._h, n_md, dt, traj_index, ctypes.byref(inf) if info else None)
         check(rc, "hh_trajectory", allow)
         return inf.as_dict() if info else None
+
+    def observables(self, n_noise, traj=0):
+        """Noise estimators of diag M^{-1} at the current field (hh_observables)."""
+        inf = hh_obs_info()
+        check(self._lib.hh_observables(self._h, n_noise, traj, ctypes.byref(inf)), "hh_observables")
+        return inf.as_dict()
 
     def counters_reset(self, profile_engine=False):
         check(self._lib.hh_counters_reset(self._h, int(bool(profile_engine))), "hh_counters_reset")

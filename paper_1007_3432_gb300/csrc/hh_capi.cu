@@ -152,6 +152,10 @@ struct hh_ctx {
                             // fused FP32 d = 3 kernel where it applies
     double *z, *u;          // Chebyshev preconditioner vectors (cap_rhs each), or null
     double *d_cheb;         // its coefficient table
+    // Observables: noise, M^T noise and solutions (obs_cap vectors each), the
+    // reduction partials and the five results.
+    double *obs_eta, *obs_rhs, *obs_y, *obs_part, *obs_out;
+    int obs_cap;
 };
 
 namespace {
@@ -184,6 +188,8 @@ void free_ctx(hh_ctx *c)
     if (c->z) cudaFree(c->z);
     if (c->u) cudaFree(c->u);
     if (c->d_cheb) cudaFree(c->d_cheb);
+    for (double *p : {c->obs_eta, c->obs_rhs, c->obs_y, c->obs_part, c->obs_out})
+        if (p) cudaFree(p);
     if (c->ev) {
         for (int i = 0; i < c->ev_cap; ++i)
             if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -760,6 +766,59 @@ int hh_action(hh_ctx *c, const double *chi, int n_rhs, double *S, hh_solve_info 
     HH_TRY(cudaMemcpy(S, c->d_energy_out, sizeof(double), cudaMemcpyDeviceToHost));
     fill_solve_info(s, info);
     return stats_status(s);
+}
+
+int hh_observables(hh_ctx *c, int n_noise, uint64_t traj, hh_obs_info *out)
+{
+    if (!c || !out || n_noise < 2 || n_noise > kObsMaxNoise || (n_noise & 1)) return HH_EINVAL;
+    const size_t N = (size_t)c->N;
+    if (c->obs_cap < n_noise) {
+        for (double **p : {&c->obs_eta, &c->obs_rhs, &c->obs_y, &c->obs_part, &c->obs_out}) {
+            if (*p) cudaFree(*p);
+            *p = nullptr;
+        }
+        c->obs_cap = 0;
+        cudaError_t e = dalloc(&c->obs_eta, N * n_noise);
+        if (e == cudaSuccess) e = dalloc(&c->obs_rhs, N * n_noise);
+        if (e == cudaSuccess) e = dalloc(&c->obs_y, N * n_noise);
+        if (e == cudaSuccess) e = dalloc(&c->obs_part, (size_t)(n_noise + 3) * energy_blocks(c->N));
+        if (e == cudaSuccess) e = dalloc(&c->obs_out, 8);
+        if (e != cudaSuccess) return HH_ENOMEM;
+        c->obs_cap = n_noise;
+    }
+    const double h = c->prm.t * c->prm.dtau;
+    HH_TRY(launch_z2_noise(c->obs_eta, c->N, n_noise, c->prm.seed, traj, c->prm.chain_id, c->stream));
+    for (int k = 0; k < n_noise; ++k)
+        HH_TRY(launch_apply_f64(c->geo, 1, h, c->L64, c->obs_eta + k * N, c->obs_rhs + k * N, c->stream,
+                                c->prm.link_order));
+    c->n_launch += 1 + n_noise;
+    // y_k = Q^{-1} M^T eta_k, in groups of at most cap_rhs right-hand sides.
+    int iters = 0;
+    double relres = 0.0;
+    for (int k0 = 0; k0 < n_noise; k0 += c->cap_rhs) {
+        const int m = n_noise - k0 < c->cap_rhs ? n_noise - k0 : c->cap_rhs;
+        hh_solve_info si;
+        int rc = solve_from(c, c->obs_rhs + k0 * N, c->obs_y + k0 * N, m, 0, &si);
+        if (rc) return rc;
+        if (si.iterations > iters) iters = si.iterations;
+        if (si.true_relres > relres) relres = si.true_relres;
+    }
+    HH_TRY(launch_observables(c->N, n_noise, c->obs_eta, c->obs_y, c->sigma, c->obs_part, c->obs_out,
+                              c->stream));
+    c->n_launch += 2;
+    double r[5];
+    HH_TRY(cudaMemcpyAsync(c->h_pinned, c->obs_out, sizeof(r), cudaMemcpyDeviceToHost, c->stream));
+    HH_TRY(cudaStreamSynchronize(c->stream));
+    memcpy(r, c->h_pinned, sizeof(r));
+    out->trace_Minv = r[0];
+    out->trace_err = r[1];
+    out->one_minus_g_sq = r[2];
+    out->mean_sin = r[3];
+    out->mean_sin2 = r[4];
+    out->n_noise = n_noise;
+    out->cg_iterations = iters;
+    out->max_true_relres = relres;
+    return HH_OK;
 }
 
 }  // extern "C"

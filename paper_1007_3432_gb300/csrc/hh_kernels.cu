@@ -172,6 +172,93 @@ __global__ void k_sum_partials(const double *__restrict__ part, int nb, double *
     if (threadIdx.x == 0) *out = v;
 }
 
+// Z2 noise of the observables: vector k = blockIdx.y (+ gridDim.y steps) at
+// out + k n; element i is +1 when the top bit of word i & 3 of Philox block
+// i >> 2 (tag 6, a = k) is set, else -1.
+__global__ void k_z2_noise(double *__restrict__ out, int n, int nvec, uint64_t seed, uint64_t traj,
+                           uint64_t chain)
+{
+    const int nblk = (n + 3) >> 2;
+    for (int k = blockIdx.y; k < nvec; k += gridDim.y) {
+        const uint64_t ctr1 = 6u | ((uint64_t)k << 8);
+        double *o = out + (size_t)k * n;
+        for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+            U64x4 w = philox4x64_10((uint64_t)b, ctr1, traj, chain, seed, 0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = 4 * b + j;
+                if (i < n) o[i] = (w.v[j] >> 63) ? 1.0 : -1.0;
+            }
+        }
+    }
+}
+
+// Block partials of the observables: for blockIdx.y = k < nvec the dot
+// eta_k . y_k into part[k nb + b]; for blockIdx.y = nvec the site sums of
+// (1 - gA)(1 - gB), sin sigma and sin^2 sigma into part[(nvec + j) nb + b],
+// gA and gB being the means of eta_k y_k over the first and second halves of
+// the vectors.
+__global__ void k_obs_partials(int n, int nvec, const double *__restrict__ eta, const double *__restrict__ y,
+                               const double *__restrict__ sigma, double *__restrict__ part)
+{
+    __shared__ double red[kBlock / 32];
+    const int nb = gridDim.x, k = blockIdx.y;
+    if (k < nvec) {
+        const double *e = eta + (size_t)k * n, *v = y + (size_t)k * n;
+        double acc = 0.0;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nb * blockDim.x) acc = fma(e[i], v[i], acc);
+        const double tot = block_sum(acc, red);
+        if (threadIdx.x == 0) part[(size_t)k * nb + blockIdx.x] = tot;
+        return;
+    }
+    const int half = nvec / 2;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nb * blockDim.x) {
+        double gA = 0.0, gB = 0.0;
+        for (int q = 0; q < half; ++q) gA = fma(eta[(size_t)q * n + i], y[(size_t)q * n + i], gA);
+        for (int q = half; q < nvec; ++q) gB = fma(eta[(size_t)q * n + i], y[(size_t)q * n + i], gB);
+        gA /= half;
+        gB /= half;
+        a0 = fma(1.0 - gA, 1.0 - gB, a0);
+        const double sn = sin(sigma[i]);
+        a1 += sn;
+        a2 = fma(sn, sn, a2);
+    }
+    double tot = block_sum(a0, red);
+    if (threadIdx.x == 0) part[(size_t)nvec * nb + blockIdx.x] = tot;
+    __syncthreads();
+    tot = block_sum(a1, red);
+    if (threadIdx.x == 0) part[(size_t)(nvec + 1) * nb + blockIdx.x] = tot;
+    __syncthreads();
+    tot = block_sum(a2, red);
+    if (threadIdx.x == 0) part[(size_t)(nvec + 2) * nb + blockIdx.x] = tot;
+}
+
+// One warp: sums each quantity's nb partials in a fixed order and writes
+// out[0] = mean over k of t_k = dot_k / n, out[1] = its standard error,
+// out[2..4] = the three site sums over n.
+__global__ void k_obs_finish(const double *__restrict__ part, int nb, int nvec, int n, double *__restrict__ out)
+{
+    __shared__ double q[kObsMaxNoise + 3];
+    for (int j = 0; j < nvec + 3; ++j) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nb; b += 32) v += part[(size_t)j * nb + b];
+        v = warp_sum(v);
+        if (threadIdx.x == 0) q[j] = v / (double)n;
+    }
+    if (threadIdx.x != 0) return;
+    double mean = 0.0, var = 0.0;
+    for (int k = 0; k < nvec; ++k) mean += q[k];
+    mean /= nvec;
+    for (int k = 0; k < nvec; ++k) var += (q[k] - mean) * (q[k] - mean);
+    var /= (nvec - 1);
+    out[0] = mean;
+    out[1] = sqrt(var / nvec);
+    out[2] = q[nvec];
+    out[3] = q[nvec + 1];
+    out[4] = q[nvec + 2];
+}
+
 __global__ void k_metropolis(HmcScalars *sc, uint64_t seed, uint64_t traj, uint64_t chain)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -281,6 +368,26 @@ cudaError_t launch_energy(int n, const double *pi, const double *chi, const doub
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_sum_partials<<<1, 32, 0, st>>>(part, nb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_z2_noise(double *out, int n, int nvec, uint64_t seed, uint64_t traj, uint64_t chain,
+                            cudaStream_t st)
+{
+    dim3 grid(grid_for((n + 3) / 4), nvec);
+    k_z2_noise<<<grid, kBlock, 0, st>>>(out, n, nvec, seed, traj, chain);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_observables(int n, int nvec, const double *eta, const double *y, const double *sigma,
+                               double *part, double *out, cudaStream_t st)
+{
+    if (nvec < 2 || nvec > kObsMaxNoise || (nvec & 1)) return cudaErrorInvalidValue;
+    const int nb = energy_blocks(n);
+    k_obs_partials<<<dim3(nb, nvec + 1), kBlock, 0, st>>>(n, nvec, eta, y, sigma, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_obs_finish<<<1, 32, 0, st>>>(part, nb, nvec, n, out);
     return cudaGetLastError();
 }
 

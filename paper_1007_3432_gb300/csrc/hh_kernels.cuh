@@ -61,6 +61,19 @@ cudaError_t launch_metropolis(HmcScalars *sc, uint64_t seed, uint64_t traj, uint
 cudaError_t launch_restore(const Geo &g, double A, const HmcScalars *sc, double *sigma,
                            const double *sigma0, double *L64, float *L32, cudaStream_t st);
 
+// Observables (noise estimators of diag M^{-1}; see hh_observables).
+// nvec Z2 noise vectors (Philox tag 6, vector k at out + k n).
+constexpr int kObsMaxNoise = 64;
+cudaError_t launch_z2_noise(double *out, int n, int nvec, uint64_t seed, uint64_t traj, uint64_t chain,
+                            cudaStream_t st);
+// From eta_k and y_k = M^{-1} eta_k (k < nvec, even): out[0] = mean of
+// (1/n) eta_k . y_k, out[1] its standard error, out[2] = (1/n) sum_i
+// (1 - gA_i)(1 - gB_i) with gA, gB the half-set means of eta_k y_k, out[3],
+// out[4] = (1/n) sum sin sigma, sin^2 sigma.  part: (nvec + 3) *
+// energy_blocks(n) doubles of scratch.
+cudaError_t launch_observables(int n, int nvec, const double *eta, const double *y, const double *sigma,
+                               double *part, double *out, cudaStream_t st);
+
 // Chronological initial guess by linear extrapolation: x <- 2 x - xp and
 // xp <- the old x, over n elements.
 cudaError_t launch_extrapolate(double *x, double *xp, long long n, cudaStream_t st);

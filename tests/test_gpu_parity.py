@@ -569,3 +569,33 @@ def test_batched_chronological_trajectory_matches_context(hh):
         ctx.set_field(dev(sigma))
         info = ctx.trajectory(4, 0.1, 2)
     assert abs(info["dH"] - r["dH"]) <= 1e-6 and info["u"] == r["u"]
+
+
+@pytest.mark.parametrize("d,nx,ntau,precision,order", [(1, 16, 16, "fp64", 0), (1, 16, 16, "mixed", 0),
+                                                       (3, 4, 8, "fp64", 0), (1, 12, 10, "fp64", 1),
+                                                       (3, 4, 6, "mixed", 2)])
+def test_observables_match_oracle(hh, d, nx, ntau, precision, order):
+    """hh_observables against the oracle's estimators on the same Z2 noise
+    (Philox tag 6): the noise is bit-identical, the solves agree to the CG
+    tolerance, so the estimates agree to the solution error."""
+    lat = oracle.lattice(d, nx, ntau)
+    n = oracle.nsites(lat)
+    sigma = workloads.sigma_field(n, seed=900 + nx)
+    ref = oracle.observables(lat, oracle.params(seed=77, link_order=order), sigma, 6, 2)
+    assert ref["status"] == 0
+    with hh.Context(d, nx, ntau, seed=77, precision=precision, link_order=order) as ctx:
+        ctx.set_field(dev(sigma))
+        got = ctx.observables(6, 2)
+    assert got["n_noise"] == 6 and got["max_true_relres"] <= 1e-10
+    for key in ("trace_Minv", "one_minus_g_sq"):
+        assert abs(got[key] - ref[key]) <= 1e-6 * abs(ref[key]) + 1e-9, key
+    assert abs(got["trace_err"] - ref["trace_err"]) <= 1e-5 * ref["trace_err"] + 1e-9
+    for key in ("mean_sin", "mean_sin2"):
+        assert abs(got[key] - ref[key]) <= 1e-13, key
+
+
+def test_observables_reject_bad_noise_counts(hh):
+    with hh.Context(1, 8, 8) as ctx:
+        for nn in (0, 1, 3, 66):
+            with pytest.raises(hh.HHError):
+                ctx.observables(nn, 0)

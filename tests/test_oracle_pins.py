@@ -720,3 +720,86 @@ def test_exact_block_force_and_cg(orc, order, d, nx, ntau):
     S, *_ = orc.action(lat, prm, sigma, xi_chi)
     Minv_chi = [np.linalg.solve(orc.dense(lat, h, L, "MT", order=order), c) for c in xi_chi]
     assert abs(S - 0.5 * sum(v @ v for v in Minv_chi)) <= 1e-9 * S
+
+
+# --- observables: noise estimators of diag M^{-1} (reading R13) -------------
+
+
+def _free_block_energies(d, nx, h, order):
+    """E_k = 1 + x (+ x^2 / 2), x = 2h sum_j cos k_j: the hopping factor of the
+    exact-block form on a plane wave of lattice momentum k."""
+    out = []
+    for ms in itertools.product(range(nx), repeat=d):
+        x = 2.0 * h * sum(np.cos(2 * np.pi * m / nx) for m in ms)
+        out.append(1.0 + x + (0.5 * x * x if order == 2 else 0.0))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("d,nx,ntau,order", [(1, 8, 8, 1), (1, 6, 10, 2), (3, 3, 4, 1), (3, 4, 6, 2)])
+def test_free_field_trace_is_fermi_dirac(orc, d, nx, ntau, order):
+    """At A = 0 the diagonal of M^{-1} of the block form of Eq. (7) is the free
+    equal-time Green's function: (1/N) tr M^{-1} = (1/V) sum_k 1 / (1 + E_k^N_tau),
+    i.e. one minus the Fermi-Dirac occupation with E_k^N_tau in place of
+    exp(-beta eps_k) (the antiperiodic Matsubara sum of 1 / (1 - E_k e^{-i w})).
+    For reading R1 the trace is sum 1/lambda over the closed-form spectrum."""
+    lat = orc.lattice(d, nx, ntau)
+    n = orc.nsites(lat)
+    L = orc.links(lat, 0.0, np.zeros(n))
+    tr_ex = np.trace(np.linalg.inv(orc.dense(lat, H, L, "M", order=order))) / n
+    E = _free_block_energies(d, nx, H, order)
+    assert abs(tr_ex - np.mean(1.0 / (1.0 + E ** ntau))) < 1e-12
+    tr_r1 = np.trace(np.linalg.inv(orc.dense(lat, H, L, "M"))) / n
+    assert abs(tr_r1 - np.mean(1.0 / _free_eigs(d, nx, ntau, H, 1.0)).real) < 1e-12
+
+
+def test_z2_noise_matches_numpy_philox(orc):
+    for k, traj, chain in [(0, 0, 0), (3, 7, 2)]:
+        eta = orc.z2_noise(11, k, traj, chain, 37)
+        for i in range(37):
+            w = _numpy_philox_block([i >> 2, 6 | (k << 8), traj, chain], [11, 0])
+            assert eta[i] == (1.0 if w[i & 3] >> 63 else -1.0)
+    big = orc.z2_noise(5, 1, 0, 0, 100000)
+    assert set(np.unique(big)) == {-1.0, 1.0} and abs(big.mean()) < 0.02
+
+
+@pytest.mark.parametrize("d,nx,ntau,order", [(1, 8, 8, 0), (1, 6, 6, 1), (3, 3, 4, 0), (3, 3, 4, 2)])
+def test_observable_estimators_match_dense_inverse(orc, d, nx, ntau, order):
+    """Every term of the estimators against the dense inverse, with the same
+    noise vectors: t_k = (1/N) eta_k . M^{-1} eta_k, the half-set diagonal
+    estimates and the field moments."""
+    lat = orc.lattice(d, nx, ntau)
+    n = orc.nsites(lat)
+    prm = orc.params(cg_tol=1e-13, seed=21, link_order=order)
+    sigma = orc.init_field(21, 0, n)
+    Minv = np.linalg.inv(orc.dense(lat, H, orc.links(lat, 0.5, sigma), "M", order=order))
+    nn = 6
+    etas = [orc.z2_noise(21, k, 3, 0, n) for k in range(nn)]
+    t = np.array([e @ Minv @ e / n for e in etas])
+    g = [e * (Minv @ e) for e in etas]
+    gA, gB = np.mean(g[: nn // 2], axis=0), np.mean(g[nn // 2:], axis=0)
+    got = orc.observables(lat, prm, sigma, nn, 3)
+    assert got["status"] == 0
+    assert abs(got["trace_Minv"] - t.mean()) < 1e-9
+    assert abs(got["trace_err"] - t.std(ddof=1) / np.sqrt(nn)) < 1e-9
+    assert abs(got["one_minus_g_sq"] - np.mean((1 - gA) * (1 - gB))) < 1e-9
+    assert abs(got["mean_sin"] - np.mean(np.sin(sigma))) < 1e-14
+    assert abs(got["mean_sin2"] - np.mean(np.sin(sigma) ** 2)) < 1e-14
+
+
+def test_observable_estimators_are_unbiased(orc):
+    """Over many noise vectors the estimates approach the exact trace and
+    (1/N) sum_i (1 - M^{-1}_ii)^2 of the dense inverse (within 5 standard
+    errors; the product's error from the spread over independent runs)."""
+    lat = orc.lattice(1, 6, 8)
+    n = orc.nsites(lat)
+    prm = orc.params(cg_tol=1e-12, seed=4)
+    sigma = orc.init_field(4, 0, n)
+    Minv = np.linalg.inv(orc.dense(lat, H, orc.links(lat, 0.5, sigma), "M"))
+    exact_tr = np.trace(Minv) / n
+    exact_p = np.mean((1 - np.diag(Minv)) ** 2)
+    runs = [orc.observables(lat, prm, sigma, 32, traj) for traj in range(8)]
+    tr = np.array([r["trace_Minv"] for r in runs])
+    err = np.sqrt(np.sum([r["trace_err"] ** 2 for r in runs])) / len(runs)
+    assert abs(tr.mean() - exact_tr) < 5 * err
+    p = np.array([r["one_minus_g_sq"] for r in runs])
+    assert abs(p.mean() - exact_p) < 5 * p.std(ddof=1) / np.sqrt(len(p))
