@@ -62,9 +62,13 @@ def flops_per_site(d, kind, precision):
 # Bytes per site: a CG step reads r, p, p, L, t, L, x, p, r and writes p, t,
 # x, r (13 words); the minimum for one M^T M apply is x, L in and y out.
 def bytes_per_site(kind, precision):
+    """Algorithmic bytes per site of a CG step (13 words; with 16-bit links the
+    two link reads take 2 bytes each) or of an FP64 true-residual step."""
     if kind == "cg":
-        return 13 * (8 if precision == "fp64" else 4)
-    return 8 * 8 + (12 if precision == "mixed" else 0)
+        if precision == "fp64":
+            return 13 * 8
+        return 13 * 4 - (4 if precision.endswith("16link") else 0)
+    return 8 * 8 + (12 if precision != "fp64" else 0)
 
 
 # DRAM bytes per engine iteration (two right-hand sides) of the engine kernel
@@ -306,7 +310,7 @@ def run_part(args, wl, world, rank, local, dev, stream):
         x_h = torch.empty(b.shape, dtype=torch.float64).pin_memory()
         b_pin = torch.from_numpy(b_h).pin_memory()
     else:
-        dt = torch.float32 if args.precision == "mixed" else torch.float64
+        dt = torch.float64 if args.precision == "fp64" else torch.float32
         xs = torch.from_numpy(workloads.source(n, seed=wl.seed, chain=rank)).to(dev).to(dt)
         ys = torch.empty_like(xs)
 
@@ -359,7 +363,8 @@ def run_part(args, wl, world, rank, local, dev, stream):
                     "frac": ach / fp64_peak_tflops(), "traffic": engine_traffic(wl, args.precision, args.cheb, cnt),
                     "kernel": "engine_kernel (FP64 CG)"}
         else:
-            byts = n * (cnt["cg_steps"] * bytes_per_site("cg", "mixed") + cnt["ru_steps"] * bytes_per_site("ru", "mixed"))
+            byts = n * (cnt["cg_steps"] * bytes_per_site("cg", args.precision)
+                        + cnt["ru_steps"] * bytes_per_site("ru", args.precision))
             ach = byts / eng_s / 1e9
             roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": ach / peaks["hbm_gbs"], "traffic": engine_traffic(wl, args.precision, args.cheb, cnt),
@@ -371,13 +376,13 @@ def run_part(args, wl, world, rank, local, dev, stream):
     else:
         units = float(world * args.steps)
         unit = "MTM applies/s"
-        bps = 12 if args.precision == "mixed" else 24
+        bps = 24 if args.precision == "fp64" else 12
         ach = units / world * n * bps / t_dev / 1e9 * world
         roof = {"bound": "hbm", "achieved": ach / world, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / world / peaks["hbm_gbs"],
                 # one ncu capture of the apply's two sweeps (profiles/mtm_sweeps_d3_nx32_nt128_fp32.md)
                 "traffic": (33557760 + 344320 + 88320 + 6871040) if (wl.name == "d3_nx32_nt128" and args.precision == "mixed") else None,
-                "kernel": "M^T M apply (%s)" % ("FP32" if args.precision == "mixed" else "FP64"),
+                "kernel": "M^T M apply (%s)" % ("FP64" if args.precision == "fp64" else "FP32"),
                 "algorithmic_bytes_per_site": bps}
         extra = {"median_apply_us": 1000.0 * float(np.median(dev_ms))}
         e2e_bytes = (0, 0)
@@ -559,7 +564,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed-bf16link", "mixed-fix16link"],
+                    help="mixed-*16link: 16-bit links in the FP32 steps (solve and trajectory modes)")
     ap.add_argument("--n-md", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
@@ -674,7 +680,8 @@ def main():
                 "peak_source": "FP64 from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz)",
                 "launch_ms": per_launch * 1000.0}
     else:
-        byts = n * (cnt["cg_steps"] * bytes_per_site("cg", "mixed") + cnt["ru_steps"] * bytes_per_site("ru", "mixed"))
+        byts = n * (cnt["cg_steps"] * bytes_per_site("cg", args.precision)
+                    + cnt["ru_steps"] * bytes_per_site("ru", args.precision))
         achieved = byts / eng_s / 1e9 if eng_s > 0 else 0.0
         peak = peaks["hbm_gbs"]
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -59,9 +59,22 @@ extern "C" {
  *             per thread in FP32 and across threads in FP64) with reliable
  *             updates that accumulate the solution and recompute the true
  *             residual b - Q x in FP64; the stopping test is on that FP64 true
- *             residual, so both modes meet the same tolerance. */
+ *             residual, so both modes meet the same tolerance.
+ *   HH_MIXED_BF16LINK, HH_MIXED_FIX16LINK: HH_MIXED with the links of the
+ *             FP32 steps stored in 16 bits (2 bytes per site fewer per
+ *             stencil sweep): the bfloat16 rounding of the FP32 link (8
+ *             significant bits), or a fixed-point code c with L = c * 2^-e,
+ *             e = 14 while (1 + |A|) 2^14 fits in 15 bits (absolute error
+ *             <= 2^-(e+1)).  The reliable updates use the FP64 links, so the
+ *             result meets the same tolerance; the inner iteration solves a
+ *             perturbed system, which costs extra reliable updates once
+ *             cond(Q) times the link error approaches reliable_delta
+ *             (bfloat16 on hot lattices of cond(Q) ~ 1e4 and above).
+ *             Contexts with link_order 0 only. */
 #define HH_FP64 0
 #define HH_MIXED 1
+#define HH_MIXED_BF16LINK 2
+#define HH_MIXED_FIX16LINK 3
 
 /* Operators for hh_apply. */
 #define HH_OP_M 0   /* y = M x */
@@ -84,7 +97,7 @@ typedef struct {
     double t;              /* hopping amplitude; h = t * dtau */
     double dtau;           /* Trotter time step */
     double A;              /* auxiliary-field coupling in 1 + A sin(sigma) */
-    int precision;         /* HH_FP64 or HH_MIXED */
+    int precision;         /* HH_FP64, HH_MIXED, HH_MIXED_BF16LINK or HH_MIXED_FIX16LINK */
     double cg_tol;         /* stop when ||b - Q x||_2 <= cg_tol * ||b||_2 */
     int cg_maxit;          /* cap on CG iterations per solve */
     double reliable_delta; /* HH_MIXED: reliable update when ||r|| < delta * max ||r|| */

@@ -16,7 +16,9 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "hubhmc.h")
 HH_OK, HH_EINVAL, HH_ENOMEM, HH_ECUDA = 0, -1, -2, -3
 HH_ENOCONV, HH_ENUMERIC, HH_ETIMEOUT, HH_EBUSY, HH_ESIZE = -4, -5, -6, -7, -8
 HH_NOALLOC_MAX_SITES = 262144
-HH_FP64, HH_MIXED = 0, 1
+HH_FP64, HH_MIXED, HH_MIXED_BF16LINK, HH_MIXED_FIX16LINK = 0, 1, 2, 3
+PRECISIONS = {"fp64": HH_FP64, "mixed": HH_MIXED, "mixed-bf16link": HH_MIXED_BF16LINK,
+              "mixed-fix16link": HH_MIXED_FIX16LINK}
 HH_OP_M, HH_OP_MT, HH_OP_MTM = 0, 1, 2
 HH_DTYPE_F64, HH_DTYPE_F32 = 0, 1
 
@@ -210,7 +212,7 @@ class Context:
         p = hh_params()
         L.hh_default_params(ctypes.byref(p))
         p.t, p.dtau, p.A = t, dtau, A
-        p.precision = {"fp64": HH_FP64, "mixed": HH_MIXED}.get(precision, precision)
+        p.precision = PRECISIONS.get(precision, precision)
         p.cg_tol, p.cg_maxit, p.reliable_delta = cg_tol, cg_maxit, reliable_delta
         p.seed, p.n_pf, p.chain_id = seed, n_pf, chain_id
         p.cheb_degree, p.cheb_eps = cheb_degree, cheb_eps
@@ -336,7 +338,7 @@ def make_params(t=1.0, dtau=0.05, A=0.5, precision=HH_FP64, cg_tol=1e-10, cg_max
     p = hh_params()
     L.hh_default_params(ctypes.byref(p))
     p.t, p.dtau, p.A = t, dtau, A
-    p.precision = {"fp64": HH_FP64, "mixed": HH_MIXED}.get(precision, precision)
+    p.precision = PRECISIONS.get(precision, precision)
     p.cg_tol, p.cg_maxit, p.reliable_delta = cg_tol, cg_maxit, reliable_delta
     p.seed, p.n_pf, p.chain_id = seed, n_pf, chain_id
     p.cheb_degree, p.cheb_eps = cheb_degree, cheb_eps

@@ -156,6 +156,10 @@ struct hh_ctx {
     // reduction partials and the five results.
     double *obs_eta, *obs_rhs, *obs_y, *obs_part, *obs_out;
     int obs_cap;
+    // 16-bit links of the FP32 steps (HH_MIXED_BF16LINK / HH_MIXED_FIX16LINK).
+    unsigned short *L16;
+    int l16_mode;           // 0 none, 1 bfloat16, 2 fixed point
+    double l16_scale;       // fixed point: L = code * l16_scale
 };
 
 namespace {
@@ -190,6 +194,7 @@ void free_ctx(hh_ctx *c)
     if (c->d_cheb) cudaFree(c->d_cheb);
     for (double *p : {c->obs_eta, c->obs_rhs, c->obs_y, c->obs_part, c->obs_out})
         if (p) cudaFree(p);
+    if (c->L16) cudaFree(c->L16);
     if (c->ev) {
         for (int i = 0; i < c->ev_cap; ++i)
             if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -209,7 +214,8 @@ int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
     // takes longer than the control warp's wait, decision and publication
     // (about 3.5 us on GB300): FP64 systems from 2^18 sites, mixed ones from
     // 2^21.  Otherwise the systems share the grid, one tile per block.
-    const bool overlap = engine_overlap(n_rhs, c->N, c->prm.precision == HH_MIXED);
+    const bool mixed = c->prm.precision != HH_FP64;
+    const bool overlap = engine_overlap(n_rhs, c->N, mixed);
     Tiling tl = engine_tiling(c->N, overlap ? 1 : n_rhs, c->max_grid);
     int ntiles = tl.tiles * n_rhs;
     if (ntiles > c->max_tiles) return HH_EINVAL;
@@ -217,7 +223,7 @@ int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
     // Bytes the CG iteration streams per site: x, r, p, t, b, the links and
     // the second p buffer in FP64 (and z, u with the preconditioner); r, p,
     // t, x, links, p' in FP32 (mixed).
-    const long long site_bytes = c->prm.precision == HH_MIXED ? 24 : (c->prm.cheb_degree > 0 ? 72 : 56);
+    const long long site_bytes = mixed ? 24 : (c->prm.cheb_degree > 0 ? 72 : 56);
     const int pf = engine_prefetch(site_bytes * (long long)c->N * n_rhs, c->lat.d);
     std::vector<EngSystem> sys(n_rhs);
     std::vector<EngTile> tiles;
@@ -254,7 +260,10 @@ int make_plan(hh_ctx *c, const double *b, double *x, int n_rhs)
         Y.ntiles = (int)tiles.size() - Y.tile0;
         Y.part0 = Y.tile0;
         Y.owner = overlap ? a % grid : Y.tile0 % grid;
-        Y.precision = c->prm.precision;
+        Y.precision = mixed ? PREC_MIXED : PREC_FP64;
+        Y.L16 = c->L16;
+        Y.link16 = c->l16_mode;
+        Y.l16_scale = (float)c->l16_scale;
         Y.tol2 = c->prm.cg_tol * c->prm.cg_tol;
         Y.delta2 = c->prm.reliable_delta * c->prm.reliable_delta;
         Y.maxit = c->prm.cg_maxit;
@@ -388,6 +397,13 @@ bool aligned16(const void *p)
     return ((uintptr_t)p & 15u) == 0;
 }
 
+// After every change of the links: the 16-bit copy read by the FP32 steps.
+cudaError_t links16_after(hh_ctx *c)
+{
+    if (!c->l16_mode) return cudaSuccess;
+    return launch_links16(c->N, c->L64, c->L16, c->l16_mode, c->l16_scale, c->stream);
+}
+
 }  // namespace
 
 extern "C" {
@@ -434,7 +450,11 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
     if (lat->d != 1 && lat->d != 3) return HH_EINVAL;
     if (lat->nx < 2 || lat->ntau < 2) return HH_EINVAL;
     if (p->n_pf < 1 || p->n_pf > 64) return HH_EINVAL;
-    if (p->precision != HH_FP64 && p->precision != HH_MIXED) return HH_EINVAL;
+    if (p->precision < HH_FP64 || p->precision > HH_MIXED_FIX16LINK) return HH_EINVAL;
+    // 16-bit links: the fixed-point scale needs (1 + |A|) < 2^15, and the
+    // exact-block loops read FP32 links only.
+    if (p->precision >= HH_MIXED_BF16LINK && (p->link_order != 0 || !(fabs(p->A) < 32766.0)))
+        return HH_EINVAL;
     if (!(p->cg_tol > 0.0) || p->cg_maxit < 1) return HH_EINVAL;
     if (p->cheb_degree < 0 || p->cheb_degree > CHEB_MAX_DEGREE) return HH_EINVAL;
     if (p->cheb_degree > 0 && (p->precision != HH_FP64 || !(p->cheb_eps > 0.0 && p->cheb_eps < 1.0)))
@@ -459,7 +479,9 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
     c->cap_rhs = p->n_pf > 4 ? p->n_pf : 4;
     c->timeout_ns = 5LL * 1000 * 1000 * 1000;
     // The exact-block form of M runs in its own kernel.
-    c->kind = p->link_order != 0 ? ENGINE_EXBLOCK : (lat->d == 1 ? ENGINE_D1 : ENGINE_D3);
+    c->kind = p->link_order != 0 ? ENGINE_EXBLOCK
+              : p->precision >= HH_MIXED_BF16LINK ? (lat->d == 1 ? ENGINE_D1_L16 : ENGINE_D3_L16)
+                                                  : (lat->d == 1 ? ENGINE_D1 : ENGINE_D3);
     c->two_slot = p->link_order == 0 ? engine_two_slot(c->kind) : 0;
     int max_grid = engine_default_grid(c->kind);
     if (max_grid <= 0) {
@@ -531,7 +553,15 @@ int hh_create(hh_ctx **out, const hh_lattice *lat, const hh_params *p, void *cud
         cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
         if (const char *env = getenv("HH_APPLY_MTM")) c->mtm_path = atoi(env);
     }
+    if (e == cudaSuccess && p->precision >= HH_MIXED_BF16LINK) {
+        c->l16_mode = p->precision == HH_MIXED_BF16LINK ? 1 : 2;
+        int ex = 14;
+        while (ex > 0 && (1.0 + fabs(p->A)) * ldexp(1.0, ex) > 32767.0) --ex;
+        c->l16_scale = ldexp(1.0, -ex);
+        e = dalloc(&c->L16, n);
+    }
     if (e == cudaSuccess) e = launch_links(c->geo, p->A, c->sigma, c->L64, c->L32, c->stream);
+    if (e == cudaSuccess) e = links16_after(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         free_ctx(c);
@@ -566,7 +596,8 @@ int hh_set_field(hh_ctx *c, const double *sigma, int on_device)
         HH_TRY(cudaMemcpyAsync(c->sigma, sigma, bytes, cudaMemcpyHostToDevice, c->stream));
     }
     HH_TRY(launch_links(c->geo, c->prm.A, c->sigma, c->L64, c->L32, c->stream));
-    c->n_launch += 1;
+    HH_TRY(links16_after(c));
+    c->n_launch += c->l16_mode ? 2 : 1;
     if (!on_device) HH_TRY(cudaStreamSynchronize(c->stream));
     return HH_OK;
 }
@@ -589,7 +620,8 @@ int hh_init_field_random(hh_ctx *c, uint64_t seed)
     if (!c) return HH_EINVAL;
     HH_TRY(launch_init_field(c->sigma, c->N, seed, c->prm.chain_id, c->stream));
     HH_TRY(launch_links(c->geo, c->prm.A, c->sigma, c->L64, c->L32, c->stream));
-    c->n_launch += 2;
+    HH_TRY(links16_after(c));
+    c->n_launch += c->l16_mode ? 3 : 2;
     return HH_OK;
 }
 
@@ -860,11 +892,13 @@ int leapfrog_enqueue(hh_ctx *c, double *pi, const double *chi, int n_rhs, int n_
         rc = ctx_force(c, n_rhs, pi, kick, nullptr, &nl);
         if (rc) return rc;
         c->n_launch += nl - 1;
-        if (j + 1 < forces)
+        if (j + 1 < forces) {
             HH_TRY(launch_sigma_step(c->geo, A, drift, c->sigma, pi, c->L64, c->L32, c->stream));
+            HH_TRY(links16_after(c));
+        }
     }
     if (h1) HH_TRY(launch_energy(c->N, pi, chi, c->xsol, n_rhs, c->d_energy_part, h1, c->stream));
-    c->n_launch += (h0 ? 2 : 0) + (h1 ? 2 : 0) + forces + (forces - 1);
+    c->n_launch += (h0 ? 2 : 0) + (h1 ? 2 : 0) + forces + (forces - 1) * (c->l16_mode ? 2 : 1);
     return HH_OK;
 }
 
@@ -913,7 +947,8 @@ int hh_trajectory(hh_ctx *c, int n_md, double dt, uint64_t traj, hh_traj_info *i
     if (rc) return rc;
     HH_TRY(launch_metropolis(c->d_sc, seed, traj, chain, c->stream));
     HH_TRY(launch_restore(c->geo, c->prm.A, c->d_sc, c->sigma, c->sigma0, c->L64, c->L32, c->stream));
-    c->n_launch += (1 + npf) + npf + 2;
+    HH_TRY(links16_after(c));
+    c->n_launch += (1 + npf) + npf + 2 + (c->l16_mode ? 1 : 0);
     if (!info) return HH_OK;
     char *hp = (char *)c->h_pinned;
     HH_TRY(cudaMemcpyAsync(hp, c->d_stats, sizeof(EngStats), cudaMemcpyDeviceToHost, c->stream));

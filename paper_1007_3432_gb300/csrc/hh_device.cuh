@@ -4,6 +4,8 @@
 // signal slots of the persistent engine, whose waits are bounded in time.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -248,6 +250,58 @@ __device__ __forceinline__ Vec<T, W> vldg(const T *p)
     }
     return r;
 }
+
+// 16-bit links of an FP32 inner iteration (mode 1: the upper half of the FP32
+// bit pattern, bfloat16 rounded to nearest even; mode 2: fixed point, value =
+// (signed code) * scale).  FP32 links are passed as a plain pointer instead.
+struct LinkSrc {
+    const unsigned short *L16;
+    int mode;
+    float scale;
+};
+
+__device__ __forceinline__ float link16_value(unsigned u, int mode, float scale)
+{
+    return mode == 1 ? __uint_as_float(u << 16) : (float)(short)(unsigned short)u * scale;
+}
+
+// W consecutive links from site i (i a multiple of W): a vector load of the
+// FP32 or FP64 links, or of the 16-bit codes (8, 4 or 2 bytes, aligned as the
+// site index).
+template <typename T, int W, typename LK>
+__device__ __forceinline__ Vec<T, W> link_row(const LK &L, int i)
+{
+    if constexpr (std::is_same<LK, LinkSrc>::value) {
+        Vec<T, W> r;
+        if constexpr (W == 4) {
+            const uint2 q = __ldg(reinterpret_cast<const uint2 *>(L.L16 + i));
+            r.a[0] = link16_value(q.x & 0xffffu, L.mode, L.scale);
+            r.a[1] = link16_value(q.x >> 16, L.mode, L.scale);
+            r.a[2] = link16_value(q.y & 0xffffu, L.mode, L.scale);
+            r.a[3] = link16_value(q.y >> 16, L.mode, L.scale);
+        } else if constexpr (W == 2) {
+            const unsigned q = __ldg(reinterpret_cast<const unsigned *>(L.L16 + i));
+            r.a[0] = link16_value(q & 0xffffu, L.mode, L.scale);
+            r.a[1] = link16_value(q >> 16, L.mode, L.scale);
+        } else {
+            r.a[0] = link16_value(__ldg(L.L16 + i), L.mode, L.scale);
+        }
+        return r;
+    } else {
+        return vldg<T, W>(L + i);
+    }
+}
+
+// Address of the link storage of site i (for prefetches).
+template <typename LK>
+__device__ __forceinline__ const void *link_addr(const LK &L, int i)
+{
+    if constexpr (std::is_same<LK, LinkSrc>::value)
+        return (const void *)(L.L16 + i);
+    else
+        return (const void *)(L + i);
+}
+
 
 template <typename T, int W>
 __device__ __forceinline__ void vst(T *p, const Vec<T, W> &v)

@@ -38,9 +38,8 @@ __device__ __forceinline__ int cnth()
     return (int)blockDim.x - s_ctl_threads;
 }
 
-template <int D, typename T, int W>
-__device__ double gloop_M(const Geo g, const T h, const T *__restrict__ L, const T *v, T *t, int b,
-                          int e, int pf = 0)
+template <int D, typename T, int W, typename LK>
+__device__ double gloop_M(const Geo g, const T h, const LK L, const T *v, T *t, int b, int e, int pf = 0)
 {
     T acc = T(0);
     const int step = W * cnth(), ahead = pf * step;
@@ -49,13 +48,13 @@ __device__ double gloop_M(const Geo g, const T h, const T *__restrict__ L, const
             const int j = i + ahead, jp = row_prev(g, j);
             prefetch_l2(v + j);
             prefetch_l2(v + jp);
-            prefetch_l2(L + jp);
+            prefetch_l2(link_addr(L, jp));
         }
         GroupNbr nb;
         group_nbrs<D, W>(g, i, nb);
         Vec<T, W> self = vld<T, W>(v + i);
         Vec<T, W> hs = group_hop<D, T, W>(v, nb, self);
-        Vec<T, W> lk = vldg<T, W>(L + nb.prev);
+        Vec<T, W> lk = link_row<T, W>(L, nb.prev);
         Vec<T, W> pv = vld<T, W>(v + nb.prev);
         Vec<T, W> out;
 #pragma unroll
@@ -69,9 +68,9 @@ __device__ double gloop_M(const Geo g, const T h, const T *__restrict__ L, const
 }
 
 // CG slot 3: q = M^T t, x += alpha p, r -= alpha q; acc += r^2.
-template <int D, typename T, int W>
-__device__ double gloop_update(const Geo g, const T h, const T *__restrict__ L, const T *t, T *x,
-                               const T *p, T *r, const T alpha, int b, int e, int pf = 0)
+template <int D, typename T, int W, typename LK>
+__device__ double gloop_update(const Geo g, const T h, const LK L, const T *t, T *x, const T *p, T *r,
+                               const T alpha, int b, int e, int pf = 0)
 {
     T acc = T(0);
     const int step = W * cnth(), ahead = pf * step;
@@ -80,7 +79,7 @@ __device__ double gloop_update(const Geo g, const T h, const T *__restrict__ L, 
             const int j = i + ahead;
             prefetch_l2(t + j);
             prefetch_l2(t + row_next(g, j));
-            prefetch_l2(L + j);
+            prefetch_l2(link_addr(L, j));
             prefetch_l2(x + j);
             prefetch_l2(p + j);
             prefetch_l2(r + j);
@@ -89,7 +88,7 @@ __device__ double gloop_update(const Geo g, const T h, const T *__restrict__ L, 
         group_nbrs<D, W>(g, i, nb);
         Vec<T, W> self = vld<T, W>(t + i);
         Vec<T, W> hs = group_hop<D, T, W>(t, nb, self);
-        Vec<T, W> lk = vldg<T, W>(L + i);
+        Vec<T, W> lk = link_row<T, W>(L, i);
         Vec<T, W> nv = vld<T, W>(t + nb.next);
         Vec<T, W> xv = vld<T, W>(x + i);
         Vec<T, W> pv = vld<T, W>(p + i);
@@ -266,9 +265,9 @@ __device__ double gloop_residual_ex(const Geo g, const double h, const double *_
 // t = M p_new with p_new recomputed at the neighbour sites from src and p_old,
 // which are final there; acc += t^2.  The recomputed values are bitwise the
 // ones their owners store (the same fma on the same inputs).
-template <int D, typename T, int W>
-__device__ double gloop_pM(const Geo g, const T h, const T *__restrict__ L, const T *src, const T *pold,
-                           T *pnew, T *t, const T beta, bool restart, int b, int e, int pf = 0)
+template <int D, typename T, int W, typename LK>
+__device__ double gloop_pM(const Geo g, const T h, const LK L, const T *src, const T *pold, T *pnew, T *t,
+                           const T beta, bool restart, int b, int e, int pf = 0)
 {
     T acc = T(0);
     const int step = W * cnth(), ahead = pf * step;
@@ -277,7 +276,7 @@ __device__ double gloop_pM(const Geo g, const T h, const T *__restrict__ L, cons
             const int j = i + ahead, jp = row_prev(g, j);
             prefetch_l2(src + j);
             prefetch_l2(src + jp);
-            prefetch_l2(L + jp);
+            prefetch_l2(link_addr(L, jp));
             if (!restart) {
                 prefetch_l2(pold + j);
                 prefetch_l2(pold + jp);
@@ -309,7 +308,7 @@ __device__ double gloop_pM(const Geo g, const T h, const T *__restrict__ L, cons
             zm = pn_row(nb.zm);
         }
         const Vec<T, W> pv = pn_row(nb.prev);
-        const Vec<T, W> lk = vldg<T, W>(L + nb.prev);
+        const Vec<T, W> lk = link_row<T, W>(L, nb.prev);
         Vec<T, W> out;
 #pragma unroll
         for (int u = 0; u < W; ++u) {
@@ -607,6 +606,11 @@ __device__ __forceinline__ TileCtl make_ctl(const EngState &S, int two, int x0_g
     return c;
 }
 
+__device__ __forceinline__ LinkSrc link_src(const EngSystem &Y)
+{
+    return LinkSrc{Y.L16, Y.link16, Y.l16_scale};
+}
+
 __device__ __forceinline__ double *pbuf64(const EngSystem &Y, int k)
 {
     return k ? Y.p2 : Y.p;
@@ -654,14 +658,18 @@ __device__ void slot1(const EngSystem &Y, const TileCtl &c, const EngTile &T)
     }
 }
 
-template <int D, int W, bool PF = true>
+template <int D, int W, bool PF = true, bool L16 = false>
 __device__ double slot2(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 {
     const int pf = PF ? Y.pf : 0;
     if (c.mode == MODE_CG) {
         if (c.prec == PREC_FP64)
             return gloop_M<D, double, W>(Y.g, Y.h, Y.L64, pbuf64(Y, c.pnew), Y.t, T.begin, T.end, pf);
-        return gloop_M<D, float, W>(Y.g, (float)Y.h, Y.L32, pbuf32(Y, c.pnew), Y.t32, T.begin, T.end, pf);
+        if constexpr (L16)
+            return gloop_M<D, float, W>(Y.g, (float)Y.h, link_src(Y), pbuf32(Y, c.pnew), Y.t32, T.begin, T.end,
+                                        pf);
+        else
+            return gloop_M<D, float, W>(Y.g, (float)Y.h, Y.L32, pbuf32(Y, c.pnew), Y.t32, T.begin, T.end, pf);
     }
     if (c.mode == MODE_RU) gloop_M<D, double, W>(Y.g, Y.h, Y.L64, Y.x, Y.t, T.begin, T.end);
     if (c.mode == MODE_PRE)
@@ -669,7 +677,7 @@ __device__ double slot2(const EngSystem &Y, const TileCtl &c, const EngTile &T)
     return 0.0;
 }
 
-template <int D, int W, bool PF = true>
+template <int D, int W, bool PF = true, bool L16 = false>
 __device__ double slot3(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 {
     const int pf = PF ? Y.pf : 0;
@@ -677,8 +685,12 @@ __device__ double slot3(const EngSystem &Y, const TileCtl &c, const EngTile &T)
         if (c.prec == PREC_FP64)
             return gloop_update<D, double, W>(Y.g, Y.h, Y.L64, Y.t, Y.x, pbuf64(Y, c.pnew), Y.r, c.alpha,
                                               T.begin, T.end, pf);
-        return gloop_update<D, float, W>(Y.g, (float)Y.h, Y.L32, Y.t32, Y.x32, pbuf32(Y, c.pnew), Y.r32,
-                                         (float)c.alpha, T.begin, T.end, pf);
+        if constexpr (L16)
+            return gloop_update<D, float, W>(Y.g, (float)Y.h, link_src(Y), Y.t32, Y.x32, pbuf32(Y, c.pnew),
+                                             Y.r32, (float)c.alpha, T.begin, T.end, pf);
+        else
+            return gloop_update<D, float, W>(Y.g, (float)Y.h, Y.L32, Y.t32, Y.x32, pbuf32(Y, c.pnew), Y.r32,
+                                             (float)c.alpha, T.begin, T.end, pf);
     }
     if (c.mode == MODE_RU) {
         // Two-slot form: the mixed reliable update accumulates here, after
@@ -734,7 +746,7 @@ __device__ double slot3_ex(const EngSystem &Y, const TileCtl &c, const EngTile &
 
 // Two-slot first slot: slot 1 folded into slot 2.  Returns this thread's
 // |t|^2 partial for a CG step (0 otherwise).
-template <int D, int W, bool PF = true>
+template <int D, int W, bool PF = true, bool L16 = false>
 __device__ double slotA(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 {
     const int pf = PF ? Y.pf : 0;
@@ -746,8 +758,12 @@ __device__ double slotA(const EngSystem &Y, const TileCtl &c, const EngTile &T)
         if (c.prec == PREC_FP64)
             return gloop_pM<D, double, W>(Y.g, Y.h, Y.L64, Y.r, pbuf64(Y, c.pold), pbuf64(Y, c.pnew), Y.t,
                                           c.beta, restart, T.begin, T.end, pf);
-        return gloop_pM<D, float, W>(Y.g, (float)Y.h, Y.L32, Y.r32, pbuf32(Y, c.pold), pbuf32(Y, c.pnew),
-                                     Y.t32, (float)c.beta, restart, T.begin, T.end, pf);
+        if constexpr (L16)
+            return gloop_pM<D, float, W>(Y.g, (float)Y.h, link_src(Y), Y.r32, pbuf32(Y, c.pold),
+                                         pbuf32(Y, c.pnew), Y.t32, (float)c.beta, restart, T.begin, T.end, pf);
+        else
+            return gloop_pM<D, float, W>(Y.g, (float)Y.h, Y.L32, Y.r32, pbuf32(Y, c.pold), pbuf32(Y, c.pnew),
+                                         Y.t32, (float)c.beta, restart, T.begin, T.end, pf);
     }
     if (c.mode == MODE_RU) {
         if (c.prec == PREC_MIXED)
@@ -782,20 +798,23 @@ __device__ double run_slot(const EngSystem &Y, const TileCtl &c, const EngTile &
         return 0.0;
     }
     // The generic kernel (FD = 0) carries both dimensions' loops; it is
-    // compiled without the prefetches to stay within its registers.
+    // compiled without the prefetches to stay within its registers.  FD = 5
+    // and 7 are the d = 1 and d = 3 kernels whose FP32 steps read 16-bit
+    // links.
+    constexpr bool L16 = FD == 5 || FD == 7;
 #define HH_SLOT_CALL(D, W)                                   \
     if (SLOT == 1) {                                         \
         slot1<D, W, FD != 0>(Y, c, T);                       \
         return 0.0;                                          \
     } else if (SLOT == 2) {                                  \
-        return slot2<D, W, FD != 0>(Y, c, T);                \
+        return slot2<D, W, FD != 0, L16>(Y, c, T);           \
     } else if (SLOT == 4) {                                  \
-        return slotA<D, W, FD != 0>(Y, c, T);                \
+        return slotA<D, W, FD != 0, L16>(Y, c, T);           \
     } else {                                                 \
-        return slot3<D, W, FD != 0>(Y, c, T);                \
+        return slot3<D, W, FD != 0, L16>(Y, c, T);           \
     }
     const int w = Y.w;
-    if (FD == 3 || (FD == 0 && Y.g.d == 3)) {
+    if (FD == 3 || FD == 7 || (FD == 0 && Y.g.d == 3)) {
         if (w == 4) { HH_SLOT_CALL(3, 4) }
         if (w == 2) { HH_SLOT_CALL(3, 2) }
         HH_SLOT_CALL(3, 1)
@@ -1320,6 +1339,8 @@ const void *kernel_of(int kind)
     case ENGINE_D1: return (const void *)engine_kernel<1, 1>;
     case ENGINE_D3: return (const void *)engine_kernel<3, 1>;
     case ENGINE_EXBLOCK: return (const void *)engine_kernel<4, 1>;
+    case ENGINE_D1_L16: return (const void *)engine_kernel<5, 1>;
+    case ENGINE_D3_L16: return (const void *)engine_kernel<7, 1>;
     default: return (const void *)engine_kernel<0, 1>;
     }
 }
@@ -1431,7 +1452,7 @@ int engine_two_slot(int kind)
     // Measured on GB300: the fused form is faster for d = 1 (its neighbour
     // recomputation is two x-halo sites and one earlier row), slower for
     // d = 3, where it re-reads both operands of p at six neighbour rows.
-    return kind == ENGINE_D1 ? 1 : 0;
+    return (kind == ENGINE_D1 || kind == ENGINE_D1_L16) ? 1 : 0;
 }
 
 int engine_default_grid(int kind)

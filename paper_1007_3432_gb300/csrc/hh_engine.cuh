@@ -82,6 +82,10 @@ struct EngSystem {
     double *z, *u;                    // FP64 preconditioner vectors (when cheb_n > 0)
     double *p2;                       // second FP64 p buffer (two-slot launches)
     float *p32b;                      // second FP32 p buffer (two-slot launches)
+    const unsigned short *L16;        // 16-bit links of the FP32 steps (link16 != 0)
+    int link16;                       // links of the FP32 steps: 0 L32; 1 L16 as bfloat16;
+                                      // 2 L16 as fixed point times l16_scale (see LinkSrc)
+    float l16_scale;
 };
 
 // FP32 steps after which a mixed system takes a reliable update even if its
@@ -155,8 +159,17 @@ __host__ __device__ constexpr size_t engine_sig_count(int parts)
 // that dimension and are compiled for it.
 // ENGINE_EXBLOCK runs systems with the exact-block form of M (link_order 1,
 // 2) only, with scalar site loops, kept apart so that the other kernels do
-// not carry its code.
-enum EngKind : int { ENGINE_GENERIC = 0, ENGINE_D1 = 1, ENGINE_D3 = 3, ENGINE_EXBLOCK = 4 };
+// not carry its code.  ENGINE_D1_L16 / ENGINE_D3_L16 are the d = 1 / d = 3
+// kernels whose FP32 steps read 16-bit links (EngSystem::link16 != 0 for
+// every mixed system of the launch), likewise kept apart.
+enum EngKind : int {
+    ENGINE_GENERIC = 0,
+    ENGINE_D1 = 1,
+    ENGINE_D3 = 3,
+    ENGINE_EXBLOCK = 4,
+    ENGINE_D1_L16 = 5,
+    ENGINE_D3_L16 = 7
+};
 
 // Host launcher: runs the engine with a cooperative launch of 'grid' blocks.
 // The barrier counter ctl->count must be zero when the launch starts.

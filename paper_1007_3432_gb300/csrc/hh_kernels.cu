@@ -1,6 +1,8 @@
 // Non-persistent kernels of the HMC path (Sec. 4.1): links, stencil applies,
 // Philox draws, the pseudofermion force with the fused momentum update, the
 // sigma step, energy reductions and the Metropolis test.
+#include <cuda_bf16.h>
+
 #include "hh_kernels.cuh"
 
 namespace hh {
@@ -170,6 +172,23 @@ __global__ void k_sum_partials(const double *__restrict__ part, int nb, double *
     for (int j = threadIdx.x; j < nb; j += 32) v += part[j];
     v = warp_sum(v);
     if (threadIdx.x == 0) *out = v;
+}
+
+// 16-bit links of the FP32 steps from the FP64 links: mode 1 the bfloat16
+// rounding (to nearest even) of the FP32 value, mode 2 the fixed-point code
+// rint(L / scale) (|L| / scale < 2^15 by the choice of scale).
+__global__ void k_links16(int n, const double *__restrict__ L64, unsigned short *__restrict__ L16, int mode,
+                          double inv_scale)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = L64[i];
+        unsigned short u;
+        if (mode == 1)
+            u = __bfloat16_as_ushort(__float2bfloat16_rn(__double2float_rn(v)));
+        else
+            u = (unsigned short)(short)__double2int_rn(v * inv_scale);
+        L16[i] = u;
+    }
 }
 
 // Z2 noise of the observables: vector k = blockIdx.y (+ gridDim.y steps) at
@@ -368,6 +387,12 @@ cudaError_t launch_energy(int n, const double *pi, const double *chi, const doub
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_sum_partials<<<1, 32, 0, st>>>(part, nb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_links16(int n, const double *L64, unsigned short *L16, int mode, double scale, cudaStream_t st)
+{
+    k_links16<<<grid_for(n), kBlock, 0, st>>>(n, L64, L16, mode, 1.0 / scale);
     return cudaGetLastError();
 }
 

@@ -61,6 +61,10 @@ cudaError_t launch_metropolis(HmcScalars *sc, uint64_t seed, uint64_t traj, uint
 cudaError_t launch_restore(const Geo &g, double A, const HmcScalars *sc, double *sigma,
                            const double *sigma0, double *L64, float *L32, cudaStream_t st);
 
+// 16-bit links of the FP32 steps (mode 1 bfloat16, mode 2 fixed point with
+// value = code * scale) from the FP64 links.
+cudaError_t launch_links16(int n, const double *L64, unsigned short *L16, int mode, double scale, cudaStream_t st);
+
 // Observables (noise estimators of diag M^{-1}; see hh_observables).
 // nvec Z2 noise vectors (Philox tag 6, vector k at out + k n).
 constexpr int kObsMaxNoise = 64;

@@ -142,7 +142,7 @@ def test_field_roundtrip_and_random_init(hh):
         assert np.array_equal(got.cpu().numpy(), oracle.init_field(77, 3, n))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-bf16link", "mixed-fix16link"])
 @pytest.mark.parametrize("d,nx,ntau,n_rhs", [(1, 32, 64, 2), (1, 19, 11, 1), (3, 6, 8, 2), (3, 4, 16, 3)])
 def test_solve_true_residual_and_solution(hh, precision, d, nx, ntau, n_rhs):
     lat = oracle.lattice(d, nx, ntau)
@@ -210,7 +210,7 @@ def test_action_heatbath_identity(hh):
     assert abs(S - S_ref) <= 1e-9 * S_ref
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-fix16link"])
 def test_trajectories_match_oracle(hh, precision):
     """Several trajectories of the d=1, 32 x 64 lattice from the same seed:
     identical accept/reject sequences and matching energies."""
@@ -599,3 +599,11 @@ def test_observables_reject_bad_noise_counts(hh):
         for nn in (0, 1, 3, 66):
             with pytest.raises(hh.HHError):
                 ctx.observables(nn, 0)
+
+
+@pytest.mark.parametrize("precision", ["mixed-bf16link", "mixed-fix16link"])
+def test_16bit_links_rejected_where_unsupported(hh, precision):
+    with pytest.raises(hh.HHError):
+        hh.Context(1, 8, 8, precision=precision, link_order=1)
+    with pytest.raises(hh.HHError):
+        hh.Context(1, 8, 8, precision=precision, cheb_degree=8)
