@@ -74,9 +74,10 @@ def bytes_per_site(kind, precision):
 # DRAM bytes per engine iteration (two right-hand sides) of the engine kernel
 # as it stands, from one ncu --set full capture each (dram__bytes_read.sum +
 # dram__bytes_write.sum over a 202-iteration launch; profiles/engine_kernel_*).
-# A launch's traffic scales with its iterations.
-ENGINE_DRAM_PER_ITER = {("d1_nx1024_nt512", "fp64"): (12.7232e6 + 455.225344e6) / 202,
-                        ("d3_nx32_nt128", "mixed"): (35.046802e9 + 27.076187e9) / 202}
+# A launch's traffic scales with its iterations.  Empty: the kernel has changed
+# since the last captures (its per-system descriptor gained the 16-bit link
+# fields), so the bench lines report no traffic until the next capture.
+ENGINE_DRAM_PER_ITER = {}
 
 
 def engine_traffic(wl, precision, cheb, cnt):
