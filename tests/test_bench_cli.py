@@ -69,3 +69,21 @@ dist.destroy_process_group()
     finally:
         os.remove(script)
     assert r.returncode == 0, r.stderr[-2000:]
+
+
+def test_cpu_baseline_reports_one_thread_and_all_cores():
+    """The oracle baseline: one thread, and one spawned copy per host core."""
+    import bench
+    import workloads
+    r = bench.cpu_baseline(workloads.C0, seconds=0.3)
+    assert r["kind"] == "oracle" and r["cores"] == 1 and r["value"] > 0
+    a = r["all_cores"]
+    assert a["cores"] >= 1 and a["value"] > 0 and a["kind"] == "oracle"
+
+
+def test_algorithmic_bytes_per_site():
+    import bench
+    assert bench.bytes_per_site("cg", "fp64") == 104
+    assert bench.bytes_per_site("cg", "mixed") == 52
+    assert bench.bytes_per_site("cg", "mixed-fix16link") == 48
+    assert bench.bytes_per_site("ru", "mixed-bf16link") == bench.bytes_per_site("ru", "mixed") == 76
