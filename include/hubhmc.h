@@ -313,7 +313,10 @@ typedef struct {
     hh_lattice lat;
     hh_params prm;       /* as for hh_create; for a solve, n_pf is the number of
                             right-hand sides (1..4); cheb_degree > 0 (FP64 only)
-                            preconditions the request's solves as in hh_solve */
+                            preconditions the request's solves as in hh_solve;
+                            precision HH_FP64 or HH_MIXED (the 16-bit link
+                            precisions and link_order != 0 are for contexts
+                            only: HH_EINVAL) */
     const double *sigma; /* host, N doubles, copied at submit; NULL: sigma from
                             Philox tag 0 with prm.seed (as hh_init_field_random) */
     const double *b;     /* solve: host, n_pf*N doubles copied at submit; NULL:
