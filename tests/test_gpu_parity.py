@@ -607,3 +607,42 @@ def test_16bit_links_rejected_where_unsupported(hh, precision):
         hh.Context(1, 8, 8, precision=precision, link_order=1)
     with pytest.raises(hh.HHError):
         hh.Context(1, 8, 8, precision=precision, cheb_degree=8)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_prefetch_leaves_results_bitwise_unchanged(hh, monkeypatch, precision):
+    """The L2 prefetch of the CG site loops is a hint: solutions are bitwise
+    the same at every distance.  16^3 x 80 gives tiles of two or more loop
+    rounds, so the prefetches are issued."""
+    from paper_1007_3432_gb300.binding import HH_ENOCONV
+    d, nx, ntau = 3, 16, 80
+    n = nx ** 3 * ntau
+    sigma = workloads.sigma_field(n, seed=41)
+    b = np.stack([workloads.source(n, seed=42, rhs=a) for a in range(2)])
+    outs = []
+    for pf in ("0", "1", "3"):
+        monkeypatch.setenv("HH_ENGINE_PREFETCH", pf)
+        with hh.Context(d, nx, ntau, precision=precision, cg_maxit=300) as ctx:
+            ctx.set_field(dev(sigma))
+            x = torch.zeros(2, n, dtype=torch.float64, device="cuda")
+            ctx.solve(dev(b), x, 2, allow=(HH_ENOCONV,))
+            outs.append(x.cpu())
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_dependent_launch_leaves_apply_bitwise_unchanged(hh, monkeypatch, dtype):
+    """The two Q sweeps with and without the programmatic dependent launch."""
+    d, nx, ntau = 3, 8, 12
+    n = nx ** 3 * ntau
+    sigma = workloads.sigma_field(n, seed=43)
+    x = dev(workloads.source(n, seed=44)).to(dtype)
+    outs = []
+    for path in ("1", "2"):
+        monkeypatch.setenv("HH_APPLY_MTM", path)
+        with hh.Context(d, nx, ntau) as ctx:
+            ctx.set_field(dev(sigma))
+            y = torch.empty_like(x)
+            ctx.apply(hh.HH_OP_MTM, x, y)
+            outs.append(y.cpu())
+    assert torch.equal(outs[0], outs[1])
