@@ -803,3 +803,21 @@ def test_observable_estimators_are_unbiased(orc):
     assert abs(tr.mean() - exact_tr) < 5 * err
     p = np.array([r["one_minus_g_sq"] for r in runs])
     assert abs(p.mean() - exact_p) < 5 * p.std(ddof=1) / np.sqrt(len(p))
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_free_field_double_occupancy_estimate(orc, order):
+    """At A = 0 every M^{-1}_ii of the block form is the same (translations in
+    space and time), so (1/N) sum_i (1 - M^{-1}_ii)^2 = (1 - n_F)^2 with
+    1 - n_F the Fermi-Dirac trace of the free-field pin: the product estimate
+    over independent noise runs agrees within five standard errors."""
+    d, nx, ntau = 1, 8, 8
+    lat = orc.lattice(d, nx, ntau)
+    n = orc.nsites(lat)
+    prm = orc.params(cg_tol=1e-12, seed=9, A=0.0, link_order=order)
+    E = _free_block_energies(d, nx, H, order)
+    g = np.mean(1.0 / (1.0 + E ** ntau))
+    runs = [orc.observables(lat, prm, np.zeros(n), 16, traj) for traj in range(8)]
+    p = np.array([r["one_minus_g_sq"] for r in runs])
+    assert abs(p.mean() - (1.0 - g) ** 2) < 5 * p.std(ddof=1) / np.sqrt(len(p)) + 1e-12
+    assert all(abs(r["mean_sin"]) == 0.0 and r["mean_sin2"] == 0.0 for r in runs)
