@@ -74,6 +74,8 @@ cudaError_t launch_sweep(const Geo &g, T h, const T *L, const T *x, T *y, cudaSt
     const int w = engine_group_width(g.nx);
     long long groups = g.N / w;
     int blocks = (int)((groups + 255) / 256);
+    // Grid cap: 16 blocks per SM of the 152 (HH_APPLY_SWEEP_BLOCKS overrides
+    // it, 0 removes it; measured on GB300 the same or slower either way).
     static const int cap = [] {
         const char *env = getenv("HH_APPLY_SWEEP_BLOCKS");
         return env ? atoi(env) : 152 * 16;
