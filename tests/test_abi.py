@@ -57,3 +57,15 @@ def test_fast_division_matches_integer_division(tmp_path):
                            "-o", exe])
     out = subprocess.run([exe], capture_output=True, text=True)
     assert out.returncode == 0, out.stdout + out.stderr
+
+
+def test_host_logic_tiling_and_md_schedules(tmp_path):
+    """Engine tiling covers every site once in 32-aligned chunks; leapfrog and
+    Omelyan schedules kick and drift n_md * dt in total (host-only build)."""
+    import shutil
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    exe = str(tmp_path / "host_logic_check")
+    subprocess.check_call([nvcc, "-O2", "-std=c++17", "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "native", "host_logic_check.cu"), "-o", exe])
+    out = subprocess.run([exe], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
