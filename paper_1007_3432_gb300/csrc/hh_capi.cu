@@ -1,6 +1,7 @@
-// C ABI of the library: contexts, solves and the HMC trajectory driver.
-// Every step of the path runs in the kernels of hh_kernels.cu and
-// hh_engine.cu; this file only allocates, validates, plans and enqueues.
+// C ABI of the library: contexts, applies, solves, observables and the HMC
+// trajectory driver.  Every step of the path runs in the kernels of
+// hh_kernels.cu, hh_apply.cu and hh_engine.cu; this file only allocates,
+// validates, plans and enqueues.
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
