@@ -69,3 +69,24 @@ def test_host_logic_tiling_and_md_schedules(tmp_path):
                            os.path.join(ROOT, "tests", "native", "host_logic_check.cu"), "-o", exe])
     out = subprocess.run([exe], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
+
+
+def test_chebyshev_table_matches_oracle_polynomial(tmp_path):
+    """The engine's Chebyshev table (Leja-ordered real factors, Sec. 4.2),
+    evaluated factor by factor on the host, against the oracle's P(z) of
+    Eq. (13) on [eps, 1]: the same polynomial to 1e-11 relative."""
+    import shutil
+    import numpy as np
+    import oracle
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    exe = str(tmp_path / "cheb_table_dump")
+    subprocess.check_call([nvcc, "-O2", "-std=c++17", "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "native", "cheb_table_dump.cu"),
+                           os.path.join(ROOT, "paper_1007_3432_gb300", "csrc", "hh_engine_host.cu"), "-o", exe])
+    for n, eps in [(4, 1e-3), (8, 1e-4), (32, 1e-5), (64, 1e-6)]:
+        zs = np.concatenate([np.geomspace(eps, 1.0, 25), np.linspace(0.0, 1.0, 11)])
+        out = subprocess.run([exe, str(n), repr(eps)] + [repr(float(z)) for z in zs],
+                             capture_output=True, text=True, check=True)
+        got = np.array([float(v) for v in out.stdout.split()])
+        ref = np.array([oracle.cheb_poly(n, eps, float(z)) for z in zs])
+        assert np.all(np.abs(got - ref) <= 1e-11 * np.abs(ref)), (n, eps, np.max(np.abs(got - ref) / np.abs(ref)))
