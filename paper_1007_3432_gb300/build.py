@@ -2,7 +2,7 @@
 
 Each ``csrc/*.cu`` translation unit is compiled in parallel with
 ``-gencode arch=compute_103a,code=sm_103a`` and linked with the static CUDA
-runtime, so the library depends only on the driver.  The output goes to
+runtime, so the library depends only on the NVIDIA driver.  The output goes to
 ``paper_1007_3432_gb300/lib/``.
 """
 import concurrent.futures as cf
