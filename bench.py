@@ -91,6 +91,14 @@ def engine_traffic(wl, precision, cheb, cnt):
     return per_iter * iters
 
 
+def us_per_engine_iteration(cnt, n_rhs=2):
+    """Engine time per iteration in microseconds: the n_rhs systems of a
+    launch advance together, one INIT iteration per launch, then their CG
+    steps and true-residual checks (summed over systems in the counters)."""
+    iters = (cnt["cg_steps"] + cnt["ru_steps"]) / float(n_rhs) + cnt["engine_launches"]
+    return 1000.0 * cnt["engine_ms"] / iters if iters > 0 else None
+
+
 def fp64_peak_tflops():
     """FP64 peak of GB300 from unit counts and clocks: 152 SMs x 2 DFMA per
     clock per SM x 2 flops x 2.07 GHz (maximum SM clock) = 1.26 TFLOP/s, the
@@ -702,6 +710,7 @@ def main():
         "dH": [i["dH"] for i in infos],
         "exp_minus_dH_mean": float(np.mean([np.exp(-i["dH"]) for i in infos])),
         "max_true_relres": max(i["max_true_relres"] for i in infos),
+        "us_per_cg_iteration": us_per_engine_iteration(cnt),
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
         "gpu_launches": int(cnt["kernel_launches"]),
         "clocks": clk, "roofline": roof,

@@ -87,3 +87,11 @@ def test_algorithmic_bytes_per_site():
     assert bench.bytes_per_site("cg", "mixed") == 52
     assert bench.bytes_per_site("cg", "mixed-fix16link") == 48
     assert bench.bytes_per_site("ru", "mixed-bf16link") == bench.bytes_per_site("ru", "mixed") == 76
+
+
+def test_us_per_engine_iteration():
+    import bench
+    cnt = {"cg_steps": 2000, "ru_steps": 4, "engine_launches": 1, "engine_ms": 30.09}
+    assert abs(bench.us_per_engine_iteration(cnt) - 30090.0 / 1003.0) < 1e-9
+    assert bench.us_per_engine_iteration({"cg_steps": 0, "ru_steps": 0, "engine_launches": 0,
+                                          "engine_ms": 0.0}) is None
