@@ -90,3 +90,11 @@ def test_chebyshev_table_matches_oracle_polynomial(tmp_path):
         got = np.array([float(v) for v in out.stdout.split()])
         ref = np.array([oracle.cheb_poly(n, eps, float(z)) for z in zs])
         assert np.all(np.abs(got - ref) <= 1e-11 * np.abs(ref)), (n, eps, np.max(np.abs(got - ref) / np.abs(ref)))
+
+
+def test_public_header_compiles_as_c99_and_cxx11():
+    """include/hubhmc.h is a plain C header: no CUDA or C++ types leak into it."""
+    hdr = os.path.join(ROOT, "include", "hubhmc.h")
+    for cmd in (["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-x", "c", hdr],
+                ["g++", "-std=c++11", "-Wall", "-Werror", "-fsyntax-only", "-x", "c++", hdr]):
+        subprocess.check_call(cmd)
