@@ -13,7 +13,13 @@
  *     conjugate gradient (Sec. 4.1);
  *   - the pseudofermion action S_pf = 1/2 sum_a chi_a^T Q^{-1} chi_a
  *     (Eqs. (11)-(12)), its force dS_pf/dsigma, leapfrog molecular dynamics and
- *     the Metropolis accept/reject step of the phi-algorithm (Sec. 4.1).
+ *     the Metropolis accept/reject step of the phi-algorithm (Sec. 4.1);
+ *   - the Chebyshev-polynomial preconditioner of Sec. 4.2 and the exact-block
+ *     form of Eq. (7) as options.
+ * Beyond the paper: FP32 inner CG with FP64 reliable updates (optionally with
+ * 16-bit links), the Omelyan integrator and chronological initial guesses,
+ * noise estimators of diag M^{-1} (observables), a batched multi-chain engine
+ * with a serving loop, and an allocation-free solve.
  *
  * Conventions for every call:
  *   - Arrays are indexed by site i = x + Nx*(y + Nx*(z + Nx*tau)) for d = 3 and
