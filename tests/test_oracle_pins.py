@@ -821,3 +821,40 @@ def test_free_field_double_occupancy_estimate(orc, order):
     p = np.array([r["one_minus_g_sq"] for r in runs])
     assert abs(p.mean() - (1.0 - g) ** 2) < 5 * p.std(ddof=1) / np.sqrt(len(p)) + 1e-12
     assert all(abs(r["mean_sin"]) == 0.0 and r["mean_sin2"] == 0.0 for r in runs)
+
+
+def _hop_matrix(d, nx):
+    """Adjacency H of the periodic d-dimensional spatial lattice (x fastest)."""
+    V = nx ** d
+    Hm = np.zeros((V, V))
+    for s in range(V):
+        c = [(s // nx ** k) % nx for k in range(d)]
+        for k in range(d):
+            for step in (1, -1):
+                cc = list(c)
+                cc[k] = (cc[k] + step) % nx
+                Hm[s, sum(cc[j] * nx ** j for j in range(d))] += 1.0
+    return Hm
+
+
+@pytest.mark.parametrize("d,nx,ntau,order", [(1, 4, 5, 1), (1, 5, 4, 2), (3, 2, 3, 1), (3, 3, 3, 2)])
+def test_diagonal_blocks_are_equal_time_greens_functions(orc, d, nx, ntau, order):
+    """The reading behind the observables (R13): for the block form of Eq. (7)
+    with B_tau = E diag(1 + A sin sigma(., tau-1)) and the +B corner of the
+    antiperiodic boundary, the tau-th diagonal block of M^{-1} is
+    (1 + B_tau B_{tau-1} ... B_{tau+1})^{-1}, built here from sigma directly."""
+    lat = orc.lattice(d, nx, ntau)
+    n = orc.nsites(lat)
+    V = nx ** d
+    sigma = orc.init_field(3 + order, 0, n)
+    Minv = np.linalg.inv(orc.dense(lat, H, orc.links(lat, 0.5, sigma), "M", order=order))
+    Hm = _hop_matrix(d, nx)
+    E = np.eye(V) + H * Hm + (0.5 * H * H * Hm @ Hm if order == 2 else 0.0)
+    c = 1.0 + 0.5 * np.sin(sigma.reshape(ntau, V))
+    B = [E @ np.diag(c[(tau - 1) % ntau]) for tau in range(ntau)]
+    for tau in range(ntau):
+        P = np.eye(V)
+        for k in range(ntau):
+            P = P @ B[(tau - k) % ntau]
+        G = np.linalg.inv(np.eye(V) + P)
+        assert np.max(np.abs(G - Minv[tau * V:(tau + 1) * V, tau * V:(tau + 1) * V])) < 1e-12
