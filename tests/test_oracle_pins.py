@@ -858,3 +858,22 @@ def test_diagonal_blocks_are_equal_time_greens_functions(orc, d, nx, ntau, order
             P = P @ B[(tau - k) % ntau]
         G = np.linalg.inv(np.eye(V) + P)
         assert np.max(np.abs(G - Minv[tau * V:(tau + 1) * V, tau * V:(tau + 1) * V])) < 1e-12
+
+
+@pytest.mark.parametrize("d,nx,ntau", [(1, 6, 4), (3, 3, 3)])
+def test_reading_r1_is_exp_k_times_block_form_to_first_order(orc, d, nx, ntau):
+    """Reading R1 against the exact-block form at order 1: with D the diagonal
+    blocks 1 - hH of M_R1 and S = M_R1 - D its link part, D M_ex1 = D + (1 - h^2
+    H^2) S, so M_R1 = (1 - hH) M_ex1 + h^2 H^2 S: the two forms differ by the
+    factor e^{dtau K} ~ 1 - hH on the left, to first order in h."""
+    lat = orc.lattice(d, nx, ntau)
+    n = orc.nsites(lat)
+    V = nx ** d
+    L = orc.links(lat, 0.5, orc.init_field(17, 0, n))
+    M_r1 = orc.dense(lat, H, L, "M")
+    M_ex1 = orc.dense(lat, H, L, "M", order=1)
+    Hm = _hop_matrix(d, nx)
+    D = np.kron(np.eye(ntau), np.eye(V) - H * Hm)
+    S = M_r1 - D
+    H2 = np.kron(np.eye(ntau), Hm @ Hm)
+    assert np.max(np.abs(M_r1 - D @ M_ex1 - H * H * H2 @ S)) < 1e-13
