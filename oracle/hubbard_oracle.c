@@ -32,6 +32,15 @@
  *      counter (block, tag | a<<8, traj, chain) and key (seed, 0);
  *      tags 0 sigma init, 1 momenta, 2 pseudofermion sources, 3 Metropolis,
  *      6 observable noise.
+ *   R8 (Eq. (9)): with N_x = 2 both neighbours along an axis are one site and
+ *      both count (coefficient -2h).
+ *   R10 (Sec. 4.2, root ordering referenced but not given): the n conjugate
+ *      root pairs form real quadratic factors applied in the Leja order of
+ *      their centres.
+ *   R11 (Eq. (7), exact blocks): B = e^{-dtau K} e^{-dtau V} with e^{-dtau K}
+ *      = e^{hH} expanded to first or second order (link_order 1, 2).
+ *   R12 (MD beyond leapfrog): Omelyan's second-order minimum-norm scheme;
+ *      chronological initial guesses of the MD solves.
  *   R13 (observables, none named by the paper): noise estimators of
  *      diag(M^{-1}), whose diagonal blocks are the equal-time Green's
  *      functions (1 + B_tau ... B_{tau+1})^{-1} of the block form of Eq. (7).
