@@ -407,21 +407,28 @@ int hh_batch_autotune(const hh_request *sample, int n, size_t hbm_budget_bytes, 
  * HH_NOALLOC_SCRATCH_MB (about 9 MiB), which every device that loads the
  * library keeps until the process exits.
  *
- * hh_solve_noalloc solves Q x = b (Sec. 4.1; Q = M^T M of Eq. (10) built from
- * sigma with the parameters t, dtau, A of p) by FP64 CG with x0 = 0, one
- * right-hand side, the same algorithm and stopping test as hh_solve.
+ * hh_solve_noalloc solves Q x = b, Q = M^T M with M built from sigma and the
+ * parameters t, dtau, A of p exactly as for a context (link_order 0), by FP64
+ * CG with x0 = 0 and one right-hand side: the same algorithm and stopping
+ * test (true relative residual <= cg_tol) as hh_solve.
  *   lat, p:  lattice and parameters; p->precision must be HH_FP64, and
  *            N = Nx^d * Ntau must not exceed HH_NOALLOC_MAX_SITES, else the
  *            call returns HH_ESIZE without touching the device.
  *   sigma, b, x: device pointers to N doubles owned by the caller.
  *   cuda_stream: the cudaStream_t to run on (NULL: legacy default stream).
- *   info: if non-NULL the call synchronises the stream and fills it.
- * The first call on a device looks up the array's device address and the
- * kernel's occupancy; make that first call before any stream capture.
+ *   info: if non-NULL the call synchronises the stream and fills it, and
+ *            returns the solve's status (HH_ENOCONV, HH_ETIMEOUT, HH_ENUMERIC).
+ *            It must be NULL while the stream is being captured (the
+ *            synchronisation is not allowed there; HH_EINVAL).  With info
+ *            NULL the call only enqueues the work and returns HH_OK: the
+ *            solve's outcome is not reported, and the next call overwrites
+ *            it in the shared array.
+ * Every call looks up the array's device address, which stays valid if the
+ * caller resets the device; the first call on a device also queries the
+ * kernel's occupancy: make that first call before any stream capture.
  * The call allocates no device or host memory.  All calls share the array and
  * overwrite it (the call clears what must start at zero); calls whose GPU work
- * overlaps in time race on it and must be serialised by the caller.
- * Returns the same codes as hh_solve, plus HH_ESIZE. */
+ * overlaps in time race on it and must be serialised by the caller. */
 #define HH_ESIZE (-8) /* problem larger than the static scratch of hh_solve_noalloc */
 #define HH_NOALLOC_MAX_SITES 262144
 #define HH_NOALLOC_SCRATCH_MB 9

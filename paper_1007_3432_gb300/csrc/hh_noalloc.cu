@@ -12,10 +12,18 @@
 // library for as long as the process lives.
 //
 // The array is shared by all calls: each call overwrites it, and the parts
-// that must start from zero (barrier counter, engine state) are cleared by the
-// call itself.  Calls whose GPU work overlaps (two host threads, or two
-// streams running at once) race on the array and give wrong results; callers
-// must serialise them.
+// that must start from a known value (the engine's signal slots, both engine
+// state buffers, and the control block's error word and iteration counters)
+// are reset by the call itself.  Calls whose GPU work overlaps (two host
+// threads, or two streams running at once) race on the array and give wrong
+// results; callers must serialise them.
+//
+// The array's device address is looked up on every call
+// (cudaGetSymbolAddress, which allocates nothing): a caller that resets the
+// device, or otherwise re-creates its primary context, gets the library's
+// module loaded again and the array may then live at another address.  Only
+// the engine's co-resident grid size, a property of the device, is kept
+// between calls.
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -53,26 +61,25 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-unsigned char *g_scratch_addr[kMaxDevices];
-int g_max_grid[kMaxDevices][2];   // engine grid for d = 1 and d = 3
+int g_max_grid[kMaxDevices][2];   // engine grid for d = 1 and d = 3 (0: not yet queried)
 
-// Once per device, with that device current: the device address of the
-// scratch array (the host-side symbol is only a stand-in) and the engine's
-// co-resident grid size.
+// With the device 'dev' current: the device address of the scratch array
+// (the host-side symbol is only a stand-in for it), looked up on every call,
+// and the engine's co-resident grid size, queried on the first call on that
+// device and kept.
 int setup_device(int dev, int d, unsigned char **base, int *max_grid)
 {
     if (dev < 0 || dev >= kMaxDevices) return HH_EINVAL;
+    void *addr = nullptr;
+    if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) return HH_ECUDA;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *addr = nullptr;
-        if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) return HH_ECUDA;
+    if (g_max_grid[dev][0] <= 0) {
         int g1 = engine_default_grid(ENGINE_D1), g3 = engine_default_grid(ENGINE_D3);
         if (g1 <= 0 || g3 <= 0) return HH_ECUDA;
         g_max_grid[dev][0] = g1;
         g_max_grid[dev][1] = g3;
-        g_scratch_addr[dev] = (unsigned char *)addr;
     }
-    *base = g_scratch_addr[dev];
+    *base = (unsigned char *)addr;
     *max_grid = g_max_grid[dev][d == 1 ? 0 : 1];
     return HH_OK;
 }
@@ -147,6 +154,13 @@ extern "C" int hh_solve_noalloc(const hh_lattice *lat, const hh_params *p, const
     long long N = V * lat->ntau;
     if (N > kMaxSites) return HH_ESIZE;
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (info) {
+        // Filling info copies the outcome to the host and synchronises the
+        // stream, which a stream being captured into a graph does not allow.
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return HH_ECUDA;
+        if (cap != cudaStreamCaptureStatusNone) return HH_EINVAL;
+    }
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return HH_ECUDA;
