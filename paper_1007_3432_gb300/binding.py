@@ -132,6 +132,7 @@ def load(path: str = LIB_PATH):
         "hh_get_field": (i, [vp, vp, i]),
         "hh_init_field_random": (i, [vp, u64]),
         "hh_apply": (i, [vp, i, vp, vp, i]),
+        "hh_apply_multi": (i, [vp, i, vp, vp, i, i]),
         "hh_solve": (i, [vp, vp, vp, i, ctypes.POINTER(hh_solve_info)]),
         "hh_solve_guess": (i, [vp, vp, vp, i, ctypes.POINTER(hh_solve_info)]),
         "hh_force": (i, [vp, vp, i, vp, ctypes.POINTER(hh_solve_info)]),
@@ -267,6 +268,13 @@ class Context:
             import torch
             dtype = HH_DTYPE_F32 if x.dtype == torch.float32 else HH_DTYPE_F64
         check(self._lib.hh_apply(self._h, op, _ptr(x), _ptr(y), dtype), "hh_apply")
+
+    def apply_multi(self, op, x, y, n_vec, dtype=None):
+        """y_v = op(x_v) for n_vec vectors stored back to back (hh_apply_multi)."""
+        if dtype is None:
+            import torch
+            dtype = HH_DTYPE_F32 if x.dtype == torch.float32 else HH_DTYPE_F64
+        check(self._lib.hh_apply_multi(self._h, op, _ptr(x), _ptr(y), n_vec, dtype), "hh_apply_multi")
 
     def solve(self, b, x, n_rhs=1, info=True, allow=(), guess=False):
         """guess: start from the x passed in (hh_solve_guess) instead of zero."""

@@ -26,4 +26,14 @@ size_t fused_mtm_smem(int nx, int tz);
 cudaError_t launch_mtm_fused_f32(const Geo &g, float h, const float *L, const float *x, float *y, int *err,
                                  int nsm, cudaStream_t st);
 
+// Whether the multi-vector FP32 d = 3 Q kernel applies to this lattice and
+// these pointers (4 | Nx, Nx <= 32, 16-byte alignment).
+bool multi_mtm_ok(const Geo &g, const void *L, const void *x, const void *y);
+
+// y_v = M^T M x_v for the k FP32 vectors x_v = x + v N (y likewise) in one
+// persistent launch that reads the links once (hh_apply_multi.cu).  *err is
+// set to HH_ETIMEOUT if a bounded wait ran out (timeout_ns each).
+cudaError_t launch_mtm_multi_f32(const Geo &g, float h, const float *L, const float *x, float *y, int k, int *err,
+                                 int nsm, long long timeout_ns, cudaStream_t st);
+
 }  // namespace hh

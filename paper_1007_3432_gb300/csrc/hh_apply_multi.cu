@@ -1,0 +1,548 @@
+// Q = M^T M (Eq. (10); Q applied as M then M^T, Sec. 4.3) on k FP32 vectors
+// that share one field, d = 3: y_v = Q x_v for v = 0 .. k-1 in one persistent
+// launch.
+//
+// Work split.  The lattice is cut into z-slabs of TZ planes (all x, y); CTA b
+// owns slab b % nslab and, in that slab, a contiguous range of the k N_tau
+// (vector, time slice) pairs u = v N_tau + tau, range b / nslab of m equal
+// ranges.  All slabs use the same m ranges, so the CTAs of neighbouring slabs
+// work on the same (vector, slice) at about the same time and the halo planes
+// one CTA copies are the core planes its neighbours have just brought into L2.
+// The links are read with an L2 evict-last policy (every vector reads them;
+// they stay in L2 for the launch) and q is stored with evict-first (written
+// once), so HBM sees every x_v and the links once and every y_v once:
+// (8 k + 4) bytes per site.
+//
+// A CTA marches its range in time slices with the paper's thread blocking
+// (Sec. 4.3: shared-memory tiles with a boundary layer), laid out as a TMA
+// pipeline:
+//  * per step, x(tau + 1) on the slab plus two halo planes arrives in one of
+//    NS shared-memory stages by 1-D TMA bulk copies completing on an mbarrier.
+//    Thread 0 issues them: the first NS stages up front, then the stage NS
+//    ahead right after each step's barrier (the barrier proves the slot's
+//    previous stage has been read); it also prefetches later stages (x and
+//    the links) into L2;
+//  * the threads build t(tau + 1) = (M x)(tau + 1) on the slab plus one halo
+//    plane.  A thread owns one float4 group of one (x, y) row in one part of
+//    the slab's planes and streams z with the z neighbours in registers; the
+//    x(tau) of the link term is carried in registers from the previous step,
+//    and the links L(tau) of its planes are loaded into registers at the start
+//    of the step, so that their L2 round trip overlaps the wait for the stage.
+//    As soon as t(tau + 1) is known on a core plane, the thread writes q(tau)
+//    = t(tau) - h hop t(tau) + L(tau) t(tau + 1) there, from the shared-memory
+//    copy of t(tau) (written in the previous step) and the registers holding
+//    L(tau) and t(tau + 1).  Two t buffers alternate, so one barrier per step
+//    orders the writes of t(tau + 1) against the reads of t(tau).  The
+//    stencil sums run in packed FP32 pairs (two sites per instruction).
+// A segment of a range (one vector, slices [ta, tb)) takes tb - ta + 2 steps:
+// x(ta - 1) into the carry registers, t(ta), then one step per q slice.
+//
+// Every wait is bounded in time; on expiry the CTA records HH_ETIMEOUT, thread
+// 0 waits (bounded) for the copies in flight, and the CTA leaves.
+//
+// What bounds it (GB300, 32^3 x 128, 8 vectors): the shared-memory datapath.
+// Per site and vector the CTA moves about 55 bytes through shared memory (the
+// stage copies with their halo planes, the x and t rows of the y neighbours,
+// the t planes) against 8.5 bytes of HBM traffic; ncu shows the L1/shared
+// pipe at 72% when the kernel runs without its memory waits.
+#include <cstdlib>
+
+#include "hh_apply.cuh"
+#include "hh_slab.cuh"
+
+namespace hh {
+
+namespace {
+
+struct MultiCfg {
+    Geo g;
+    float h;
+    int nslab;          // Nx / TZ
+    int P;              // Nx * Nx
+    int k;              // vectors
+    int m;              // ranges (CTAs per slab)
+    int shfl;           // x halo by warp shuffles (else from shared memory)
+    int pf_ahead;       // L2 prefetch of the stage this many after the one being copied
+    long long timeout_ns;
+};
+
+constexpr int kPartThreads = 256;  // threads per part (one float4 group of each x-y row per thread)
+constexpr int kPrefetchAhead = 1;  // default L2 prefetch distance, in stages after the one being copied
+constexpr int kMaxRuns = 4;        // contiguous z runs of a slab's planes (periodic z, Nx >= 4)
+
+enum StageKind : int { STAGE_PRE = 0, STAGE_TFIRST = 1, STAGE_FULL = 2, STAGE_END = 3 };
+
+// A CTA's range [w, w1) of u = v * Ntau + tau as the sequence of its
+// pipeline stages (kind, v, tau'); the stage of tau' holds x_v(tau' + 1) and
+// works with L(tau').  A segment of slices [ta, tb) of one vector gives
+// tau' = ta - 2 (STAGE_PRE: x_v(ta - 1) for the carry), ta - 1 (STAGE_TFIRST:
+// t(ta)), then ta .. tb - 1 (STAGE_FULL: t(tau' + 1) and q(tau')).
+struct StageIter {
+    long long w, w1;
+    int ntau, vec, tau, ta, tb;
+    bool in_seg;
+
+    __device__ void init(long long a, long long b, int nt)
+    {
+        w = a;
+        w1 = b;
+        ntau = nt;
+        in_seg = false;
+    }
+
+    __device__ int next(int &v, int &tp)
+    {
+        if (!in_seg || tau >= tb) {
+            if (w >= w1) return STAGE_END;
+            vec = (int)(w / ntau);
+            ta = (int)(w - (long long)vec * ntau);
+            const long long rem = w1 - w;
+            tb = (rem < (long long)(ntau - ta)) ? ta + (int)rem : ntau;
+            w = (long long)vec * ntau + tb;
+            tau = ta - 2;
+            in_seg = true;
+        }
+        v = vec;
+        tp = tau;
+        const int kind = (tau == ta - 2) ? STAGE_PRE : (tau == ta - 1) ? STAGE_TFIRST : STAGE_FULL;
+        ++tau;
+        return kind;
+    }
+};
+
+// tau in [-ntau, 2 ntau) to [0, ntau).
+__device__ __forceinline__ int wrap_once(int t, int ntau)
+{
+    return t < 0 ? t + ntau : (t >= ntau ? t - ntau : t);
+}
+
+// Bounded wait on an mbarrier phase: false once budget_ns has passed or the
+// CTA has been told to abort.
+__device__ __forceinline__ bool wait_bounded(uint64_t *bar, unsigned parity, long long budget_ns,
+                                             const volatile int *abort)
+{
+    uint64_t t0 = 0;
+    unsigned spins = 0;
+    while (!mbar_try_wait(bar, parity)) {
+        if ((++spins & 31u) == 0) {
+            if (*abort) return false;
+            const uint64_t now = global_ns();
+            if (t0 == 0)
+                t0 = now;
+            else if ((long long)(now - t0) > budget_ns)
+                return false;
+        }
+    }
+    return true;
+}
+
+// Block-wide barrier that also ORs a flag over the block.  The two halves of
+// the block reach it from different code (one instantiation each), so it is
+// the non-.aligned form of the barrier, on its own id.
+constexpr int kBarBlock = 1;
+template <int NTHREADS>
+__device__ __forceinline__ int block_sync_or(int flag)
+{
+    int out;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.s32 q, %1, 0;\n\t"
+        "barrier.red.or.pred p, %2, %3, q;\n\t"
+        "selp.s32 %0, 1, 0, p;\n\t}"
+        : "=r"(out)
+        : "r"(flag), "r"(kBarBlock), "r"(NTHREADS)
+        : "memory");
+    return out;
+}
+
+template <int TZ, int NS>
+struct MultiLayout {
+    static constexpr int XPL = TZ + 4;   // x planes per stage
+    static constexpr int TPL = TZ + 2;   // t planes
+    static constexpr int TBUF = 2;
+    static size_t smem(int P)
+    {
+        return ((size_t)NS * XPL + (size_t)TBUF * TPL) * (size_t)P * sizeof(float);
+    }
+};
+
+// Contiguous runs of the periodic z range [z_first, z_first + count):
+// run r covers planes off[r] .. off[r] + n[r] - 1 of the range, starting at z[r].
+struct ZRuns {
+    int nr;
+    int z[kMaxRuns], off[kMaxRuns], n[kMaxRuns];
+
+    __device__ void init(int z_first, int count, int nx)
+    {
+        int zz = ((z_first % nx) + nx) % nx, done = 0;
+        nr = 0;
+        while (done < count && nr < kMaxRuns) {
+            int run = count - done;
+            if (zz + run > nx) run = nx - zz;
+            z[nr] = zz;
+            off[nr] = done;
+            n[nr] = run;
+            ++nr;
+            done += run;
+            zz = 0;
+        }
+    }
+};
+
+// Issues the copies of the stages of a CTA's range in order (thread 0 only;
+// the state lives in shared memory): stage j goes to slot j % NS, whose
+// previous stage j - NS must have been read.
+template <int TZ, int NS>
+struct Issuer {
+    StageIter it, pf;
+    ZRuns xr, lr;        // runs of the x planes and of the link planes of the slab
+    long long issued;
+    int done;
+
+    __device__ void init(long long w0, long long w1, const MultiCfg &c, const float *x, const float *L, int z0)
+    {
+        it.init(w0, w1, c.g.ntau);
+        pf.init(w0, w1, c.g.ntau);
+        xr.init(z0 - 2, TZ + 4, c.g.nx);
+        lr.init(z0 - 1, TZ + 2, c.g.nx);
+        issued = 0;
+        done = 0;
+        // the prefetch iterator runs kPrefetchAhead stages ahead of the copies
+        int v, tp;
+        pf.next(v, tp);
+        for (int a = 1; a <= c.pf_ahead; ++a) prefetch_next(c, x, L);
+    }
+
+    __device__ void prefetch_next(const MultiCfg &c, const float *x, const float *L)
+    {
+        int v, tp;
+        const int kind = pf.next(v, tp);
+        if (kind == STAGE_END) return;
+        const int P = c.P;
+        const float *xb = x + (size_t)v * c.g.N + (size_t)wrap_once(tp + 1, c.g.ntau) * c.g.V;
+        for (int r = 0; r < xr.nr; ++r)
+            bulk_prefetch_l2(xb + (size_t)xr.z[r] * P, (unsigned)(xr.n[r] * P * sizeof(float)));
+        if (kind != STAGE_PRE) {
+            const float *lb = L + (size_t)wrap_once(tp, c.g.ntau) * c.g.V;
+            for (int r = 0; r < lr.nr; ++r)
+                bulk_prefetch_l2(lb + (size_t)lr.z[r] * P, (unsigned)(lr.n[r] * P * sizeof(float)));
+        }
+    }
+
+    // Issue every stage j <= upto that has not been issued yet.
+    __device__ void issue_upto(long long upto, const MultiCfg &c, float *XS, uint64_t *full, const float *x,
+                               const float *L)
+    {
+        constexpr int XPL = TZ + 4;
+        const int P = c.P;
+        const unsigned stage_bytes = (unsigned)XPL * (unsigned)P * (unsigned)sizeof(float);
+        while (!done && issued <= upto) {
+            int v, tau;
+            if (it.next(v, tau) == STAGE_END) {
+                done = 1;
+                break;
+            }
+            const int slot = (int)(issued % NS);
+            const float *xb = x + (size_t)v * c.g.N + (size_t)wrap_once(tau + 1, c.g.ntau) * c.g.V;
+            float *dst = XS + (size_t)slot * XPL * P;
+            mbar_expect_tx(&full[slot], stage_bytes);
+            for (int r = 0; r < xr.nr; ++r)
+                bulk_g2s(dst + (size_t)xr.off[r] * P, xb + (size_t)xr.z[r] * P,
+                         (unsigned)(xr.n[r] * P * sizeof(float)), &full[slot]);
+            ++issued;
+            prefetch_next(c, x, L);
+        }
+    }
+};
+
+// One plane of the stencil c - h hop(c) + l o for a float4 group of x sites
+// in packed FP32 pairs (sites 0, 1 and 2, 3): the x neighbours are the
+// group's own lanes plus xm, xp, the y neighbours yp, ym, the z neighbours
+// a(bove), b(elow).  The sums are taken in the order
+// ((x- + x+) + (y+ + y-)) + (z+ + z-), each lane rounded as in FP32.
+__device__ __forceinline__ float4 stencil_x2(const float4 &c, const float4 &b, const float4 &a, const float4 &yp,
+                                             const float4 &ym, float xm, float xp, const float4 &l,
+                                             const float4 &o, const float2 mh)
+{
+    const float2 mid = make_float2(c.y, c.z);
+    float2 s0 = __fadd2_rn(make_float2(xm, c.x), mid);
+    float2 s1 = __fadd2_rn(mid, make_float2(c.w, xp));
+    s0 = __fadd2_rn(s0, __fadd2_rn(make_float2(yp.x, yp.y), make_float2(ym.x, ym.y)));
+    s1 = __fadd2_rn(s1, __fadd2_rn(make_float2(yp.z, yp.w), make_float2(ym.z, ym.w)));
+    s0 = __fadd2_rn(s0, __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y)));
+    s1 = __fadd2_rn(s1, __fadd2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w)));
+    const float2 r0 = __ffma2_rn(make_float2(l.x, l.y), make_float2(o.x, o.y),
+                                 __ffma2_rn(mh, s0, make_float2(c.x, c.y)));
+    const float2 r1 = __ffma2_rn(make_float2(l.z, l.w), make_float2(o.z, o.w),
+                                 __ffma2_rn(mh, s1, make_float2(c.z, c.w)));
+    return make_float4(r0.x, r0.y, r1.x, r1.y);
+}
+
+// The per-thread part of the march for one of PARTS parts of the slab's
+// planes (PARTS = 2: PART 0 has t planes [0, TPL/2) and core planes
+// [0, TZ/2), PART 1 the rest; PARTS = 1: all), compiled per part so that
+// every register array is indexed by constants.  NX > 0 fixes N_x at compile
+// time (plane offsets become immediates); NX = 0 reads it from c.
+template <int NX, int TZ, int NS, int PARTS, int PART>
+__device__ __forceinline__ void multi_consumer(const MultiCfg &c, float *XS, float *TS, uint64_t *full,
+                                               volatile int *abort, void *issuer_mem, long long w0, long long w1,
+                                               const float *__restrict__ x, const float *__restrict__ L,
+                                               float *__restrict__ y, int slab, int *err)
+{
+    constexpr int TPL = TZ + 2, XPL = TZ + 4, TH = TPL / PARTS, CH = TZ / PARTS;
+    constexpr int NTHREADS = kPartThreads * PARTS;
+    constexpr int TLO = PART * TH;   // first t plane of this part
+    constexpr int CLO = PART * CH;   // first core plane (core plane cc is t plane cc + 1)
+    constexpr int PC0 = CLO + 1, PC1 = CLO + CH;   // core t planes of this part
+    const int nx = NX ? NX : c.g.nx;
+    const int P = nx * nx, ntau = c.g.ntau, V = NX ? NX * NX * NX : c.g.V;
+    const size_t N = (size_t)c.g.N;
+    const int lane = (int)threadIdx.x & 31;
+    const int col = (int)threadIdx.x - PART * kPartThreads;
+    const int G = P / 4;
+    const bool active = col < G;     // Nx <= 32: at most one group per thread
+    const PlaneGroup q = plane_group(active ? col : 0, nx);
+    const int gpr = nx / 4, jx = lane % gpr;
+    const bool shfl = NX ? ((32 % (NX / 4) == 0) && ((NX * NX / 4) % 32 == 0)) : (c.shfl != 0);
+    const int src_m = (jx == 0) ? lane + gpr - 1 : lane - 1;
+    const int src_p = (jx == gpr - 1) ? lane - gpr + 1 : lane + 1;
+    const float2 mh = make_float2(-c.h, -c.h);
+    const int z0 = slab * TZ;
+    const uint64_t pol_y = l2_policy_evict_first();
+    const uint64_t pol_l = l2_policy_evict_last();
+    // In-slice offsets of this thread's group in each of its part's t planes
+    // (t plane p is z = z0 - 1 + p, periodic).
+    int loff[TH];
+#pragma unroll
+    for (int pp = 0; pp < TH; ++pp) {
+        int z = z0 - 1 + TLO + pp;
+        z = z < 0 ? z + nx : (z >= nx ? z - nx : z);
+        loff[pp] = z * P + q.s;
+    }
+    auto halo = [&](const float *pl, const float4 &self, float &hm, float &hp) {
+        if (shfl) {
+            hm = __shfl_sync(0xffffffffu, self.w, src_m);
+            hp = __shfl_sync(0xffffffffu, self.x, src_p);
+        } else {
+            hm = pl[q.xm];
+            hp = pl[q.xp];
+        }
+    };
+
+    // Thread 0 issues the copies: the first NS stages now.
+    const bool issuer = PART == 0 && threadIdx.x == 0;
+    Issuer<TZ, NS> &is = *static_cast<Issuer<TZ, NS> *>(issuer_mem);
+    if (issuer) {
+        is.init(w0, w1, c, x, L, z0);
+        is.issue_upto(NS - 1, c, XS, full, x, L);
+    }
+
+    float4 xc[TH];   // x(tau) at this thread's group of each of the part's t planes (link term)
+    float4 lc[TH];   // L(tau') of the current stage at the part's t planes
+    StageIter it;
+    it.init(w0, w1, ntau);
+    int slot = 0;
+    unsigned phase = 0;   // parity of the slot's current use
+    long long j = 0;      // stage index
+    int cb = 0;           // t buffer holding t(tau)
+    int failed = 0;       // warp-uniform: a wait of this warp ran out
+    bool aborted = false; // block-uniform: some warp's wait ran out
+    for (;;) {
+        int v, tau;
+        const int kind = it.next(v, tau);
+        if (kind == STAGE_END) break;
+        // The links of this stage: their L2 round trip overlaps the wait.
+        if (kind != STAGE_PRE && active) {
+            const float *lb = L + (size_t)wrap_once(tau, ntau) * V;
+#pragma unroll
+            for (int pp = 0; pp < TH; ++pp) lc[pp] = ldg4_hint(lb + loff[pp], pol_l);
+        }
+        if (!failed) {
+            const bool ok = wait_bounded(&full[slot], phase, c.timeout_ns, abort);
+            failed = __all_sync(0xffffffffu, ok) ? 0 : 1;
+            if (failed && lane == 0) {
+                *abort = 1;
+                atomicCAS(err, 0, -6);
+            }
+        }
+        const float *X = XS + (size_t)slot * XPL * P;
+        if (!failed && active) {
+            const float *xs = X + q.s, *xyp = X + q.yp, *xym = X + q.ym;
+            if (kind == STAGE_PRE) {
+#pragma unroll
+                for (int pp = 0; pp < TH; ++pp) xc[pp] = ld4(xs + (TLO + pp + 1) * P);
+            } else {
+                // t(tau + 1) on the part's t planes (t plane p is the slab's
+                // z0 - 1 + p; x planes p, p + 1, p + 2 are z - 1, z, z + 1) and,
+                // on a full step, q(tau) on each core plane p - 1 as soon as
+                // t(tau + 1) at p is known: q needs t(tau) at t planes p - 1,
+                // p, p + 1 (buffer cb, written last step) and, at the site
+                // itself, t(tau + 1) and L(tau).
+                const bool full_step = kind == STAGE_FULL;
+                float *tn = TS + (size_t)(cb ^ 1) * TPL * P + q.s;
+                const float *T0 = TS + (size_t)cb * TPL * P;
+                const float *ts = T0 + q.s, *typ = T0 + q.yp, *tym = T0 + q.ym;
+                float *yo = y + (size_t)v * N + (size_t)(tau < 0 ? 0 : tau) * V + (size_t)z0 * P + q.s;
+                float4 below = ld4(xs + TLO * P), here = ld4(xs + (TLO + 1) * P);
+                float4 tb = make_float4(0.f, 0.f, 0.f, 0.f), th = tb;
+                if (full_step) {
+                    tb = ld4(ts + (PC0 - 1) * P);
+                    th = ld4(ts + PC0 * P);
+                }
+#pragma unroll
+                for (int pp = 0; pp < TH; ++pp) {
+                    const int p = TLO + pp;
+                    const float4 above = ld4(xs + (p + 2) * P);
+                    const float4 yp = ld4(xyp + (p + 1) * P), ym = ld4(xym + (p + 1) * P);
+                    float hm, hp;
+                    halo(X + (p + 1) * P, here, hm, hp);
+                    const float4 t = stencil_x2(here, below, above, yp, ym, hm, hp, lc[pp], xc[pp], mh);
+                    st4(tn + p * P, t);
+                    xc[pp] = here;
+                    below = here;
+                    here = above;
+                    if (p >= PC0 && p <= PC1 && full_step) {
+                        const float4 ta = ld4(ts + (p + 1) * P);
+                        const float4 gp = ld4(typ + p * P), gm = ld4(tym + p * P);
+                        float em, ep;
+                        halo(T0 + p * P, th, em, ep);
+                        st4_global_hint(yo + (p - 1) * P, stencil_x2(th, tb, ta, gp, gm, em, ep, lc[pp], t, mh),
+                                        pol_y);
+                        tb = th;
+                        th = ta;
+                    }
+                }
+            }
+        }
+        if (kind != STAGE_PRE) {
+            // Every stage up to j has now been read and t(tau + 1) written:
+            // stage j's slot can take stage j + NS.
+            if (block_sync_or<NTHREADS>(failed)) {
+                aborted = true;
+                break;
+            }
+            if (issuer) is.issue_upto(j + NS, c, XS, full, x, L);
+            cb ^= 1;
+        }
+        ++j;
+        if (++slot == NS) {
+            slot = 0;
+            phase ^= 1u;
+        }
+    }
+    if (issuer && aborted) {
+        // Copies in flight must land before the CTA ends (bounded wait; a
+        // phase that has already completed returns at once).
+        const int never = 0;
+        for (long long jj = j; jj < is.issued; ++jj)
+            wait_bounded(&full[(int)(jj % NS)], (unsigned)((jj / NS) & 1), c.timeout_ns, &never);
+    }
+}
+
+// TZ: core z planes of a slab; NS: pipeline stages; PARTS: parts of the
+// slab's planes (256 threads each); MINB: CTAs per SM.
+template <int NX, int TZ, int NS, int PARTS, int MINB>
+__global__ void __launch_bounds__(kPartThreads * PARTS, MINB)
+    k_mtm_multi_d3(const MultiCfg c, const float *__restrict__ L, const float *__restrict__ x,
+                   float *__restrict__ y, int *err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[NS];
+    __shared__ int s_abort;
+    __shared__ Issuer<TZ, NS> s_issuer;
+    using Lay = MultiLayout<TZ, NS>;
+    float *XS = (float *)smem_raw;                       // NS stages of x (XPL planes each)
+    float *TS = XS + (size_t)NS * Lay::XPL * c.P;        // two t buffers (TPL planes each)
+
+    const int slab = (int)blockIdx.x % c.nslab;
+    const int ci = (int)blockIdx.x / c.nslab;
+    const long long K = (long long)c.k * c.g.ntau;
+    const long long w0 = (long long)ci * K / c.m, w1 = (long long)(ci + 1) * K / c.m;
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < NS; ++b) mbar_init(&full[b], 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (PARTS == 1 || (int)threadIdx.x < kPartThreads)
+        multi_consumer<NX, TZ, NS, PARTS, 0>(c, XS, TS, full, &s_abort, &s_issuer, w0, w1, x, L, y, slab, err);
+    else
+        multi_consumer<NX, TZ, NS, PARTS, (PARTS > 1 ? 1 : 0)>(c, XS, TS, full, &s_abort, &s_issuer, w0, w1, x,
+                                                               L, y, slab, err);
+}
+
+template <int NX, int TZ, int NS, int PARTS, int MINB>
+cudaError_t launch_multi(MultiCfg c, int nsm, const float *L, const float *x, float *y, int *err, cudaStream_t st)
+{
+    const size_t smem = MultiLayout<TZ, NS>::smem(c.P);
+    auto kern = k_mtm_multi_d3<NX, TZ, NS, PARTS, MINB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    c.nslab = c.g.nx / TZ;
+    const int ctas = nsm * MINB;
+    c.m = ctas / c.nslab > 0 ? ctas / c.nslab : 1;
+    kern<<<c.m * c.nslab, kPartThreads * PARTS, smem, st>>>(c, L, x, y, err);
+    return cudaGetLastError();
+}
+
+// Pipeline forms (HH_APPLY_MULTI_FORM selects one):
+//   2 (default): 4-plane slabs, two stages, one part of 256 threads, two CTAs
+//      per SM (112 KB of shared memory each);
+//   1: 8-plane slabs, three stages, two parts, one CTA per SM (8 | Nx);
+//   3: 4-plane slabs, four stages, two parts, one CTA per SM.
+// Measured on GB300 (32^3 x 128, 8 vectors per launch): 2 and 1 take 94-98 us,
+// 3 takes 129 us.
+int multi_form(int nx)
+{
+    const char *e = getenv("HH_APPLY_MULTI_FORM");
+    const int forced = e ? atoi(e) : 0;
+    if (forced == 1 && nx % 8 == 0) return 1;
+    if (forced == 3) return 3;
+    return 2;
+}
+
+size_t multi_smem(int nx, int form)
+{
+    const int P = nx * nx;
+    return form == 1 ? MultiLayout<8, 3>::smem(P) : form == 2 ? MultiLayout<4, 2>::smem(P) : MultiLayout<4, 4>::smem(P);
+}
+
+}  // namespace
+
+bool multi_mtm_ok(const Geo &g, const void *L, const void *x, const void *y)
+{
+    if (g.d != 3 || g.nx % 4 != 0 || g.nx < 4 || g.nx > 32 || g.ntau < 2) return false;
+    if (((uintptr_t)L | (uintptr_t)x | (uintptr_t)y) & 15u) return false;
+    // dynamic shared memory, leaving 1 KB of the 227 KB for the static part
+    // (two CTAs per SM: half of it each)
+    const int form = multi_form(g.nx);
+    return multi_smem(g.nx, form) <= (form == 2 ? 112 : 226) * 1024;
+}
+
+cudaError_t launch_mtm_multi_f32(const Geo &g, float h, const float *L, const float *x, float *y, int k, int *err,
+                                 int nsm, long long timeout_ns, cudaStream_t st)
+{
+    if (k < 1) return cudaSuccess;
+    MultiCfg c;
+    c.g = g;
+    c.h = h;
+    c.P = g.nx * g.nx;
+    c.k = k;
+    const int G = c.P / 4, gpr = g.nx / 4;
+    c.shfl = (32 % gpr == 0) && (G % 32 == 0);
+    c.timeout_ns = timeout_ns;
+    const char *pfe = getenv("HH_APPLY_MULTI_PF");
+    c.pf_ahead = pfe ? atoi(pfe) : kPrefetchAhead;
+    const bool n32 = g.nx == 32;
+    switch (multi_form(g.nx)) {
+    case 1: return n32 ? launch_multi<32, 8, 3, 2, 1>(c, nsm, L, x, y, err, st)
+                       : launch_multi<0, 8, 3, 2, 1>(c, nsm, L, x, y, err, st);
+    case 2: return n32 ? launch_multi<32, 4, 2, 1, 2>(c, nsm, L, x, y, err, st)
+                       : launch_multi<0, 4, 2, 1, 2>(c, nsm, L, x, y, err, st);
+    default: return n32 ? launch_multi<32, 4, 4, 2, 1>(c, nsm, L, x, y, err, st)
+                        : launch_multi<0, 4, 4, 2, 1>(c, nsm, L, x, y, err, st);
+    }
+}
+
+}  // namespace hh

@@ -150,7 +150,9 @@ struct hh_ctx {
     int nsm;
     int mtm_path;           // Q apply path (HH_APPLY_MTM): 0 by size (see hh_apply), 1 two
                             // sweeps, 2 two sweeps with programmatic dependent launch, 3 the
-                            // fused FP32 d = 3 kernel where it applies
+                            // fused FP32 d = 3 kernel where it applies, 4 the multi-vector
+                            // FP32 d = 3 kernel (also for one vector); hh_apply_multi uses
+                            // the multi-vector kernel for two or more vectors unless 1-3
     double *z, *u;          // Chebyshev preconditioner vectors (cap_rhs each), or null
     double *d_cheb;         // its coefficient table
     // Observables: noise, M^T noise and solutions (obs_cap vectors each), the
@@ -690,7 +692,12 @@ int hh_apply(hh_ctx *c, int op, const void *x, void *y, int dtype)
             // memory, beyond that.
             const bool big = (long long)c->N * 16 > (96LL << 20);
             const bool fused = c->mtm_path == 3 || (c->mtm_path == 0 && big);
-            if (vec && fused && fused_mtm_ok(c->geo, c->L32, xf, yf)) {
+            if (vec && c->mtm_path == 4 && multi_mtm_ok(c->geo, c->L32, xf, yf)) {
+                // the multi-vector kernel with one vector (HH_APPLY_MTM=4)
+                HH_TRY(launch_mtm_multi_f32(c->geo, (float)h, c->L32, xf, yf, 1, c->d_apply_err, c->nsm,
+                                            c->timeout_ns, c->stream));
+                launches = 1;
+            } else if (vec && fused && fused_mtm_ok(c->geo, c->L32, xf, yf)) {
                 HH_TRY(launch_mtm_fused_f32(c->geo, (float)h, c->L32, xf, yf, c->d_apply_err, c->nsm, c->stream));
                 launches = 1;
             } else if (vec) {
@@ -714,6 +721,30 @@ int hh_apply(hh_ctx *c, int op, const void *x, void *y, int dtype)
         return HH_EINVAL;
     }
     c->n_launch += launches;
+    return HH_OK;
+}
+
+int hh_apply_multi(hh_ctx *c, int op, const void *x, void *y, int n_vec, int dtype)
+{
+    if (!c || !x || !y || n_vec < 1) return HH_EINVAL;
+    if (op != HH_OP_M && op != HH_OP_MT && op != HH_OP_MTM) return HH_EINVAL;
+    if (dtype != HH_DTYPE_F64 && dtype != HH_DTYPE_F32) return HH_EINVAL;
+    const size_t esz = dtype == HH_DTYPE_F64 ? sizeof(double) : sizeof(float);
+    const size_t span = (size_t)n_vec * (size_t)c->N * esz;
+    const uintptr_t xa = (uintptr_t)x, ya = (uintptr_t)y;
+    if (xa < ya + span && ya < xa + span) return HH_EINVAL;   // x and y overlap
+    if (op == HH_OP_MTM && dtype == HH_DTYPE_F32 && c->prm.link_order == 0 && n_vec >= 2 &&
+        (c->mtm_path == 0 || c->mtm_path == 4) && multi_mtm_ok(c->geo, c->L32, x, y)) {
+        HH_TRY(launch_mtm_multi_f32(c->geo, (float)(c->prm.t * c->prm.dtau), c->L32, (const float *)x,
+                                    (float *)y, n_vec, c->d_apply_err, c->nsm, c->timeout_ns, c->stream));
+        c->n_launch += 1;
+        return HH_OK;
+    }
+    for (int v = 0; v < n_vec; ++v) {
+        const size_t off = (size_t)v * (size_t)c->N * esz;
+        const int rc = hh_apply(c, op, (const char *)x + off, (char *)y + off, dtype);
+        if (rc) return rc;
+    }
     return HH_OK;
 }
 
