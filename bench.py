@@ -13,11 +13,19 @@ Q = M^T M once per right-hand side), with sigma resident on the device when a
 step's timed region starts.  e2e: the same count over wall time of the public
 calls hh_set_field(host) -> hh_trajectory -> hh_get_field(host) per step.
 
+After the timed trajectories the default line also carries, measured in the
+same run on the same GPU (--no-extras skips them): the FP32 M^T M apply on the
+d = 3, 32^3 x 128 lattice with 16 vectors per launch and with one
+(c2_apply_fp32_*), two-right-hand-side CG solves to 1e-10 on that lattice in
+FP64 and in mixed precision (c2_solves), and the 64-chain d = 3 batch in FP64
+and in mixed precision (batch64_d3), each with its own roofline.
+
 Further modes measure parts of the path (they print the same JSON line):
   --mode solve : a step is one CG solve of Q x = b for two right-hand sides
                  (value in solves/s), to compare FP64 with mixed precision;
-  --mode apply : a step is one M^T M apply with L2 flushed before it (value in
-                 applies/s), the HBM roofline of the stencil;
+  --mode apply : a step is one M^T M apply of --nvec vectors with L2 flushed
+                 before it (value in applies/s), the HBM roofline of the
+                 stencil;
   --mode batch : a step solves two right-hand sides for each of 64 d=3 chains of
                  uneven volume in the batched engine (autotuned), in solves/s;
   --mode serve : a Poisson stream of solve and trajectory requests at each rate
@@ -27,6 +35,7 @@ Further modes measure parts of the path (they print the same JSON line):
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                        [--workload c0|c1|c2] [--precision fp64|mixed]
                        [--mode trajectory|solve|apply|batch|serve] [--cg-maxit M]
+                       [--nvec K] [--no-extras] [--no-cpu]
 """
 import argparse
 import json
@@ -59,16 +68,22 @@ def flops_per_site(d, kind, precision):
     return 2 * m + 3 + (1 if precision == "mixed" else 0)
 
 
-# Bytes per site: a CG step reads r, p, p, L, t, L, x, p, r and writes p, t,
-# x, r (13 words); the minimum for one M^T M apply is x, L in and y out.
+# Algorithmic bytes per site of a CG step: the minimum traffic of the step as
+# the method states it, 11 words: p = r + beta p with q = Q p and <p, q> reads
+# r, p and the links and writes p, q; x += alpha p, r -= alpha q with <r, r>
+# reads x, p, r, q and writes x, r (88 B in FP64, 44 B in FP32; the 16-bit link
+# precisions read 2 bytes of link instead of 4).  The engine's kernel moves 13
+# words (t = M p is stored between the two sweeps of Q and the links are read
+# by both sweeps); the roofline fractions use the 11 algorithmic words.  A true-
+# residual step r = b - Q x reads x, the links and b and writes r (4 FP64
+# words), plus, in mixed precision, x32 read and written and r32 written.
 def bytes_per_site(kind, precision):
-    """Algorithmic bytes per site of a CG step (13 words; with 16-bit links the
-    two link reads take 2 bytes each) or of an FP64 true-residual step."""
+    """Algorithmic bytes per site of a CG step or of an FP64 true-residual step."""
     if kind == "cg":
         if precision == "fp64":
-            return 13 * 8
-        return 13 * 4 - (4 if precision.endswith("16link") else 0)
-    return 8 * 8 + (12 if precision != "fp64" else 0)
+            return 11 * 8
+        return 11 * 4 - (2 if precision.endswith("16link") else 0)
+    return 4 * 8 + (12 if precision != "fp64" else 0)
 
 
 # DRAM bytes per engine iteration (two right-hand sides) of the engine kernel
@@ -78,6 +93,11 @@ def bytes_per_site(kind, precision):
 # since the last captures (its per-system descriptor gained the 16-bit link
 # fields), so the bench lines report no traffic until the next capture.
 ENGINE_DRAM_PER_ITER = {}
+
+# DRAM bytes (read + write) per launch of the Q apply from one ncu capture each
+# (profiles/mtm_*): (workload, dtype, vectors per launch) -> bytes.
+APPLY_DRAM_PER_LAUNCH = {("d3_nx32_nt128", "fp32", 1): 33557760 + 344320 + 88320 + 6871040,
+                         ("d3_nx32_nt128", "fp32", 16): 301937664 + 229500160}
 
 
 def engine_traffic(wl, precision, cheb, cnt):
@@ -269,7 +289,10 @@ def run_reference(args, wl, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_of(args, wl),
+            "data": "synthetic",
+            "config": dict(config_of(args, wl),
+                           step="about %.0f s of the oracle's FP64 CG iterations (Q applies) on a Gaussian b, "
+                                "same lattice and field" % per_step),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": samples[-1] if samples else ""},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -300,115 +323,183 @@ class L2Flush:
         self.r.sum()
 
 
-def run_part(args, wl, world, rank, local, dev, stream):
-    """--mode solve / --mode apply: one CG solve (2 right-hand sides) or one
-    M^T M apply per step, each bracketed by CUDA events on the context stream,
-    L2 flushed before every step."""
+def measure_solve(wl, precision, rank, dev, stream, steps, warmup, flush, cg_maxit=1000000, cheb=0,
+                  cheb_eps=1e-4):
+    """CG solves of Q x = b for two right-hand sides b ~ N(0, 1) on workload wl,
+    each CUDA-event timed on the context stream with L2 flushed before it, the
+    host -> device copy of b before and the device -> host copy of x after the
+    timed call (counted in e2e).  Returns the rates, the engine roofline and the
+    per-step device and wall times."""
     import torch
-    from paper_1007_3432_gb300 import HH_OP_MTM, Context
-    from paper_1007_3432_gb300.binding import HH_ENOCONV
+    from paper_1007_3432_gb300 import Context
     n = wl.nsites
-    ctx = Context(wl.d, wl.nx, wl.ntau, seed=wl.seed, chain_id=rank, precision=args.precision,
-                  cg_maxit=args.cg_maxit, stream=stream, cheb_degree=args.cheb, cheb_eps=args.cheb_eps)
+    ctx = Context(wl.d, wl.nx, wl.ntau, seed=wl.seed, chain_id=rank, precision=precision,
+                  cg_maxit=cg_maxit, stream=stream, cheb_degree=cheb, cheb_eps=cheb_eps)
     ctx.set_field(torch.from_numpy(workloads.sigma_field(n, seed=wl.seed, chain=rank)).to(dev))
-    flush = L2Flush(dev)
-    if args.mode == "solve":
-        b_h = np.stack([workloads.source(n, seed=wl.seed, chain=rank, rhs=a) for a in range(2)])
-        b = torch.from_numpy(b_h).to(dev)
-        x = torch.zeros_like(b)
-        x_h = torch.empty(b.shape, dtype=torch.float64).pin_memory()
-        b_pin = torch.from_numpy(b_h).pin_memory()
-    else:
-        dt = torch.float64 if args.precision == "fp64" else torch.float32
-        xs = torch.from_numpy(workloads.source(n, seed=wl.seed, chain=rank)).to(dev).to(dt)
-        ys = torch.empty_like(xs)
+    b_h = np.stack([workloads.source(n, seed=wl.seed, chain=rank, rhs=a) for a in range(2)])
+    b = torch.from_numpy(b_h).to(dev)
+    x = torch.zeros_like(b)
+    x_h = torch.empty(b.shape, dtype=torch.float64).pin_memory()
+    b_pin = torch.from_numpy(b_h).pin_memory()
+    infos = []
 
-    def one(timed):
+    def one():
         flush()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         w0 = time.perf_counter()
-        if args.mode == "solve":
-            b.copy_(b_pin, non_blocking=True)      # host -> device input
-            e0.record(stream)
-            ctx.solve(b, x, 2, info=False)
-            e1.record(stream)
-            x_h.copy_(x, non_blocking=True)        # device -> host result
-        else:
-            e0.record(stream)
-            ctx.apply(HH_OP_MTM, xs, ys)
-            e1.record(stream)
+        b.copy_(b_pin, non_blocking=True)      # host -> device input
+        e0.record(stream)
+        rc, inf = ctx.solve(b, x, 2, info=True)
+        e1.record(stream)
+        x_h.copy_(x, non_blocking=True)        # device -> host result
         torch.cuda.synchronize(dev)
+        infos.append(inf)
         return e0.elapsed_time(e1), (time.perf_counter() - w0) * 1000.0
 
-    for _ in range(args.warmup):
-        one(False)
+    for _ in range(warmup):
+        one()
+    infos.clear()
     ctx.counters_reset(profile_engine=True)
-    clocks = ClockSampler(local)
-    clocks.start()
     dev_ms, wall_ms = [], []
-    for _ in range(args.steps):
-        a, w = one(True)
+    for _ in range(steps):
+        a, w = one()
         dev_ms.append(a)
         wall_ms.append(w)
-    clk = clocks.stop()
     cnt = ctx.counters()
+    ctx.close()
     peaks, src = measured_peaks()
-    t_dev = max_over_ranks(world, sum(dev_ms) / 1000.0)
-    t_wall = max_over_ranks(world, sum(wall_ms) / 1000.0)
-    if args.mode == "solve":
-        units = sum_over_ranks(world, float(cnt["solves"]))
-        unit = "CG solves/s"
-        eng_s = cnt["engine_ms"] / 1000.0
-        # With the Chebyshev preconditioner every CG step and true-residual check
-        # is followed by 2n sub-steps, each one Q apply with its vector update
-        # (counted at the flops of a CG step).
-        q_per_step = 2 * args.cheb + 1
-        if args.precision == "fp64":
-            flops = n * (cnt["cg_steps"] * flops_per_site(wl.d, "cg", "fp64") + cnt["ru_steps"] * flops_per_site(wl.d, "ru", "fp64"))
-            flops += n * (cnt["cg_steps"] + cnt["ru_steps"]) * (q_per_step - 1) * flops_per_site(wl.d, "cg", "fp64")
-            ach = flops / eng_s / 1e12
-            roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak_tflops(), "unit": "TFLOP/s",
-                    "frac": ach / fp64_peak_tflops(), "traffic": engine_traffic(wl, args.precision, args.cheb, cnt),
-                    "kernel": "engine_kernel (FP64 CG)"}
-        else:
-            byts = n * (cnt["cg_steps"] * bytes_per_site("cg", args.precision)
-                        + cnt["ru_steps"] * bytes_per_site("ru", args.precision))
-            ach = byts / eng_s / 1e9
-            roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": engine_traffic(wl, args.precision, args.cheb, cnt),
-                    "kernel": "engine_kernel (FP32-inner CG)"}
-        extra = {"cg_steps_per_solve": cnt["cg_steps"] / max(1, cnt["solves"]),
-                 "q_applies_per_solve": (cnt["cg_steps"] + cnt["ru_steps"]) * q_per_step / max(1, cnt["solves"]),
-                 "ru_steps": cnt["ru_steps"], "fp64_steps": cnt["fp64_steps"], "cheb_degree": args.cheb}
-        e2e_bytes = (n * 16, n * 16)
+    eng_s = cnt["engine_ms"] / 1000.0
+    # With the Chebyshev preconditioner every CG step and true-residual check
+    # is followed by 2n sub-steps, each one Q apply with its vector update
+    # (counted at the flops of a CG step).
+    q_per_step = 2 * cheb + 1
+    if precision == "fp64":
+        flops = n * (cnt["cg_steps"] * flops_per_site(wl.d, "cg", "fp64") + cnt["ru_steps"] * flops_per_site(wl.d, "ru", "fp64"))
+        flops += n * (cnt["cg_steps"] + cnt["ru_steps"]) * (q_per_step - 1) * flops_per_site(wl.d, "cg", "fp64")
+        ach = flops / eng_s / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak_tflops(), "unit": "TFLOP/s",
+                "frac": ach / fp64_peak_tflops(), "traffic": engine_traffic(wl, precision, cheb, cnt),
+                "kernel": "engine_kernel (FP64 CG)",
+                "peak_source": "FP64 from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz)"}
     else:
-        units = float(world * args.steps)
+        byts = n * (cnt["cg_steps"] * bytes_per_site("cg", precision)
+                    + cnt["ru_steps"] * bytes_per_site("ru", precision))
+        ach = byts / eng_s / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": engine_traffic(wl, precision, cheb, cnt),
+                "kernel": "engine_kernel (FP32-inner CG)",
+                "peak_source": "%s MEASURED_PEAKS.json hbm_gbs" % src,
+                "algorithmic_bytes_per_site_cg_step": bytes_per_site("cg", precision)}
+    t_dev = sum(dev_ms) / 1000.0
+    t_wall = sum(wall_ms) / 1000.0
+    return {"workload": wl.name, "precision": precision, "solves": cnt["solves"],
+            "solves_per_s": cnt["solves"] / t_dev, "e2e_solves_per_s": cnt["solves"] / t_wall,
+            "ms_per_step": 1000.0 * t_dev / steps, "dev_s": t_dev, "wall_s": t_wall,
+            "cg_steps_per_solve": cnt["cg_steps"] / max(1, cnt["solves"]),
+            "q_applies_per_solve": (cnt["cg_steps"] + cnt["ru_steps"]) * q_per_step / max(1, cnt["solves"]),
+            "ru_steps": cnt["ru_steps"], "fp64_steps": cnt["fp64_steps"], "cheb_degree": cheb,
+            "max_true_relres": max(i["true_relres"] for i in infos), "all_converged": all(i["converged"] for i in infos),
+            "gpu_launches": int(cnt["kernel_launches"]), "roofline": roof,
+            "e2e_bytes": (n * 16, n * 16)}
+
+
+def measure_apply(wl, precision, nvec, rank, dev, stream, steps, warmup, flush):
+    """One M^T M apply of nvec vectors per step (hh_apply for one vector,
+    hh_apply_multi for more), CUDA-event timed with L2 flushed before it."""
+    import torch
+    from paper_1007_3432_gb300 import HH_OP_MTM, Context
+    n = wl.nsites
+    ctx = Context(wl.d, wl.nx, wl.ntau, seed=wl.seed, chain_id=rank, precision=precision, stream=stream)
+    ctx.set_field(torch.from_numpy(workloads.sigma_field(n, seed=wl.seed, chain=rank)).to(dev))
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    xs = torch.from_numpy(np.concatenate([workloads.source(n, seed=wl.seed, chain=rank, rhs=a)
+                                          for a in range(nvec)])).to(dev).to(dt)
+    ys = torch.empty_like(xs)
+
+    def one():
+        flush()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if nvec == 1:
+            ctx.apply(HH_OP_MTM, xs, ys)
+        else:
+            ctx.apply_multi(HH_OP_MTM, xs, ys, nvec)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1)
+
+    for _ in range(warmup):
+        one()
+    ctx.counters_reset()
+    dev_ms = [one() for _ in range(steps)]
+    cnt = ctx.counters()     # raises if a bounded device-side wait ran out
+    ctx.close()
+    peaks, src = measured_peaks()
+    # x_v and y_v once per vector, the links once per launch (multi-vector
+    # kernel, FP32 d = 3); separate applies read the links per vector.
+    multi = nvec > 1 and precision != "fp64" and wl.d == 3
+    bps = 24 * nvec if precision == "fp64" else (8 * nvec + 4 if multi else 12 * nvec)
+    t_dev = sum(dev_ms) / 1000.0
+    ach = steps * n * bps / t_dev / 1e9
+    traffic = APPLY_DRAM_PER_LAUNCH.get((wl.name, "fp64" if precision == "fp64" else "fp32", nvec))
+    roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "traffic": traffic,
+            "kernel": ("k_mtm_multi_d3 (FP32, %d vectors per launch)" % nvec) if multi else
+                      "M^T M apply (%s, %d vector%s)" % ("FP64" if precision == "fp64" else "FP32", nvec,
+                                                        "s" if nvec > 1 else ""),
+            "peak_source": "%s MEASURED_PEAKS.json hbm_gbs" % src,
+            "algorithmic_bytes_per_launch_site": bps}
+    return {"workload": wl.name, "precision": "fp64" if precision == "fp64" else "fp32", "vectors_per_launch": nvec,
+            "applies_per_s": steps * nvec / t_dev, "median_launch_us": 1000.0 * float(np.median(dev_ms)),
+            "dev_s": t_dev, "gpu_launches": int(cnt["kernel_launches"]), "roofline": roof,
+            "l2": "flushed before every launch (512 MiB write, then 512 MiB read)"}
+
+
+def run_part(args, wl, world, rank, local, dev, stream):
+    """--mode solve / --mode apply: one CG solve (2 right-hand sides) or one
+    M^T M apply of --nvec vectors per step, each bracketed by CUDA events on the
+    context stream, L2 flushed before every step."""
+    flush = L2Flush(dev)
+    clocks = ClockSampler(local)
+    if args.mode == "solve":
+        clocks.start()
+        r = measure_solve(wl, args.precision, rank, dev, stream, args.steps, args.warmup, flush, args.cg_maxit,
+                          args.cheb, args.cheb_eps)
+        clk = clocks.stop()
+        t_dev = max_over_ranks(world, r["dev_s"])
+        t_wall = max_over_ranks(world, r["wall_s"])
+        units = sum_over_ranks(world, float(r["solves"]))
+        unit = "CG solves/s"
+        extra = {k: r[k] for k in ("cg_steps_per_solve", "q_applies_per_solve", "ru_steps", "fp64_steps",
+                                   "cheb_degree", "max_true_relres", "all_converged")}
+        e2e_bytes = r["e2e_bytes"]
+        e2e = {"value": units / t_wall, "unit": unit, "h2d_bytes_per_step": e2e_bytes[0],
+               "d2h_bytes_per_step": e2e_bytes[1]}
+    else:
+        clocks.start()
+        r = measure_apply(wl, args.precision, args.nvec, rank, dev, stream, args.steps, args.warmup, flush)
+        clk = clocks.stop()
+        t_dev = max_over_ranks(world, r["dev_s"])
+        units = float(world * args.steps * args.nvec)
         unit = "MTM applies/s"
-        bps = 24 if args.precision == "fp64" else 12
-        ach = units / world * n * bps / t_dev / 1e9 * world
-        roof = {"bound": "hbm", "achieved": ach / world, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / world / peaks["hbm_gbs"],
-                # one ncu capture of the apply's two sweeps (profiles/mtm_sweeps_d3_nx32_nt128_fp32.md)
-                "traffic": (33557760 + 344320 + 88320 + 6871040) if (wl.name == "d3_nx32_nt128" and args.precision == "mixed") else None,
-                "kernel": "M^T M apply (%s)" % ("FP64" if args.precision == "fp64" else "FP32"),
-                "algorithmic_bytes_per_site": bps}
-        extra = {"median_apply_us": 1000.0 * float(np.median(dev_ms))}
-        e2e_bytes = (0, 0)
+        extra = {"median_apply_us": r["median_launch_us"], "vectors_per_launch": args.nvec}
+        # inputs resident on the device: no host copies in this mode
+        e2e = {"value": units / t_dev, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     line = {"metric": METRIC, "value": units / t_dev, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * t_dev / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else ("f32" if args.mode == "apply" else "f32+f64"),
             "data": "synthetic", "config": dict(config_of(args, wl), mode=args.mode,
+                                                step=("one CG solve, 2 right-hand sides" if args.mode == "solve"
+                                                      else "one M^T M apply of %d vector(s)" % args.nvec),
                                                 **({"cheb_degree": args.cheb, "cheb_eps": args.cheb_eps}
                                                    if args.cheb else {})),
-            "e2e": {"value": units / t_wall, "unit": unit, "h2d_bytes_per_step": e2e_bytes[0],
-                    "d2h_bytes_per_step": e2e_bytes[1]},
-            "gpu_launches": int(cnt["kernel_launches"]), "clocks": clk, "roofline": roof}
+            "e2e": e2e, "gpu_launches": r["gpu_launches"], "clocks": clk, "roofline": r["roofline"]}
     line.update(extra)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
 
 
 def _batch_requests(B, chains, precision, rank, keep):
@@ -424,7 +515,7 @@ def _batch_requests(B, chains, precision, rank, keep):
     return reqs
 
 
-def run_batch(args, world, rank, local, dev, stream):
+def measure_batch(precision, rank, dev, stream, steps, warmup, budget_gb, autotune_rounds=6):
     """64 independent d=3 chains of uneven volume; one step solves both
     right-hand sides of every chain in the batched engine.  The engine
     configuration comes from the library's autotuner on this request mix."""
@@ -433,11 +524,13 @@ def run_batch(args, world, rank, local, dev, stream):
     chains = workloads.batch_chains(64)
     sites = sum(c.nsites for c in chains)
     keep = []
-    reqs = _batch_requests(B, chains, args.precision, rank, keep)
-    budget = int(min(args.budget_gb, 120.0) * (1 << 30))
-    tuned = B.autotune(reqs, hbm_budget_bytes=budget, rounds=6,
+    reqs = _batch_requests(B, chains, precision, rank, keep)
+    budget = int(min(budget_gb, 120.0) * (1 << 30))
+    t0 = time.perf_counter()
+    tuned = B.autotune(reqs, hbm_budget_bytes=budget, rounds=autotune_rounds,
                        cache_path=os.path.join(ROOT, "paper_1007_3432_gb300", "lib", "autotune.jsonl"),
                        stream=stream)
+    tune_s = time.perf_counter() - t0
     batch = B.Batch(max_slots=64, hbm_budget_bytes=budget, chunk_iters=tuned["chunk_iters"],
                     tile_sites=tuned["tile_sites"], max_active_sites=tuned["max_active_sites"], stream=stream)
 
@@ -450,44 +543,83 @@ def run_batch(args, world, rank, local, dev, stream):
         torch.cuda.synchronize(dev)
         return time.perf_counter() - t0, res
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         one()
-    clocks = ClockSampler(local)
-    clocks.start()
     times, allres = [], []
-    for _ in range(args.steps):
+    for _ in range(steps):
         t, res = one()
         times.append(t)
         allres += res
-    clk = clocks.stop()
     batch.close()
-    t_tot = max_over_ranks(world, sum(times))
-    solves = sum_over_ranks(world, float(sum(r["n_solves"] for r in allres)))
+    solves = float(sum(r["n_solves"] for r in allres))
     its = sum(r["cg_iterations"] for r in allres)
     bad = sum(1 for r in allres if r["status"] != 0 or r["max_true_relres"] > 1e-10)
     peaks, src = measured_peaks()
-    per_site = bytes_per_site("cg", args.precision)
+    per_site = bytes_per_site("cg", precision)
     size_of = {j: c.nsites for j, c in enumerate(chains)}
     site_its = sum(r["cg_iterations"] * size_of[(r["ticket"] - 1) % len(chains)] for r in allres)
     ach = site_its * per_site / sum(times) / 1e9
+    if precision == "fp64":
+        flops = sum(r["cg_iterations"] * size_of[(r["ticket"] - 1) % len(chains)] for r in allres) \
+            * flops_per_site(3, "cg", "fp64")
+        fl = flops / sum(times) / 1e12
+        roof = {"bound": "alu", "achieved": fl, "peak": fp64_peak_tflops(), "unit": "TFLOP/s",
+                "frac": fl / fp64_peak_tflops(), "traffic": None, "kernel": "engine_kernel (batched, fp64)",
+                "note": "algorithmic CG flops over the whole step wall time"}
+    else:
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "engine_kernel (batched, %s)" % precision,
+                "note": "algorithmic CG bytes (11 words per site and step) over the whole step wall time"}
+    return {"workload": "batch64_d3", "precision": precision, "chains": len(chains), "sites_total": sites,
+            "solves": solves, "solves_per_s": solves / sum(times), "s_per_step": sum(times) / steps,
+            "wall_s": sum(times), "autotuned": tuned, "autotune_s": tune_s,
+            "cg_iterations_per_solve": its / max(1, solves), "failed_solves": bad, "roofline": roof,
+            "h2d_bytes_per_step": int(sum(3 * 8 * c.nsites for c in chains))}
+
+
+def run_batch(args, world, rank, local, dev, stream):
+    """--mode batch: the 64-chain batch in the precision of --precision."""
+    clocks = ClockSampler(local)
+    clocks.start()
+    r = measure_batch(args.precision, rank, dev, stream, args.steps, args.warmup, args.budget_gb)
+    clk = clocks.stop()
+    t_tot = max_over_ranks(world, r["wall_s"])
+    solves = sum_over_ranks(world, r["solves"])
     line = {"metric": METRIC, "value": solves / t_tot, "unit": "CG solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-            "config": {"workload": "batch64_d3", "chains": len(chains), "sites_total": sites,
+            "config": {"workload": "batch64_d3", "chains": r["chains"], "sites_total": r["sites_total"],
                        "nx_choices": list(workloads.BATCH_NX), "ntau_choices": list(workloads.BATCH_NTAU),
                        "seed": workloads.BATCH_SEED, "precision": args.precision, "n_rhs": 2,
-                       "autotuned": tuned, "mode": "batch", "parallelism": "replicas%d" % world},
-            "cg_iterations_per_solve": its / max(1, solves), "failed_solves": bad,
+                       "autotuned": r["autotuned"], "mode": "batch", "parallelism": "replicas%d" % world},
+            "cg_iterations_per_solve": r["cg_iterations_per_solve"], "failed_solves": r["failed_solves"],
             "e2e": {"value": solves / t_tot, "unit": "CG solves/s",
-                    "h2d_bytes_per_step": int(sum(3 * 8 * c.nsites for c in chains)), "d2h_bytes_per_step": 0},
-            "gpu_launches": None, "clocks": clk,
-            "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": ach / peaks["hbm_gbs"], "traffic": None,
-                         "kernel": "engine_kernel (batched, %s)" % args.precision,
-                         "note": "algorithmic CG bytes over the whole step wall time"}}
+                    "h2d_bytes_per_step": r["h2d_bytes_per_step"], "d2h_bytes_per_step": 0},
+            "gpu_launches": None, "clocks": clk, "roofline": r["roofline"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def default_extras(rank, dev, stream, budget_gb):
+    """The spec comparisons, measured in the same run as the headline
+    trajectory line: the C2 FP32 M^T M apply (16 vectors per launch, and one),
+    C2 solves in FP64 and in mixed precision, and the 64-chain batch in FP64
+    and mixed precision, each with its roofline."""
+    flush = L2Flush(dev)
+    c2 = workloads.C2
+    out = {}
+    out["c2_apply_fp32_16vec"] = measure_apply(c2, "mixed", 16, rank, dev, stream, 20, 3, flush)
+    out["c2_apply_fp32_1vec"] = measure_apply(c2, "mixed", 1, rank, dev, stream, 20, 3, flush)
+    sol = {p: measure_solve(c2, p, rank, dev, stream, 2, 1, flush) for p in ("fp64", "mixed")}
+    for r in sol.values():
+        r.pop("e2e_bytes", None)
+    out["c2_solves"] = dict(sol, mixed_over_fp64=sol["mixed"]["solves_per_s"] / sol["fp64"]["solves_per_s"])
+    del flush
+    bat = {p: measure_batch(p, rank, dev, stream, 1, 1, budget_gb, autotune_rounds=4) for p in ("fp64", "mixed")}
+    out["batch64_d3"] = dict(bat, mixed_over_fp64=bat["mixed"]["solves_per_s"] / bat["fp64"]["solves_per_s"])
+    return out
 
 
 def solver_for(r):
@@ -589,6 +721,9 @@ def main():
     ap.add_argument("--serve-dt", type=float, default=0.002)
     ap.add_argument("--dt", type=float, default=None, help="MD step (default: the workload's)")
     ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--nvec", type=int, default=1, help="--mode apply: vectors per launch (hh_apply_multi)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="trajectory mode: skip the C2 apply, C2 solve and batch comparisons after the timed region")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.n_md is None:
@@ -715,13 +850,17 @@ def main():
         "gpu_launches": int(cnt["kernel_launches"]),
         "clocks": clk, "roofline": roof,
     }
+    ctx.close()
+    if not args.no_extras:
+        # After the timed region: the spec comparisons on this GPU.
+        extras = default_extras(rank, dev, stream, args.budget_gb)
+        line.update(extras)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     elif rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = None
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

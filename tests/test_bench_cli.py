@@ -82,11 +82,15 @@ def test_cpu_baseline_reports_one_thread_and_all_cores():
 
 
 def test_algorithmic_bytes_per_site():
+    """11 words per CG step (r, p, L in and p, q out for the direction and
+    Q p; x, p, r, q in and x, r out for the updates), a true-residual step
+    reads x, L, b and writes r (plus x32 in and out and r32 out when mixed)."""
     import bench
-    assert bench.bytes_per_site("cg", "fp64") == 104
-    assert bench.bytes_per_site("cg", "mixed") == 52
-    assert bench.bytes_per_site("cg", "mixed-fix16link") == 48
-    assert bench.bytes_per_site("ru", "mixed-bf16link") == bench.bytes_per_site("ru", "mixed") == 76
+    assert bench.bytes_per_site("cg", "fp64") == 88
+    assert bench.bytes_per_site("cg", "mixed") == 44
+    assert bench.bytes_per_site("cg", "mixed-fix16link") == 42
+    assert bench.bytes_per_site("ru", "fp64") == 32
+    assert bench.bytes_per_site("ru", "mixed-bf16link") == bench.bytes_per_site("ru", "mixed") == 44
 
 
 def test_us_per_engine_iteration():
