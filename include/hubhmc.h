@@ -288,6 +288,15 @@ int hh_observables(hh_ctx *ctx, int n_noise, uint64_t traj, hh_obs_info *out);
 int hh_leapfrog(hh_ctx *ctx, double *pi, const double *chi, int n_rhs, int n_md, double dt,
                 hh_solve_info *info);
 
+/* Bound, in seconds, of every device-side wait of the context's kernels (the
+ * persistent CG engine's waits for other blocks' partial sums, the
+ * multi-vector apply's waits for its bulk copies); default 5.  A wait that
+ * runs out makes the kernel record HH_ETIMEOUT and leave: hh_solve and the
+ * calls built on it return HH_ETIMEOUT, an apply reports it at the next
+ * hh_counters_get.  The context stays usable: every solve starts from a reset
+ * engine state.  Errors: HH_EINVAL (seconds < 0 or > 3600). */
+int hh_set_timeout(hh_ctx *ctx, double seconds);
+
 /* Work counters of a context, for throughput and roofline accounting. */
 typedef struct {
     long long kernel_launches; /* kernels this context launched since the last reset */
@@ -304,11 +313,14 @@ typedef struct {
     long long sites;           /* N of the context's lattice */
 } hh_counters;
 
-/* Zero the counters.  profile_engine = 1 records a CUDA event pair around
- * every persistent CG launch (on the context stream) until the next reset. */
+/* Zero the counters and clear a device-side error recorded by an apply.
+ * profile_engine = 1 records a CUDA event pair around every persistent CG
+ * launch (on the context stream) until the next reset. */
 int hh_counters_reset(hh_ctx *ctx, int profile_engine);
 
-/* Read the counters; synchronises the context stream. */
+/* Read the counters; synchronises the context stream.  Returns HH_ETIMEOUT
+ * if an apply since the last reset recorded a bounded wait that ran out (the
+ * counters are filled all the same). */
 int hh_counters_get(hh_ctx *ctx, hh_counters *out);
 
 /* ---- Batched multi-chain engine and serving loop ---------------------------
@@ -393,6 +405,12 @@ int hh_batch_submit(hh_batch *b, const hh_request *req, uint64_t *ticket);
  * advance or retire requests.  *n_busy (may be NULL) receives queued + active
  * requests.  Must not be called while the worker thread runs. */
 int hh_batch_step(hh_batch *b, int *n_busy);
+
+/* Bound, in seconds, of every device-side wait of the batch engine's
+ * launches (default 5; thread safe, read at each launch).  A launch whose wait
+ * runs out fails the requests on the device with HH_ETIMEOUT; requests
+ * admitted afterwards start from empty signal slots.  Errors: HH_EINVAL. */
+int hh_batch_set_timeout(hh_batch *b, double seconds);
 
 /* Run scheduling rounds on a background thread until hh_batch_stop. */
 int hh_batch_start(hh_batch *b);

@@ -140,6 +140,8 @@ def load(path: str = LIB_PATH):
         "hh_trajectory": (i, [vp, i, d, u64, ctypes.POINTER(hh_traj_info)]),
         "hh_observables": (i, [vp, i, u64, ctypes.POINTER(hh_obs_info)]),
         "hh_leapfrog": (i, [vp, vp, vp, i, i, d, ctypes.POINTER(hh_solve_info)]),
+        "hh_set_timeout": (i, [vp, d]),
+        "hh_batch_set_timeout": (i, [vp, d]),
         "hh_counters_reset": (i, [vp, i]),
         "hh_counters_get": (i, [vp, ctypes.POINTER(hh_counters)]),
         "hh_solve_noalloc": (i, [ctypes.POINTER(hh_lattice), ctypes.POINTER(hh_params), vp, vp, vp, vp,
@@ -315,6 +317,10 @@ class Context:
         check(self._lib.hh_observables(self._h, n_noise, traj, ctypes.byref(inf)), "hh_observables")
         return inf.as_dict()
 
+    def set_timeout(self, seconds):
+        """Bound of every device-side wait (hh_set_timeout)."""
+        check(self._lib.hh_set_timeout(self._h, float(seconds)), "hh_set_timeout")
+
     def counters_reset(self, profile_engine=False):
         check(self._lib.hh_counters_reset(self._h, int(bool(profile_engine))), "hh_counters_reset")
 
@@ -412,11 +418,15 @@ class Batch:
             self._keep[t.value] = keep
         return rc, t.value
 
-    def step(self):
+    def step(self, allow=()):
         n = ctypes.c_int()
         rc = self._lib.hh_batch_step(self._h, ctypes.byref(n))
-        check(rc, "hh_batch_step")
+        check(rc, "hh_batch_step", allow)
         return n.value
+
+    def set_timeout(self, seconds):
+        """Bound of every device-side wait of the engine launches (hh_batch_set_timeout)."""
+        check(self._lib.hh_batch_set_timeout(self._h, float(seconds)), "hh_batch_set_timeout")
 
     def start(self):
         check(self._lib.hh_batch_start(self._h), "hh_batch_start")
@@ -438,10 +448,10 @@ class Batch:
         check(self._lib.hh_batch_pending(self._h, ctypes.byref(q), ctypes.byref(a)), "hh_batch_pending")
         return q.value, a.value
 
-    def run_until_idle(self, max_steps=10 ** 7):
+    def run_until_idle(self, max_steps=10 ** 7, allow=()):
         results = []
         for _ in range(max_steps):
-            busy = self.step()
+            busy = self.step(allow)
             results += self.poll()
             if busy == 0:
                 break

@@ -63,6 +63,8 @@ struct MultiCfg {
     int m;              // ranges (CTAs per slab)
     int shfl;           // x halo by warp shuffles (else from shared memory)
     int pf_ahead;       // L2 prefetch of the stage this many after the one being copied
+    int drop_tx;        // fault injection for tests: the first stage expects 16 bytes more than
+                        // it copies, so its waits run out
     long long timeout_ns;
 };
 
@@ -236,6 +238,7 @@ struct Issuer {
         constexpr int XPL = TZ + 4;
         const int P = c.P;
         const unsigned stage_bytes = (unsigned)XPL * (unsigned)P * (unsigned)sizeof(float);
+        const unsigned extra0 = (c.drop_tx && issued == 0) ? 16u : 0u;
         while (!done && issued <= upto) {
             int v, tau;
             if (it.next(v, tau) == STAGE_END) {
@@ -245,7 +248,7 @@ struct Issuer {
             const int slot = (int)(issued % NS);
             const float *xb = x + (size_t)v * c.g.N + (size_t)wrap_once(tau + 1, c.g.ntau) * c.g.V;
             float *dst = XS + (size_t)slot * XPL * P;
-            mbar_expect_tx(&full[slot], stage_bytes);
+            mbar_expect_tx(&full[slot], stage_bytes + (issued == 0 ? extra0 : 0u));
             for (int r = 0; r < xr.nr; ++r)
                 bulk_g2s(dst + (size_t)xr.off[r] * P, xb + (size_t)xr.z[r] * P,
                          (unsigned)(xr.n[r] * P * sizeof(float)), &full[slot]);
@@ -431,11 +434,13 @@ __device__ __forceinline__ void multi_consumer(const MultiCfg &c, float *XS, flo
         }
     }
     if (issuer && aborted) {
-        // Copies in flight must land before the CTA ends (bounded wait; a
-        // phase that has already completed returns at once).
+        // Copies in flight must land before the CTA ends (bounded wait, at
+        // least a second whatever the caller's budget; a phase that has
+        // already completed returns at once).
         const int never = 0;
+        const long long drain_ns = c.timeout_ns > 1000000000LL ? c.timeout_ns : 1000000000LL;
         for (long long jj = j; jj < is.issued; ++jj)
-            wait_bounded(&full[(int)(jj % NS)], (unsigned)((jj / NS) & 1), c.timeout_ns, &never);
+            wait_bounded(&full[(int)(jj % NS)], (unsigned)((jj / NS) & 1), drain_ns, &never);
     }
 }
 
@@ -534,6 +539,9 @@ cudaError_t launch_mtm_multi_f32(const Geo &g, float h, const float *L, const fl
     c.timeout_ns = timeout_ns;
     const char *pfe = getenv("HH_APPLY_MULTI_PF");
     c.pf_ahead = pfe ? atoi(pfe) : kPrefetchAhead;
+    // Fault injection for the failure-detection tests (HH_APPLY_MULTI_DROP_TX=1).
+    const char *dte = getenv("HH_APPLY_MULTI_DROP_TX");
+    c.drop_tx = dte ? atoi(dte) : 0;
     const bool n32 = g.nx == 32;
     switch (multi_form(g.nx)) {
     case 1: return n32 ? launch_multi<32, 8, 3, 2, 1>(c, nsm, L, x, y, err, st)

@@ -249,6 +249,7 @@ struct hh_batch {
     std::thread worker;
     std::atomic<bool> running{false};
     bool failed = false;
+    std::atomic<long long> timeout_ns{5LL * 1000 * 1000 * 1000};   // bound of every device-side wait
 };
 
 namespace {
@@ -682,7 +683,12 @@ int step(hh_batch *b)
     memset(&c, 0, sizeof(c));
     c.k = b->k;
     c.k_end = b->k;
-    c.timeout_ns = 5LL * 1000 * 1000 * 1000;
+    c.timeout_ns = b->timeout_ns.load();
+    {
+        // fault injection for tests (HH_ENGINE_DROP_SIGNAL, as for contexts)
+        const char *e = getenv("HH_ENGINE_DROP_SIGNAL");
+        c.drop_sig = e ? atoi(e) : 0;
+    }
     HB_TRY(cudaMemcpyAsync(b->d_ctl, &c, sizeof(c), cudaMemcpyHostToDevice, b->stream));
     rc = launch_chunk(b, grid);
     if (rc) return rc;
@@ -819,6 +825,13 @@ int hh_batch_create(hh_batch **out, const hh_batch_config *cfg, void *cuda_strea
     cudaMemcpy(b->d_state[0], done.data(), sizeof(EngState) * b->max_sys, cudaMemcpyHostToDevice);
     cudaMemcpy(b->d_state[1], done.data(), sizeof(EngState) * b->max_sys, cudaMemcpyHostToDevice);
     *out = b;
+    return HH_OK;
+}
+
+int hh_batch_set_timeout(hh_batch *b, double seconds)
+{
+    if (!b || !(seconds >= 0.0) || seconds > 3600.0) return HH_EINVAL;
+    b->timeout_ns.store((long long)(seconds * 1e9));
     return HH_OK;
 }
 

@@ -32,7 +32,7 @@ struct EngStats {
 // New solves: states MODE_NEW, empty signal slots for 'parts' tile partials,
 // iteration counter 0.
 __global__ void k_engine_reset(EngState *s0, EngState *s1, int nsys, unsigned long long *sig, int parts,
-                               EngCtl *ctl, long long timeout_ns)
+                               EngCtl *ctl, long long timeout_ns, int drop_sig)
 {
     for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
         EngState z;
@@ -48,7 +48,18 @@ __global__ void k_engine_reset(EngState *s0, EngState *s1, int nsys, unsigned lo
         ctl->k = 0;
         ctl->k_end = 0;
         ctl->timeout_ns = timeout_ns;
+        ctl->drop_sig = drop_sig;
     }
+}
+
+// Fault injection for the failure-detection tests: HH_ENGINE_DROP_SIGNAL=j + 1
+// makes the next engine launches never publish tile partial j (a signal that
+// nothing sets), so their waits run out after the wait budget.  Read at every
+// launch; unset or 0: none.
+int engine_drop_signal()
+{
+    const char *e = getenv("HH_ENGINE_DROP_SIGNAL");
+    return e ? atoi(e) : 0;
 }
 
 __device__ int severity(int st)
@@ -331,7 +342,7 @@ int run_engine(hh_ctx *c)
 {
     const Plan &P = c->plan;
     k_engine_reset<<<1, 256, 0, c->stream>>>(c->d_state[0], c->d_state[1], P.nsys, c->d_sig,
-                                             c->max_tiles, c->d_ctl, c->timeout_ns);
+                                             c->max_tiles, c->d_ctl, c->timeout_ns, engine_drop_signal());
     HH_TRY(cudaGetLastError());
     EngLaunch L;
     L.sys = c->d_sys;
@@ -724,6 +735,13 @@ int hh_apply(hh_ctx *c, int op, const void *x, void *y, int dtype)
     return HH_OK;
 }
 
+int hh_set_timeout(hh_ctx *c, double seconds)
+{
+    if (!c || !(seconds >= 0.0) || seconds > 3600.0) return HH_EINVAL;
+    c->timeout_ns = (long long)(seconds * 1e9);
+    return HH_OK;
+}
+
 int hh_apply_multi(hh_ctx *c, int op, const void *x, void *y, int n_vec, int dtype)
 {
     if (!c || !x || !y || n_vec < 1) return HH_EINVAL;
@@ -1017,6 +1035,7 @@ int hh_counters_reset(hh_ctx *c, int profile_engine)
         for (int i = 0; i < cap; ++i) HH_TRY(cudaEventCreate(&c->ev[i]));
     }
     HH_TRY(cudaMemsetAsync(c->d_totals, 0, sizeof(EngTotals), c->stream));
+    HH_TRY(cudaMemsetAsync(c->d_apply_err, 0, sizeof(int), c->stream));
     HH_TRY(cudaStreamSynchronize(c->stream));
     return HH_OK;
 }

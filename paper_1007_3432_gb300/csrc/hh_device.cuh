@@ -455,7 +455,8 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 // ---------------------------------------------------------------------------
 struct EngCtl {
     int error;              // 0, or a negative library error code (first one wins)
-    int pad0;
+    int drop_sig;           // fault injection for tests: j + 1 makes the launch never publish
+                            // tile partial j, so every wait for it runs out; 0: none
     long long k;            // engine iteration counter when the launch starts
     long long k_end;        // engine iteration counter after it (max over blocks)
     long long timeout_ns;   // bound of every wait

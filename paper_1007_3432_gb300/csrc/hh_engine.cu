@@ -914,6 +914,7 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
     EngCtl *ctl = L.ctl;
     const unsigned G = gridDim.x;
     long long k = *(volatile long long *)&ctl->k;
+    const int drop = *(volatile int *)&ctl->drop_sig;   // tile partial (+ 1) never published: tests only
 
     if (threadIdx.x == 0) {
         int n = 0, ok = 1, j = 0;
@@ -1053,7 +1054,7 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                     // after the last preconditioner sub-step, else 0; the block sum
                     // ends with a __syncthreads() after all of the tile's writes.
                     const double tot = block_sum(v, s_red);
-                    if (threadIdx.x == 0) sig_publish(sig_now + T.part, sig_next + T.part, tot);
+                    if (threadIdx.x == 0 && T.part + 1 != drop) sig_publish(sig_now + T.part, sig_next + T.part, tot);
                 }
                 if (ph == 0) {
                     // Leave once every system of this block is done: no other block
@@ -1149,7 +1150,8 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                 double tot = 0.0;
                 for (int w = 0; w < ncw; ++w) tot += s_part[b][w];
                 const PubMsg pm = s_pub[b];
-                if (!*(volatile int *)&s_failed) sig_publish(pm.now + pm.part, pm.next + pm.part, tot);
+                if (!*(volatile int *)&s_failed && pm.part + 1 != drop)
+                    sig_publish(pm.now + pm.part, pm.next + pm.part, tot);
                 __threadfence_block();
                 *(volatile int *)&s_published = t + 1;
             }
@@ -1180,7 +1182,7 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
             if (lane == 0) {
                 double tot = 0.0;
                 for (int w = 0; w < ncw; ++w) tot += s_part[pend_buf][w];
-                if (!failed) sig_publish(pend_now + pend_part, pend_next + pend_part, tot);
+                if (!failed && pend_part + 1 != drop) sig_publish(pend_now + pend_part, pend_next + pend_part, tot);
             }
             __syncwarp();
         } else if (!wait_count(&s_published, posted)) {

@@ -136,6 +136,7 @@ __global__ void k_noalloc_plan(unsigned char *base, Geo g, double h, const doubl
         ctl->k = 0;
         ctl->k_end = 0;
         ctl->timeout_ns = timeout_ns;
+        ctl->drop_sig = 0;
     }
 }
 
