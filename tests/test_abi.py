@@ -100,19 +100,26 @@ def test_public_header_compiles_as_c99_and_cxx11():
         subprocess.check_call(cmd)
 
 
-def test_plain_c_program_links_against_the_library(tmp_path):
-    """tests/native/c_consumer.c (a context, a solve, the observables and a
-    trajectory through the C ABI) compiles as C99 and links against the
-    built library; running it needs a GPU."""
+def build_c_consumer(out_dir):
+    """Compile tests/native/c_consumer.c as C99 and link it against the built
+    library and the CUDA runtime; returns (executable, library directories)."""
     import glob
+    import shutil
     from paper_1007_3432_gb300 import build
     build.build()
-    import shutil
     cuda = os.path.dirname(os.path.dirname(shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"))
-    libdir = next((d for d in glob.glob(os.path.join(cuda, "lib*")) if glob.glob(os.path.join(d, "libcudart.so*"))),
-                  os.path.join(cuda, "lib64"))
-    exe = str(tmp_path / "c_consumer")
+    libdir = next((d for d in glob.glob(os.path.join(cuda, "lib*")) + glob.glob(os.path.join(cuda, "targets", "*", "lib"))
+                   if glob.glob(os.path.join(d, "libcudart.so*"))), os.path.join(cuda, "lib64"))
+    exe = os.path.join(str(out_dir), "c_consumer")
     subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
                            "-I", os.path.join(cuda, "include"), os.path.join(ROOT, "tests", "native", "c_consumer.c"),
                            "-L", os.path.dirname(build.LIB), "-lhubhmc", "-L", libdir, "-lcudart", "-o", exe])
+    return exe, [os.path.dirname(build.LIB), libdir]
+
+
+def test_plain_c_program_links_against_the_library(tmp_path):
+    """tests/native/c_consumer.c (a context, a solve, a multi-vector apply,
+    the observables and a trajectory through the C ABI) compiles as C99 and
+    links against the built library; tests/test_gpu_c_consumer.py runs it."""
+    exe, _ = build_c_consumer(tmp_path)
     assert os.path.exists(exe)

@@ -3,7 +3,8 @@ bench.py times (the context solver with two right-hand sides):
 
 * d = 1, 1024 x 512 (524,288 sites): FP64 CG in the overlapped layout (every
   block holds a tile of both systems, control warp), mixed CG in the flat one;
-* d = 3, 32^3 x 128 (4.2M sites): mixed CG, overlapped layout.
+* d = 3, 32^3 x 128 (4.2M sites): mixed CG, overlapped layout; and every
+  element of its FP64 M, M^T and Q applies.
 
 The oracle cannot run CG at these sizes in a test's time, so it checks what
 holds at any size: the true residual b - Q x of the returned solutions with its
@@ -76,3 +77,33 @@ def test_full_size_solve_residual_and_force(hh, wl, precision):
         s = 1.0 if tau == wl.ntau - 1 else -1.0
         ref = -sum(y[a][inext] * s * A * np.cos(sigma[i]) * x[a][i] for a in range(2))
         assert abs(F[i] - ref) <= 1e-6 * scale, (i, F[i], ref)
+
+
+@pytest.mark.parametrize("op", ["M", "MT", "MTM"])
+def test_full_size_fp64_apply_per_element(hh, op):
+    """Every element of the FP64 M, M^T and Q = M^T M applies on the d = 3,
+    32^3 x 128 lattice (4.2M sites) against the oracle, to 1e-12 of the sum
+    of the magnitudes of each row's terms (the tolerance of the small-lattice
+    FP64 parity tests)."""
+    wl = workloads.C2
+    lat = oracle.lattice(wl.d, wl.nx, wl.ntau)
+    n = wl.nsites
+    sigma = workloads.sigma_field(n, seed=wl.seed)
+    x = workloads.source(n, seed=wl.seed + 5)
+    L = oracle.links(lat, A, sigma)
+    f = {"M": oracle.apply_M, "MT": oracle.apply_MT, "MTM": oracle.apply_MTM}[op]
+    ref = f(lat, H, L, x)
+    La, xa = np.abs(L), np.abs(x)
+    if op == "M":
+        mag = oracle.apply_M(lat, -H, La, xa)
+    elif op == "MT":
+        mag = oracle.apply_MT(lat, -H, La, xa)
+    else:
+        mag = oracle.apply_MT(lat, -H, La, oracle.apply_M(lat, -H, La, xa))
+    code = {"M": hh.HH_OP_M, "MT": hh.HH_OP_MT, "MTM": hh.HH_OP_MTM}[op]
+    with hh.Context(wl.d, wl.nx, wl.ntau) as ctx:
+        ctx.set_field(dev(sigma))
+        y = torch.empty(n, dtype=torch.float64, device="cuda")
+        ctx.apply(code, dev(x), y)
+        got = y.cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 1e-12 * mag), np.max(np.abs(got - ref) / mag)
