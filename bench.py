@@ -89,10 +89,9 @@ def bytes_per_site(kind, precision):
 # DRAM bytes per engine iteration (two right-hand sides) of the engine kernel
 # as it stands, from one ncu --set full capture each (dram__bytes_read.sum +
 # dram__bytes_write.sum over a 202-iteration launch; profiles/engine_kernel_*).
-# A launch's traffic scales with its iterations.  Empty: the kernel has changed
-# since the last captures (its per-system descriptor gained the 16-bit link
-# fields), so the bench lines report no traffic until the next capture.
-ENGINE_DRAM_PER_ITER = {}
+# A launch's traffic scales with its iterations.
+ENGINE_DRAM_PER_ITER = {("d1_nx1024_nt512", "fp64"): (12760832 + 71143936) / 202.0,
+                        ("d3_nx32_nt128", "mixed"): (35681830000 + 27052524000) / 202.0}
 
 # DRAM bytes (read + write) per launch of the Q apply from one ncu capture each
 # (profiles/mtm_*): (workload, dtype, vectors per launch) -> bytes.
@@ -332,6 +331,7 @@ def measure_solve(wl, precision, rank, dev, stream, steps, warmup, flush, cg_max
     per-step device and wall times."""
     import torch
     from paper_1007_3432_gb300 import Context
+    from paper_1007_3432_gb300.binding import HH_ENOCONV
     n = wl.nsites
     ctx = Context(wl.d, wl.nx, wl.ntau, seed=wl.seed, chain_id=rank, precision=precision,
                   cg_maxit=cg_maxit, stream=stream, cheb_degree=cheb, cheb_eps=cheb_eps)
@@ -350,7 +350,9 @@ def measure_solve(wl, precision, rank, dev, stream, steps, warmup, flush, cg_max
         w0 = time.perf_counter()
         b.copy_(b_pin, non_blocking=True)      # host -> device input
         e0.record(stream)
-        rc, inf = ctx.solve(b, x, 2, info=True)
+        # an iteration cap below convergence (--cg-maxit, as the profiling
+        # commands use) returns HH_ENOCONV with the last iterate
+        rc, inf = ctx.solve(b, x, 2, info=True, allow=(HH_ENOCONV,))
         e1.record(stream)
         x_h.copy_(x, non_blocking=True)        # device -> host result
         torch.cuda.synchronize(dev)
@@ -622,78 +624,144 @@ def default_extras(rank, dev, stream, budget_gb):
     return out
 
 
-def solver_for(r):
-    """Solver of a served request.  d = 1 lattices with N_tau >= 256 (beta >= 12.8)
-    use FP64 CG with the Chebyshev preconditioner of Sec. 4.2 (n = 8, eps =
-    1e-4): on some of them plain CG, FP64 or mixed, stalls near a relative
-    residual of 1e-7 (1255 x 504, seed 101103049: 400k FP64 CG steps reach
-    1.4e-7; the preconditioned solve converges in 4.2k steps).  The others use
+def solver_for(r, arm="mixed"):
+    """Solver of a served request.  Arm "mixed": d = 1 lattices with N_tau >=
+    256 (beta >= 12.8) use FP64 CG with the Chebyshev preconditioner of Sec.
+    4.2 (n = 8, eps = 1e-4): on some of them plain CG, FP64 or mixed, stalls
+    near a relative residual of 1e-7 (1255 x 504, seed 101103049: 400k FP64 CG
+    steps reach 1.4e-7; the preconditioned solve converges in 4.2k steps); the
+    others use mixed precision.  Arm "fp64": the same with FP64 CG in place of
     mixed precision."""
     if r.d == 1 and r.ntau >= 256:
         return {"precision": "fp64", "cheb_degree": 8, "cheb_eps": 1e-4}
-    return {"precision": "mixed"}
+    return {"precision": "mixed" if arm == "mixed" else "fp64"}
 
 
-def run_serve(args, world, rank, local, dev, stream):
-    """Poisson arrivals of solve and trajectory requests, served by the
-    continuous-batching worker thread; p50/p99 latency and solves/s per rate."""
+def _percentiles(vals):
+    if not vals:
+        return {"p50": None, "p99": None, "max": None}
+    a = np.array(vals)
+    return {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99)), "max": float(a.max())}
+
+
+def serve_one(args, rate, arm, rank, dev, stream, n_req, cap_s, n_check):
+    """One Poisson stream of n_req requests at `rate` served by the continuous-
+    batching worker, for at most cap_s seconds of wall time (arrivals and
+    service); latencies of the completed requests split into queueing (submit
+    -> admitted into a slot) and service (admitted -> result).  The first
+    n_check solve requests keep their solutions, and are then solved alone in
+    a fresh batch: the results must be bitwise the same."""
     import torch
     from paper_1007_3432_gb300 import binding as B
     from paper_1007_3432_gb300.binding import HH_REQ_SOLVE, HH_REQ_TRAJECTORY
     budget = int(args.budget_gb * (1 << 30))
-    per_rate = []
-    for rate in [float(x) for x in args.rates.split(",")]:
-        reqs = workloads.poisson_requests(rate, args.requests, seed=workloads.SERVE_SEED + 17 * rank)
-        batch = B.Batch(max_slots=64, hbm_budget_bytes=budget, chunk_iters=32, tile_sites=4096, stream=stream)
-        batch.start()
-        keep, got = [], []
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for r in reqs:
-            while time.perf_counter() - t0 < r.arrival_s:
-                time.sleep(0.0002)
-            sigma = workloads.sigma_field(r.nsites, seed=r.seed)
-            prm = solver_for(r)
-            if r.kind == "solve":
-                req = B.make_request(HH_REQ_SOLVE, r.d, r.nx, r.ntau, sigma=sigma, seed=r.seed, n_pf=2,
-                                     traj_index=r.rid, **prm)
-            else:
-                req = B.make_request(HH_REQ_TRAJECTORY, r.d, r.nx, r.ntau, sigma=sigma, seed=r.seed, n_pf=2,
-                                     n_md=args.serve_n_md, dt=args.serve_dt, traj_index=r.rid, **prm)
-            keep.append(sigma)
-            batch.submit(req)
-            got += batch.poll()
-        deadline = time.perf_counter() + 600
-        while len(got) < len(reqs) and time.perf_counter() < deadline:
-            got += batch.poll()
-            time.sleep(0.001)
-        wall = time.perf_counter() - t0
-        batch.stop()
-        batch.close()
-        lat = np.array([g["latency_ms"] for g in got]) if got else np.array([np.nan])
-        per_rate.append({"rate_hz": rate, "requests": len(reqs), "completed": len(got),
-                         "failed": sum(1 for g in got if g["status"] != 0),
-                         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                         "solves_per_s": sum(g["n_solves"] for g in got) / wall,
-                         "requests_per_s": len(got) / wall, "wall_s": wall,
-                         "mean_queue_ms": float(np.mean([g["queue_ms"] for g in got])) if got else None,
-                         "status_counts": {str(k): int(v) for k, v in zip(*np.unique([g["status"] for g in got],
-                                                                                  return_counts=True))} if got else {},
-                         "requests_detail": [[reqs[g["ticket"] - 1].kind[0], reqs[g["ticket"] - 1].d,
-                                              reqs[g["ticket"] - 1].nx, reqs[g["ticket"] - 1].ntau, g["status"],
-                                              round(g["latency_ms"], 1), g["cg_iterations"]] for g in got]})
-    best = max(per_rate, key=lambda d: d["solves_per_s"])
+    reqs = workloads.poisson_requests(rate, n_req, seed=workloads.SERVE_SEED + 17 * rank)
+
+    def make(r, out=None):
+        sigma = workloads.sigma_field(r.nsites, seed=r.seed)
+        prm = solver_for(r, arm)
+        if r.kind == "solve":
+            return B.make_request(HH_REQ_SOLVE, r.d, r.nx, r.ntau, sigma=sigma, seed=r.seed, n_pf=2,
+                                  traj_index=r.rid, out=out, **prm), sigma
+        return B.make_request(HH_REQ_TRAJECTORY, r.d, r.nx, r.ntau, sigma=sigma, seed=r.seed, n_pf=2,
+                              n_md=args.serve_n_md, dt=args.serve_dt, traj_index=r.rid, **prm), sigma
+
+    checks = {}
+    batch = B.Batch(max_slots=64, hbm_budget_bytes=budget, chunk_iters=32, tile_sites=4096, stream=stream)
+    batch.start()
+    keep, got, tickets = [], [], {}
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    submitted = 0
+    for r in reqs:
+        while time.perf_counter() - t0 < r.arrival_s:
+            time.sleep(0.0002)
+        if time.perf_counter() - t0 > cap_s:
+            break
+        out = None
+        if r.kind == "solve" and len(checks) < n_check:
+            out = np.zeros((2, r.nsites))
+        req, sigma = make(r, out)
+        keep.append((sigma, out))
+        _, t = batch.submit(req)
+        tickets[t] = r
+        if out is not None:
+            checks[t] = (r, out)
+        submitted += 1
+        got += batch.poll()
+    while len(got) < submitted and time.perf_counter() - t0 < cap_s:
+        got += batch.poll()
+        time.sleep(0.001)
+    wall = time.perf_counter() - t0
+    batch.stop()
+    got += batch.poll()
+    batch.close()
+    done = [g for g in got]
+    ok = [g for g in done if g["status"] == 0]
+    lat = [g["latency_ms"] for g in ok]
+    que = [g["queue_ms"] for g in ok]
+    svc = [g["latency_ms"] - g["queue_ms"] for g in ok]
+    # alone-vs-mix: the sampled solves, each alone in a fresh batch
+    same, compared = True, 0
+    done_tickets = {g["ticket"] for g in ok}
+    for t, (r, out) in checks.items():
+        if t not in done_tickets:
+            continue
+        ref = np.zeros_like(out)
+        with B.Batch(max_slots=4, hbm_budget_bytes=budget, chunk_iters=32, tile_sites=4096, stream=stream) as solo:
+            req, sigma = make(r, ref)
+            solo.submit(req, keep=(sigma, ref))
+            solo.run_until_idle()
+        same = same and bool(np.array_equal(out, ref))
+        compared += 1
+    return {"rate_hz": rate, "arm": arm, "requests_offered": n_req, "submitted": submitted,
+            "completed": len(done), "failed": sum(1 for g in done if g["status"] != 0),
+            "unfinished_at_cap": submitted - len(done), "wall_s": wall, "cap_s": cap_s,
+            "solves_per_s": sum(g["n_solves"] for g in ok) / wall, "requests_per_s": len(ok) / wall,
+            "latency_ms": _percentiles(lat), "queue_ms": _percentiles(que), "service_ms": _percentiles(svc),
+            "alone_vs_mix": {"compared": compared, "bitwise_equal": same if compared else None},
+            "status_counts": {str(k): int(v) for k, v in zip(*np.unique([g["status"] for g in done],
+                                                                       return_counts=True))} if done else {}}
+
+
+def run_serve(args, world, rank, local, dev, stream):
+    """Poisson arrivals of solve and trajectory requests, served by the
+    continuous-batching worker; per rate and arm: solves/s, end-to-end,
+    queueing and service latency percentiles, completion within the cap, and
+    the alone-vs-mix check."""
+    per = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    for arm in args.serve_arms.split(","):
+        rates = [float(x) for x in (args.rates if arm == "mixed" else args.fp64_rates).split(",")]
+        for rate in rates:
+            below = rate < 1.0
+            n_req = args.requests_low if below else args.requests
+            # below capacity: long enough for every arrival plus a minute of service
+            cap = n_req / rate + 60.0 if below else args.serve_cap_s
+            r = serve_one(args, rate, arm, rank, dev, stream, n_req, cap, args.serve_checks)
+            per.append(r)
+            if rank == 0:
+                print("# serve %s %.2f/s: %d/%d done, %.2f solves/s, p50 %.0f ms, p99 %.0f ms"
+                      % (arm, rate, r["completed"], r["submitted"], r["solves_per_s"],
+                         r["latency_ms"]["p50"] or -1, r["latency_ms"]["p99"] or -1), file=sys.stderr, flush=True)
+    clk = clocks.stop()
+    mixed = [r for r in per if r["arm"] == "mixed"]
+    best = max(mixed or per, key=lambda d: d["solves_per_s"])
     line = {"metric": METRIC, "value": best["solves_per_s"], "unit": "CG solves/s", "n_gpus": world,
-            "steps": len(per_rate), "warmup": 0, "ms_per_step": 1000.0 * sum(d["wall_s"] for d in per_rate) / len(per_rate),
+            "steps": len(per), "warmup": 0, "ms_per_step": 1000.0 * sum(d["wall_s"] for d in per) / len(per),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": "serve_poisson", "seed": workloads.SERVE_SEED, "requests_per_rate": args.requests,
+            "config": {"workload": "serve_poisson", "seed": workloads.SERVE_SEED,
+                       "requests_per_rate": args.requests, "requests_below_capacity": args.requests_low,
+                       "cap_s_per_rate": args.serve_cap_s,
                        "d1": {"nx": [64, 2048], "ntau": [64, 512]}, "d3": {"nx": [8, 24], "ntau": [40, 256]},
                        "trajectory_n_md": args.serve_n_md, "trajectory_dt": args.serve_dt,
                        "hbm_budget_gb": args.budget_gb,
-                       "precision": "mixed; FP64 + Chebyshev n=8 eps=1e-4 for d=1 with N_tau >= 256",
+                       "arms": {"mixed": "mixed; FP64 + Chebyshev n=8 eps=1e-4 for d=1 with N_tau >= 256",
+                                "fp64": "FP64; FP64 + Chebyshev n=8 eps=1e-4 for d=1 with N_tau >= 256"},
                        "mode": "serve", "parallelism": "replicas%d" % world},
-            "per_rate": per_rate, "e2e": None, "gpu_launches": None}
+            "per_rate": per, "clocks": clk, "e2e": None, "gpu_launches": None}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -715,8 +783,14 @@ def main():
     ap.add_argument("--cheb", type=int, default=0, help="Chebyshev preconditioner degree n (FP64; solve and trajectory)")
     ap.add_argument("--integrator", default="leapfrog", choices=["leapfrog", "omelyan"])
     ap.add_argument("--cheb-eps", type=float, default=1e-4)
-    ap.add_argument("--rates", default="10,100,1000")
-    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--rates", default="0.25,10,30,100,300,1000",
+                    help="serve: arrival rates (req/s) of the mixed arm; rates below 1 are below capacity")
+    ap.add_argument("--fp64-rates", default="10,1000", help="serve: arrival rates of the FP64 arm")
+    ap.add_argument("--serve-arms", default="mixed,fp64")
+    ap.add_argument("--requests", type=int, default=200, help="serve: requests per rate")
+    ap.add_argument("--requests-low", type=int, default=30, help="serve: requests at rates below 1/s")
+    ap.add_argument("--serve-cap-s", type=float, default=100.0, help="serve: wall-time cap per rate")
+    ap.add_argument("--serve-checks", type=int, default=2, help="serve: alone-vs-mix checks per rate")
     ap.add_argument("--serve-n-md", type=int, default=4)
     ap.add_argument("--serve-dt", type=float, default=0.002)
     ap.add_argument("--dt", type=float, default=None, help="MD step (default: the workload's)")
