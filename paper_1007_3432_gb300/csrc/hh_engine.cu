@@ -905,6 +905,11 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
     __shared__ int s_sys[kCacheSys];
     __shared__ unsigned char s_slot[kCacheTiles];
     __shared__ int s_ok;
+    // Uncached blocks: the mode each system was given by this block's own
+    // slot-1 decision of the current iteration (its full state is read back
+    // from global memory only after the next wait, once the owner block's copy
+    // is certainly written).
+    __shared__ unsigned char s_umode[ENGINE_MAX_SYSTEMS];
     // Read-only descriptors of this block's tiles and systems, copied once:
     // re-reading them from global memory after each wait would cost two
     // dependent L2 round trips per slot.
@@ -1011,23 +1016,25 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                                         if (S.mode != MODE_DONE) live = 1;
                                         s_cache[slot] = S;
                                         s_tctl[slot] = make_ctl(S, two, Y.x0_given);
+                                        if (!cached) s_umode[T.sys] = (unsigned char)S.mode;
                                     }
                                 }
                             }
                         } else {
-                            if (!cached && threadIdx.x == 0) {
-                                const EngState S = nxt[T.sys];
-                                s_cache[0] = S;
-                                s_tctl[0] = make_ctl(S, two, Y.x0_given);
-                            }
-                            __syncthreads();
+                            // An uncached block re-reads the system's state from the
+                            // owner block's copy, after the wait that orders it.
                             if (threadIdx.x < 32) {
                                 bool ok = true;
                                 double tt = 0.0;
-                                if (s_tctl[slot].mode != MODE_DONE)
-                                    ok = poll_sum(sig_wait + Y.part0, Y.ntiles, ctl, tt);
+                                const int m = cached ? s_tctl[slot].mode : (int)s_umode[T.sys];
+                                if (m != MODE_DONE) ok = poll_sum(sig_wait + Y.part0, Y.ntiles, ctl, tt);
                                 if (threadIdx.x == 0) {
                                     s_flag = ok ? 1 : 0;
+                                    if (ok && !cached) {
+                                        const EngState S = nxt[T.sys];
+                                        s_cache[0] = S;
+                                        s_tctl[0] = make_ctl(S, two, Y.x0_given);
+                                    }
                                     if (ok && sl == 3 && s_tctl[slot].mode == MODE_CG)
                                         s_tctl[slot].alpha = s_cache[slot].rr_alpha / tt;
                                 }
@@ -1243,9 +1250,16 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                             if (S.mode != MODE_DONE) live = 1;
                             s_cache[slot] = S;
                             s_tctl[slot] = make_ctl(S, two, Y.x0_given);
+                            if (!cached) s_umode[T.sys] = (unsigned char)S.mode;
                         }
                     } else {
-                        if (!cached) {
+                        // An uncached block re-reads the system's state from the
+                        // owner block's copy, after the wait that orders it.
+                        __syncwarp();
+                        const int m = cached ? s_tctl[slot].mode : (int)s_umode[T.sys];
+                        double tt = 0.0;
+                        if (m != MODE_DONE) ok = poll_sum(sig_wait + Y.part0, Y.ntiles, ctl, tt);
+                        if (ok && !cached) {
                             if (lane == 0) {
                                 const EngState S = nxt[T.sys];
                                 s_cache[0] = S;
@@ -1253,9 +1267,6 @@ __global__ void __launch_bounds__(ENGINE_BLOCK, MINB) engine_kernel(EngLaunch L)
                             }
                             __syncwarp();
                         }
-                        const int m = s_tctl[slot].mode;
-                        double tt = 0.0;
-                        if (m != MODE_DONE) ok = poll_sum(sig_wait + Y.part0, Y.ntiles, ctl, tt);
                         if (ok && lane == 0 && sl == 3 && m == MODE_CG)
                             s_tctl[slot].alpha = s_cache[slot].rr_alpha / tt;
                     }
@@ -1351,6 +1362,7 @@ const void *kernel_of(int kind)
 
 cudaError_t engine_launch(const EngLaunch &L, int grid, int block, cudaStream_t stream, int kind)
 {
+    if (L.nsys > ENGINE_MAX_SYSTEMS) return cudaErrorInvalidValue;
     EngLaunch arg = L;
     void *args[] = {(void *)&arg};
     return cudaLaunchCooperativeKernel(kernel_of(kind), dim3(grid), dim3(block), args, 0, stream);

@@ -185,6 +185,8 @@ const void *engine_kernel_fn(int kind);
 int engine_max_grid(int block, int kind);
 
 constexpr int ENGINE_BLOCK = 512;
+// Systems of one launch, at most (the per-block record of decided modes).
+constexpr int ENGINE_MAX_SYSTEMS = 1024;
 constexpr int ENGINE_MIN_TILE = 512;   // sites per tile, at least one per thread
 
 // Default grid: one block per SM (fewer blocks per wait), capped

@@ -115,6 +115,43 @@ def test_result_is_identical_alone_and_in_the_mix(hh):
     assert dha == dhb and acca == accb
 
 
+def test_many_systems_per_block_uncached_path(hh):
+    """80 two-source requests of 40 tiles each: 6400 tiles over one block per
+    SM, so every block holds tiles of more distinct systems than its
+    shared-memory cache (32) and runs the uncached path, which re-reads each
+    system's state from global memory after the wait that orders it.  Every
+    request converges to the FP64 true residual, and two of them agree bit
+    for bit with the same request run alone (where the block caches)."""
+    from paper_1007_3432_gb300 import binding as B
+    d, nx, nt = 3, 8, 40                       # 20480 sites = 40 tiles of 512
+    specs = [(1000 + j, "mixed" if j % 2 else "fp64") for j in range(80)]
+    alone = {}
+    for j in (0, 1):
+        with B.Batch(max_slots=2, hbm_budget_bytes=1 << 30, chunk_iters=32, tile_sites=512) as batch:
+            req, k = _solve_req(B, d, nx, nt, *specs[j])
+            batch.submit(req, keep=k)
+            res = batch.run_until_idle()
+            assert res[0]["status"] == 0, res
+            alone[j] = k[2].copy()
+    keeps = []
+    with B.Batch(max_slots=80, hbm_budget_bytes=4 << 30, chunk_iters=32, tile_sites=512) as batch:
+        for seed, prec in specs:
+            req, k = _solve_req(B, d, nx, nt, seed, prec)
+            batch.submit(req, keep=k)
+            keeps.append(k)
+        res = {r["ticket"]: r for r in batch.run_until_idle()}
+    assert len(res) == len(specs)
+    for t in range(1, len(specs) + 1):
+        assert res[t]["status"] == 0 and res[t]["max_true_relres"] <= 1e-10, res[t]
+    for j in (0, 1):
+        assert np.array_equal(keeps[j][2], alone[j])
+    sigma, b, out = keeps[5]
+    lat = oracle.lattice(d, nx, nt)
+    L = oracle.links(lat, workloads.A_HS, sigma)
+    for a in range(2):
+        assert np.linalg.norm(b[a] - oracle.apply_MTM(lat, H, L, out[a])) <= 1.0001e-10 * np.linalg.norm(b[a])
+
+
 def test_batched_trajectories_match_context(hh):
     from paper_1007_3432_gb300 import binding as B
     cases = [(1, 16, 16, 81, 4, 0.1, 0), (3, 4, 6, 82, 3, 0.1, 1), (1, 32, 64, 83, 5, 0.04, 2)]
