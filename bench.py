@@ -720,6 +720,9 @@ def serve_one(args, rate, arm, rank, dev, stream, n_req, cap_s, n_check):
             "solves_per_s": sum(g["n_solves"] for g in ok) / wall, "requests_per_s": len(ok) / wall,
             "latency_ms": _percentiles(lat), "queue_ms": _percentiles(que), "service_ms": _percentiles(svc),
             "alone_vs_mix": {"compared": compared, "bitwise_equal": same if compared else None},
+            "failed_detail": [[tickets[g["ticket"]].rid, tickets[g["ticket"]].kind, tickets[g["ticket"]].d,
+                               tickets[g["ticket"]].nx, tickets[g["ticket"]].ntau, g["status"], g["cg_iterations"],
+                               g["dH"]] for g in done if g["status"] != 0],
             "status_counts": {str(k): int(v) for k, v in zip(*np.unique([g["status"] for g in done],
                                                                        return_counts=True))} if done else {}}
 

@@ -430,6 +430,62 @@ int hh_batch_pending(hh_batch *b, int *queued, int *active);
 int hh_batch_autotune(const hh_request *sample, int n, size_t hbm_budget_bytes, int rounds,
                       const char *cache_path, void *cuda_stream, hh_batch_config *best);
 
+/* ---- Time-slab decomposition over several ranks ---------------------------
+ * One lattice split by time slices over R ranks (processes, typically one GPU
+ * each): rank r owns slices [tau0, tau1) of every vector.  M couples slice tau
+ * to tau - 1 and M^T couples it to tau + 1 (Eq. (10)), so an apply of M needs
+ * the previous rank's last slice of x, an apply of M^T the next rank's first
+ * slice of t = M x, and CG (Sec. 4.1) two global sums per iteration.  The
+ * sign of the antiperiodic wrap link N_tau - 1 -> 0 follows the global slice
+ * index, so it stays with the rank owning slice N_tau - 1.  Ranks form a ring:
+ * the rank owning slice 0 has the rank owning N_tau - 1 as its previous one.
+ *
+ * The library is communication-agnostic and stages every halo through host
+ * memory between kernel launches (no kernel waits for another rank): the
+ * caller supplies the two callbacks of hh_comm, called from the calling
+ * thread after the slab's stream has been synchronised; they must complete
+ * before returning and return 0 on success (any other value: HH_ECUDA).
+ *   exchange(user, dir, send, recv, bytes): dir = +1: send the host buffer
+ *     send (bytes) to the next rank and receive the previous rank's into recv;
+ *     dir = -1: send to the previous rank and receive from the next.  With
+ *     one rank, copy send into recv.
+ *   allreduce_sum(user, vals, n): replace the n host doubles by their sums
+ *     over all ranks. */
+typedef struct hh_slab hh_slab;
+
+typedef struct {
+    int (*exchange)(void *user, int dir, const void *send, void *recv, size_t bytes);
+    int (*allreduce_sum)(void *user, double *vals, int n);
+    void *user;
+} hh_comm;
+
+/* Slab of slices [tau0, tau1) of the lattice lat (FP64 only, link_order 0,
+ * no preconditioner).  Allocates the slab's field, links and work vectors on
+ * the current device; stream: cudaStream_t (NULL: legacy default stream).
+ * Errors: HH_EINVAL (shapes, empty slab, missing callbacks, other precision),
+ * HH_ENOMEM, HH_ECUDA. */
+int hh_slab_create(hh_slab **out, const hh_lattice *lat, const hh_params *p, int tau0, int tau1,
+                   const hh_comm *comm, void *cuda_stream);
+int hh_slab_destroy(hh_slab *s);
+
+/* The slab's part of sigma: (tau1 - tau0) * V doubles (slice tau0 first),
+ * device (on_device = 1) or host memory; exchanges the slice before tau0 with
+ * the previous rank (collective: every rank calls it) and computes the links.
+ * Synchronises. */
+int hh_slab_set_field(hh_slab *s, const double *sigma, int on_device);
+
+/* y = op(x) on the slab's slices, op in {HH_OP_M, HH_OP_MT, HH_OP_MTM}; x and
+ * y: device pointers to (tau1 - tau0) * V doubles.  Collective.  Synchronises. */
+int hh_slab_apply(hh_slab *s, int op, const double *x, double *y);
+
+/* Q x = b by FP64 CG over all ranks, x0 = 0, stopping on the global true
+ * residual ||b - Q x|| <= cg_tol ||b|| as hh_solve; b, x: device pointers to
+ * the slab's part.  Collective.  info (may be NULL): iterations, true-residual
+ * checks (reliable_updates), final true relative residual, converged flag.
+ * Returns HH_ENOCONV at the iteration cap, HH_ENUMERIC on a non-finite or
+ * non-positive <p, Q p>. */
+int hh_slab_solve(hh_slab *s, const double *b, double *x, hh_solve_info *info);
+
 /* ---- Allocation-free solve ------------------------------------------------
  * The paper has no counterpart of this entry point; it exists for callers
  * that cannot allocate memory when they need a solve: code running while its

@@ -106,6 +106,15 @@ class hh_batch_config(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_size_t)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int)
+
+
+class hh_comm(ctypes.Structure):
+    _fields_ = [("exchange", EXCHANGE_FN), ("allreduce_sum", ALLREDUCE_FN), ("user", ctypes.c_void_p)]
+
+
 HH_REQ_SOLVE, HH_REQ_TRAJECTORY = 0, 1
 HH_LEAPFROG, HH_OMELYAN = 0, 1
 INTEGRATORS = {"leapfrog": HH_LEAPFROG, "omelyan": HH_OMELYAN}
@@ -146,6 +155,12 @@ def load(path: str = LIB_PATH):
         "hh_counters_get": (i, [vp, ctypes.POINTER(hh_counters)]),
         "hh_solve_noalloc": (i, [ctypes.POINTER(hh_lattice), ctypes.POINTER(hh_params), vp, vp, vp, vp,
                                  ctypes.POINTER(hh_solve_info)]),
+        "hh_slab_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(hh_lattice), ctypes.POINTER(hh_params), i, i,
+                               ctypes.POINTER(hh_comm), vp]),
+        "hh_slab_destroy": (i, [vp]),
+        "hh_slab_set_field": (i, [vp, vp, i]),
+        "hh_slab_apply": (i, [vp, i, vp, vp]),
+        "hh_slab_solve": (i, [vp, vp, vp, ctypes.POINTER(hh_solve_info)]),
         "hh_batch_default_config": (None, [ctypes.POINTER(hh_batch_config)]),
         "hh_batch_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(hh_batch_config), vp]),
         "hh_batch_destroy": (i, [vp]),
@@ -468,3 +483,123 @@ def autotune(requests, hbm_budget_bytes=4 << 30, rounds=8, cache_path=None, stre
                               cache_path.encode() if cache_path else None, _stream_handle(stream),
                               ctypes.byref(best)), "hh_batch_autotune")
     return best.as_dict()
+
+
+class TorchDistComm:
+    """The two host-side callbacks of a time slab (hh_comm) over
+    torch.distributed with CPU tensors (gloo): exchange of one time slice with
+    the neighbouring ranks of the ring, and the sum of a few doubles over all
+    ranks.  With one rank the exchange copies send into recv."""
+
+    def __init__(self, group=None):
+        import torch.distributed as dist
+        self.dist = dist
+        self.group = group
+        self.rank = dist.get_rank(group) if dist.is_initialized() else 0
+        self.world = dist.get_world_size(group) if dist.is_initialized() else 1
+        self.error = None
+
+    def exchange_host(self, direction, send, recv):
+        """send, recv: 1-D CPU tensors of the same size."""
+        if self.world == 1:
+            recv.copy_(send)
+            return
+        nxt, prv = (self.rank + 1) % self.world, (self.rank - 1) % self.world
+        to, frm = (nxt, prv) if direction > 0 else (prv, nxt)
+        req = self.dist.isend(send, to, group=self.group)
+        self.dist.recv(recv, frm, group=self.group)
+        req.wait()
+
+    def allreduce_host(self, vals):
+        if self.world > 1:
+            self.dist.all_reduce(vals, op=self.dist.ReduceOp.SUM, group=self.group)
+
+    def c_callbacks(self):
+        """An hh_comm whose callbacks call the methods above (keep the returned
+        object alive while the slab exists)."""
+        import torch
+
+        def _exchange(user, direction, send, recv, nbytes):
+            try:
+                n = int(nbytes) // 8
+                s = torch.frombuffer((ctypes.c_double * n).from_address(send), dtype=torch.float64)
+                r = torch.frombuffer((ctypes.c_double * n).from_address(recv), dtype=torch.float64)
+                self.exchange_host(int(direction), s.clone(), r)
+                return 0
+            except Exception as e:   # no exception may cross the C ABI
+                self.error = e
+                return 1
+
+        def _allreduce(user, vals, n):
+            try:
+                v = torch.frombuffer((ctypes.c_double * int(n)).from_address(ctypes.addressof(vals.contents)),
+                                     dtype=torch.float64)
+                t = v.clone()
+                self.allreduce_host(t)
+                v.copy_(t)
+                return 0
+            except Exception as e:
+                self.error = e
+                return 1
+
+        self._ex = EXCHANGE_FN(_exchange)
+        self._ar = ALLREDUCE_FN(_allreduce)
+        return hh_comm(self._ex, self._ar, None)
+
+
+class Slab:
+    """The slices [tau0, tau1) of one lattice on this rank (hh_slab_*)."""
+
+    def __init__(self, d, nx, ntau, tau0, tau1, comm=None, stream=None, **prm):
+        L = load()
+        self._lib = L
+        self.comm = comm if comm is not None else TorchDistComm()
+        self._c = self.comm.c_callbacks()
+        self.lat = hh_lattice(d, nx, ntau)
+        p = make_params(**prm)
+        h = ctypes.c_void_p()
+        check(L.hh_slab_create(ctypes.byref(h), ctypes.byref(self.lat), ctypes.byref(p), tau0, tau1,
+                               ctypes.byref(self._c), _stream_handle(stream)), "hh_slab_create")
+        self._h = h
+        self.V = nx ** d
+        self.n = self.V * (tau1 - tau0)
+
+    def _check(self, rc, what):
+        if rc != HH_OK and self.comm.error is not None:
+            err, self.comm.error = self.comm.error, None
+            raise HHError(rc, what + " (callback: %r)" % (err,))
+        check(rc, what)
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hh_slab_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_field(self, sigma_slab):
+        on_device = getattr(sigma_slab, "is_cuda", False)
+        ptr = _ptr(sigma_slab) if not hasattr(sigma_slab, "ctypes") else sigma_slab.ctypes.data
+        self._check(self._lib.hh_slab_set_field(self._h, ptr, int(bool(on_device))), "hh_slab_set_field")
+
+    def apply(self, op, x, y):
+        self._check(self._lib.hh_slab_apply(self._h, op, _ptr(x), _ptr(y)), "hh_slab_apply")
+
+    def solve(self, b, x, allow=()):
+        inf = hh_solve_info()
+        rc = self._lib.hh_slab_solve(self._h, _ptr(b), _ptr(x), ctypes.byref(inf))
+        if rc not in allow:
+            self._check(rc, "hh_slab_solve")
+        return rc, inf.as_dict()
+
