@@ -96,7 +96,7 @@ ENGINE_DRAM_PER_ITER = {("d1_nx1024_nt512", "fp64"): (12760832 + 71143936) / 202
 # DRAM bytes (read + write) per launch of the Q apply from one ncu capture each
 # (profiles/mtm_*): (workload, dtype, vectors per launch) -> bytes.
 APPLY_DRAM_PER_LAUNCH = {("d3_nx32_nt128", "fp32", 1): 33557760 + 344320 + 88320 + 6871040,
-                         ("d3_nx32_nt128", "fp32", 16): 301937664 + 229500160}
+                         ("d3_nx32_nt128", "fp32", 16): 300300288 + 229754880}
 
 
 def engine_traffic(wl, precision, cheb, cnt):
@@ -448,7 +448,8 @@ def measure_apply(wl, precision, nvec, rank, dev, stream, steps, warmup, flush):
     traffic = APPLY_DRAM_PER_LAUNCH.get((wl.name, "fp64" if precision == "fp64" else "fp32", nvec))
     roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": ach / peaks["hbm_gbs"], "traffic": traffic,
-            "kernel": ("k_mtm_multi_d3 (FP32, %d vectors per launch)" % nvec) if multi else
+            "kernel": ("multi-vector Q apply (FP32, %d vectors per launch; k_mtm_multi_rp_d3 for N_x = 32)" % nvec)
+                      if multi else
                       "M^T M apply (%s, %d vector%s)" % ("FP64" if precision == "fp64" else "FP32", nvec,
                                                         "s" if nvec > 1 else ""),
             "peak_source": "%s MEASURED_PEAKS.json hbm_gbs" % src,

@@ -40,11 +40,15 @@
 // Every wait is bounded in time; on expiry the CTA records HH_ETIMEOUT, thread
 // 0 waits (bounded) for the copies in flight, and the CTA leaves.
 //
-// What bounds it (GB300, 32^3 x 128, 8 vectors): the shared-memory datapath.
-// Per site and vector the CTA moves about 55 bytes through shared memory (the
-// stage copies with their halo planes, the x and t rows of the y neighbours,
-// the t planes) against 8.5 bytes of HBM traffic; ncu shows the L1/shared
-// pipe at 72% when the kernel runs without its memory waits.
+// What bounds it (GB300, 32^3 x 128, 16 vectors).  The one-row form (a
+// thread owns one float4 group of one row) is bound by the shared-memory
+// datapath: per site and vector it moves about 50 bytes through it (the x
+// and t rows of the y neighbours, the t planes, the links and q through L1)
+// against 8.5 bytes of HBM traffic, and ncu shows the pipe 67-74% busy.  The
+// row-pair form (below) halves the y-neighbour reads and keeps t in
+// registers: the pipe drops to 43% and the kernel is then bound by latency,
+// with 8 warps per SM held to one block barrier per step (its register
+// count, 255, leaves no room for more warps).
 #include <cstdlib>
 
 #include "hh_apply.cuh"
@@ -174,22 +178,45 @@ struct ZRuns {
     int nr;
     int z[kMaxRuns], off[kMaxRuns], n[kMaxRuns];
 
+    // Unrolled over the run index, so that the arrays can live in registers.
     __device__ void init(int z_first, int count, int nx)
     {
         int zz = ((z_first % nx) + nx) % nx, done = 0;
         nr = 0;
-        while (done < count && nr < kMaxRuns) {
+#pragma unroll
+        for (int r = 0; r < kMaxRuns; ++r) {
             int run = count - done;
             if (zz + run > nx) run = nx - zz;
-            z[nr] = zz;
-            off[nr] = done;
-            n[nr] = run;
-            ++nr;
-            done += run;
+            z[r] = zz;
+            off[r] = done;
+            n[r] = run > 0 ? run : 0;
+            if (run > 0) nr = r + 1;
+            done += run > 0 ? run : 0;
             zz = 0;
         }
     }
 };
+
+// L2 prefetch of the next stage of 'pf': its x planes and, after the first
+// stage of a segment, its link planes.
+__device__ __forceinline__ void prefetch_stage(StageIter &pf, const ZRuns &xr, const ZRuns &lr, const MultiCfg &c,
+                                               const float *x, const float *L)
+{
+    int v, tp;
+    const int kind = pf.next(v, tp);
+    if (kind == STAGE_END) return;
+    const int P = c.P;
+    const float *xb = x + (size_t)v * c.g.N + (size_t)wrap_once(tp + 1, c.g.ntau) * c.g.V;
+#pragma unroll
+    for (int r = 0; r < kMaxRuns; ++r)
+        if (r < xr.nr) bulk_prefetch_l2(xb + (size_t)xr.z[r] * P, (unsigned)(xr.n[r] * P * sizeof(float)));
+    if (kind != STAGE_PRE) {
+        const float *lb = L + (size_t)wrap_once(tp, c.g.ntau) * c.g.V;
+#pragma unroll
+        for (int r = 0; r < kMaxRuns; ++r)
+            if (r < lr.nr) bulk_prefetch_l2(lb + (size_t)lr.z[r] * P, (unsigned)(lr.n[r] * P * sizeof(float)));
+    }
+}
 
 // Issues the copies of the stages of a CTA's range in order (thread 0 only;
 // the state lives in shared memory): stage j goes to slot j % NS, whose
@@ -217,18 +244,7 @@ struct Issuer {
 
     __device__ void prefetch_next(const MultiCfg &c, const float *x, const float *L)
     {
-        int v, tp;
-        const int kind = pf.next(v, tp);
-        if (kind == STAGE_END) return;
-        const int P = c.P;
-        const float *xb = x + (size_t)v * c.g.N + (size_t)wrap_once(tp + 1, c.g.ntau) * c.g.V;
-        for (int r = 0; r < xr.nr; ++r)
-            bulk_prefetch_l2(xb + (size_t)xr.z[r] * P, (unsigned)(xr.n[r] * P * sizeof(float)));
-        if (kind != STAGE_PRE) {
-            const float *lb = L + (size_t)wrap_once(tp, c.g.ntau) * c.g.V;
-            for (int r = 0; r < lr.nr; ++r)
-                bulk_prefetch_l2(lb + (size_t)lr.z[r] * P, (unsigned)(lr.n[r] * P * sizeof(float)));
-        }
+        prefetch_stage(pf, xr, lr, c, x, L);
     }
 
     // Issue every stage j <= upto that has not been issued yet.
@@ -249,8 +265,9 @@ struct Issuer {
             const float *xb = x + (size_t)v * c.g.N + (size_t)wrap_once(tau + 1, c.g.ntau) * c.g.V;
             float *dst = XS + (size_t)slot * XPL * P;
             mbar_expect_tx(&full[slot], stage_bytes + (issued == 0 ? extra0 : 0u));
-            for (int r = 0; r < xr.nr; ++r)
-                bulk_g2s(dst + (size_t)xr.off[r] * P, xb + (size_t)xr.z[r] * P,
+#pragma unroll
+            for (int r = 0; r < kMaxRuns; ++r)
+                if (r < xr.nr) bulk_g2s(dst + (size_t)xr.off[r] * P, xb + (size_t)xr.z[r] * P,
                          (unsigned)(xr.n[r] * P * sizeof(float)), &full[slot]);
             ++issued;
             prefetch_next(c, x, L);
@@ -444,6 +461,245 @@ __device__ __forceinline__ void multi_consumer(const MultiCfg &c, float *XS, flo
     }
 }
 
+// Row-pair form of the march (N_x = 32).  A thread owns one float4 group in
+// each of two adjacent rows y0, y0 + 1 of one part of the slab's planes, so
+// the y neighbour between the two rows comes from registers and only rows
+// y0 - 1 and y0 + 2 are read from shared memory: two 16-byte loads per plane
+// and row pair for the y neighbours instead of four.  The thread also keeps
+// its own t(tau) (written by itself in the previous step) in registers, so q
+// reads from shared memory only the y neighbours of t, plus one plane at a
+// part boundary.  Per core site this moves about 35 bytes through the
+// shared-memory datapath against about 50 for the one-row form.
+constexpr int kPairThreads = 128;  // threads per part: (32 x 32 / 4) groups / 2 rows
+template <int TZ, int NS, int PARTS, int PART>
+__device__ __forceinline__ void multi_consumer_rp(const MultiCfg &c, float *XS, float *TS, uint64_t *full,
+                                                  volatile int *abort, long long w0, long long w1,
+                                                  const float *__restrict__ x, const float *__restrict__ L,
+                                                  float *__restrict__ y, int slab, int *err)
+{
+    constexpr int NX = 32, P = NX * NX, V = NX * NX * NX, GPR = NX / 4;
+    constexpr int TPL = TZ + 2, XPL = TZ + 4, TH = TPL / PARTS, CH = TZ / PARTS;
+    constexpr int NTHREADS = kPairThreads * PARTS;
+    constexpr int TLO = PART * TH;   // first t plane of this part
+    constexpr int CLO = PART * CH;   // first core plane (core plane cc is t plane cc + 1)
+    constexpr int PC0 = CLO + 1, PC1 = CLO + CH;   // core t planes of this part
+    static_assert(TPL % PARTS == 0 && TZ % PARTS == 0, "parts split the planes evenly");
+    static_assert(PC0 - TLO >= 0 && PC1 - TLO < TH, "a part holds t(tau) of its own core planes");
+    const int ntau = c.g.ntau;
+    const size_t N = (size_t)c.g.N;
+    const int lane = (int)threadIdx.x & 31;
+    const int col = (int)threadIdx.x - PART * kPairThreads;   // 0 .. 127, all active for N_x = 32
+    const int jx = col % GPR, y0 = 2 * (col / GPR);
+    const int sA = y0 * NX + 4 * jx, sB = sA + NX;                       // rows y0, y0 + 1
+    const int sM = (y0 == 0 ? NX - 1 : y0 - 1) * NX + 4 * jx;            // row y0 - 1
+    const int sP = (y0 + 2 == NX ? 0 : y0 + 2) * NX + 4 * jx;            // row y0 + 2
+    const int src_m = (jx == 0) ? lane + GPR - 1 : lane - 1;
+    const int src_p = (jx == GPR - 1) ? lane - GPR + 1 : lane + 1;
+    const float2 mh = make_float2(-c.h, -c.h);
+    const int z0 = slab * TZ;
+    const uint64_t pol_y = l2_policy_evict_first();
+    const uint64_t pol_l = l2_policy_evict_last();
+    int zoff[TH];   // in-slice offset of each of the part's t planes (t plane p is z = z0 - 1 + p)
+#pragma unroll
+    for (int pp = 0; pp < TH; ++pp) {
+        int z = z0 - 1 + TLO + pp;
+        z = z < 0 ? z + NX : (z >= NX ? z - NX : z);
+        zoff[pp] = z * P;
+    }
+    auto halo = [&](const float4 &self, float &hm, float &hp) {
+        hm = __shfl_sync(0xffffffffu, self.w, src_m);
+        hp = __shfl_sync(0xffffffffu, self.x, src_p);
+    };
+
+    // Thread 0 issues the copies, its issuer state in registers (this form
+    // has the registers to spare; a thread holds 2 TH float4 of each of x,
+    // t and L).
+    const bool issuer = PART == 0 && threadIdx.x == 0;
+    Issuer<TZ, NS> is;
+    if (issuer) {
+        is.init(w0, w1, c, x, L, z0);
+        is.issue_upto(NS - 1, c, XS, full, x, L);
+    }
+
+    float4 xcA[TH], xcB[TH];   // x(tau) of the two rows at the part's t planes (link term)
+    float4 tcA[TH], tcB[TH];   // t(tau), computed by this thread in the previous step
+    float4 lcA[TH], lcB[TH];   // L(tau') of the current stage
+    StageIter it;
+    it.init(w0, w1, ntau);
+    int slot = 0;
+    unsigned phase = 0;
+    long long j = 0;
+    int cb = 0;
+    int failed = 0;
+    bool aborted = false;
+    for (;;) {
+        int v, tau;
+        const int kind = it.next(v, tau);
+        if (kind == STAGE_END) break;
+        if (kind != STAGE_PRE) {
+            const float *lb = L + (size_t)wrap_once(tau, ntau) * V;
+#pragma unroll
+            for (int pp = 0; pp < TH; ++pp) {
+                lcA[pp] = ldg4_hint(lb + zoff[pp] + sA, pol_l);
+                lcB[pp] = ldg4_hint(lb + zoff[pp] + sB, pol_l);
+            }
+        }
+        if (!failed) {
+            const bool ok = wait_bounded(&full[slot], phase, c.timeout_ns, abort);
+            failed = __all_sync(0xffffffffu, ok) ? 0 : 1;
+            if (failed && lane == 0) {
+                *abort = 1;
+                atomicCAS(err, 0, -6);
+            }
+        }
+        const float *X = XS + (size_t)slot * XPL * P;
+        if (!failed) {
+            if (kind == STAGE_PRE) {
+#pragma unroll
+                for (int pp = 0; pp < TH; ++pp) {
+                    xcA[pp] = ld4(X + (TLO + pp + 1) * P + sA);
+                    xcB[pp] = ld4(X + (TLO + pp + 1) * P + sB);
+                }
+            } else {
+                const bool full_step = kind == STAGE_FULL;
+                float *tn = TS + (size_t)(cb ^ 1) * TPL * P;
+                const float *T0 = TS + (size_t)cb * TPL * P;
+                float *yo = y + (size_t)v * N + (size_t)(tau < 0 ? 0 : tau) * V + (size_t)z0 * P;
+                float4 belowA = ld4(X + TLO * P + sA), hereA = ld4(X + (TLO + 1) * P + sA);
+                float4 belowB = ld4(X + TLO * P + sB), hereB = ld4(X + (TLO + 1) * P + sB);
+                // t(tau) at planes p - 1 and p of the q march (rolling)
+                float4 tbA = make_float4(0.f, 0.f, 0.f, 0.f), tbB = tbA, thA = tbA, thB = tbA;
+                if (full_step) {
+                    if (PC0 - 1 >= TLO) {
+                        tbA = tcA[PC0 - 1 >= TLO ? PC0 - 1 - TLO : 0];
+                        tbB = tcB[PC0 - 1 >= TLO ? PC0 - 1 - TLO : 0];
+                    } else {   // the plane below is the other part's
+                        tbA = ld4(T0 + (PC0 - 1) * P + sA);
+                        tbB = ld4(T0 + (PC0 - 1) * P + sB);
+                    }
+                    thA = tcA[PC0 - TLO];
+                    thB = tcB[PC0 - TLO];
+                }
+#pragma unroll
+                for (int pp = 0; pp < TH; ++pp) {
+                    const int p = TLO + pp;
+                    const float *Xp = X + (p + 1) * P;
+                    const float4 aboveA = ld4(X + (p + 2) * P + sA), aboveB = ld4(X + (p + 2) * P + sB);
+                    const float4 ymA = ld4(Xp + sM), ypB = ld4(Xp + sP);
+                    const float4 lA = lcA[pp], lB = lcB[pp];
+                    float hmA, hpA, hmB, hpB;
+                    halo(hereA, hmA, hpA);
+                    halo(hereB, hmB, hpB);
+                    const float4 tA = stencil_x2(hereA, belowA, aboveA, hereB, ymA, hmA, hpA, lA, xcA[pp], mh);
+                    const float4 tB = stencil_x2(hereB, belowB, aboveB, ypB, hereA, hmB, hpB, lB, xcB[pp], mh);
+                    xcA[pp] = hereA;
+                    xcB[pp] = hereB;
+                    belowA = hereA;
+                    belowB = hereB;
+                    hereA = aboveA;
+                    hereB = aboveB;
+                    if (p >= PC0 && p <= PC1 && full_step) {
+                        float4 taA, taB;
+                        if (pp + 1 < TH) {
+                            taA = tcA[pp + 1 < TH ? pp + 1 : 0];
+                            taB = tcB[pp + 1 < TH ? pp + 1 : 0];
+                        } else {   // the plane above is the other part's
+                            taA = ld4(T0 + (p + 1) * P + sA);
+                            taB = ld4(T0 + (p + 1) * P + sB);
+                        }
+                        const float4 gmA = ld4(T0 + p * P + sM), gpB = ld4(T0 + p * P + sP);
+                        float emA, epA, emB, epB;
+                        halo(thA, emA, epA);
+                        halo(thB, emB, epB);
+                        float *yq = yo + (p - 1) * P;
+                        st4_global_hint(yq + sA, stencil_x2(thA, tbA, taA, thB, gmA, emA, epA, lA, tA, mh), pol_y);
+                        st4_global_hint(yq + sB, stencil_x2(thB, tbB, taB, gpB, thA, emB, epB, lB, tB, mh), pol_y);
+                        tbA = thA;
+                        tbB = thB;
+                        thA = taA;
+                        thB = taB;
+                    }
+                    tcA[pp] = tA;
+                    tcB[pp] = tB;
+                }
+                // The shared-memory copy of t(tau + 1) (the other threads' y
+                // neighbours) is written after the march, so that no store
+                // sits between the loads of the march.
+#pragma unroll
+                for (int pp = 0; pp < TH; ++pp) {
+                    st4(tn + (TLO + pp) * P + sA, tcA[pp]);
+                    st4(tn + (TLO + pp) * P + sB, tcB[pp]);
+                }
+            }
+        }
+        if (kind != STAGE_PRE) {
+            if (block_sync_or<NTHREADS>(failed)) {
+                aborted = true;
+                break;
+            }
+            // Every stage up to j has been read and t(tau + 1) written:
+            // stage j's slot can take stage j + NS.
+            if (issuer) is.issue_upto(j + NS, c, XS, full, x, L);
+            cb ^= 1;
+        }
+        ++j;
+        if (++slot == NS) {
+            slot = 0;
+            phase ^= 1u;
+        }
+    }
+    if (issuer && aborted) {
+        const int never = 0;
+        const long long drain_ns = c.timeout_ns > 1000000000LL ? c.timeout_ns : 1000000000LL;
+        for (long long jj = j; jj < is.issued; ++jj)
+            wait_bounded(&full[(int)(jj % NS)], (unsigned)((jj / NS) & 1), drain_ns, &never);
+    }
+}
+
+template <int TZ, int NS, int PARTS, int MINB>
+__global__ void __launch_bounds__(kPairThreads * PARTS, MINB)
+    k_mtm_multi_rp_d3(const MultiCfg c, const float *__restrict__ L, const float *__restrict__ x,
+                      float *__restrict__ y, int *err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[NS];
+    __shared__ int s_abort;
+    using Lay = MultiLayout<TZ, NS>;
+    float *XS = (float *)smem_raw;
+    float *TS = XS + (size_t)NS * Lay::XPL * c.P;
+
+    const int slab = (int)blockIdx.x % c.nslab;
+    const int ci = (int)blockIdx.x / c.nslab;
+    const long long K = (long long)c.k * c.g.ntau;
+    const long long w0 = (long long)ci * K / c.m, w1 = (long long)(ci + 1) * K / c.m;
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < NS; ++b) mbar_init(&full[b], 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (PARTS == 1 || (int)threadIdx.x < kPairThreads)
+        multi_consumer_rp<TZ, NS, PARTS, 0>(c, XS, TS, full, &s_abort, w0, w1, x, L, y, slab, err);
+    else
+        multi_consumer_rp<TZ, NS, PARTS, (PARTS > 1 ? 1 : 0)>(c, XS, TS, full, &s_abort, w0, w1, x, L, y, slab, err);
+}
+
+template <int TZ, int NS, int PARTS, int MINB>
+cudaError_t launch_multi_rp(MultiCfg c, int nsm, const float *L, const float *x, float *y, int *err,
+                            cudaStream_t st)
+{
+    const size_t smem = MultiLayout<TZ, NS>::smem(c.P);
+    auto kern = k_mtm_multi_rp_d3<TZ, NS, PARTS, MINB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    c.nslab = c.g.nx / TZ;
+    const int ctas = nsm * MINB;
+    c.m = ctas / c.nslab > 0 ? ctas / c.nslab : 1;
+    kern<<<c.m * c.nslab, kPairThreads * PARTS, smem, st>>>(c, L, x, y, err);
+    return cudaGetLastError();
+}
+
 // TZ: core z planes of a slab; NS: pipeline stages; PARTS: parts of the
 // slab's planes (256 threads each); MINB: CTAs per SM.
 template <int NX, int TZ, int NS, int PARTS, int MINB>
@@ -492,25 +748,42 @@ cudaError_t launch_multi(MultiCfg c, int nsm, const float *L, const float *x, fl
 }
 
 // Pipeline forms (HH_APPLY_MULTI_FORM selects one):
-//   2 (default): 4-plane slabs, two stages, one part of 256 threads, two CTAs
-//      per SM (112 KB of shared memory each);
-//   1: 8-plane slabs, three stages, two parts, one CTA per SM (8 | Nx);
-//   3: 4-plane slabs, four stages, two parts, one CTA per SM.
-// Measured on GB300 (32^3 x 128, 8 vectors per launch): 2 and 1 take 94-98 us,
-// 3 takes 129 us.
+//   5 (default for N_x = 32): row pairs, 8-plane slabs, two stages, two parts
+//      of 128 threads, one CTA per SM (176 KB of shared memory);
+//   2 (default otherwise): one float4 group per thread, 4-plane slabs, two
+//      stages, one part of 256 threads, two CTAs per SM (112 KB each);
+//   1: one group per thread, 8-plane slabs, three stages, two parts, one CTA
+//      per SM (8 | N_x);
+//   3: one group per thread, 4-plane slabs, four stages, two parts, one CTA
+//      per SM;
+//   4 (N_x = 32): row pairs, 4-plane slabs, two stages, one part of 128
+//      threads, two CTAs per SM.
+// Measured on GB300 (32^3 x 128, 16 vectors per launch, cold L2, fraction of
+// the measured HBM bandwidth on (8 k + 4) bytes per site): 5: 0.52-0.535;
+// 2: 0.47-0.48; 1: 0.47; 4: 0.40-0.49; 3: 0.34.  Variants with more warps
+// per SM (two parts of row pairs in two CTAs per SM) or with a producer warp
+// of their own ran out of registers (at most 128 and 168 per thread) and
+// were slower.
 int multi_form(int nx)
 {
     const char *e = getenv("HH_APPLY_MULTI_FORM");
     const int forced = e ? atoi(e) : 0;
     if (forced == 1 && nx % 8 == 0) return 1;
-    if (forced == 3) return 3;
-    return 2;
+    if (forced == 2 || forced == 3) return forced;
+    if ((forced == 4 || forced == 5) && nx == 32) return forced;
+    return nx == 32 ? 5 : 2;
 }
 
 size_t multi_smem(int nx, int form)
 {
     const int P = nx * nx;
-    return form == 1 ? MultiLayout<8, 3>::smem(P) : form == 2 ? MultiLayout<4, 2>::smem(P) : MultiLayout<4, 4>::smem(P);
+    switch (form) {
+    case 1: return MultiLayout<8, 3>::smem(P);
+    case 2: return MultiLayout<4, 2>::smem(P);
+    case 4: return MultiLayout<4, 2>::smem(P);
+    case 5: return MultiLayout<8, 2>::smem(P);
+    default: return MultiLayout<4, 4>::smem(P);
+    }
 }
 
 }  // namespace
@@ -522,7 +795,7 @@ bool multi_mtm_ok(const Geo &g, const void *L, const void *x, const void *y)
     // dynamic shared memory, leaving 1 KB of the 227 KB for the static part
     // (two CTAs per SM: half of it each)
     const int form = multi_form(g.nx);
-    return multi_smem(g.nx, form) <= (form == 2 ? 112 : 226) * 1024;
+    return multi_smem(g.nx, form) <= (form == 2 || form == 4 ? 112 : 226) * 1024;
 }
 
 cudaError_t launch_mtm_multi_f32(const Geo &g, float h, const float *L, const float *x, float *y, int k, int *err,
@@ -548,6 +821,8 @@ cudaError_t launch_mtm_multi_f32(const Geo &g, float h, const float *L, const fl
                        : launch_multi<0, 8, 3, 2, 1>(c, nsm, L, x, y, err, st);
     case 2: return n32 ? launch_multi<32, 4, 2, 1, 2>(c, nsm, L, x, y, err, st)
                        : launch_multi<0, 4, 2, 1, 2>(c, nsm, L, x, y, err, st);
+    case 4: return launch_multi_rp<4, 2, 1, 2>(c, nsm, L, x, y, err, st);
+    case 5: return launch_multi_rp<8, 2, 2, 1>(c, nsm, L, x, y, err, st);
     default: return n32 ? launch_multi<32, 4, 4, 2, 1>(c, nsm, L, x, y, err, st)
                         : launch_multi<0, 4, 4, 2, 1>(c, nsm, L, x, y, err, st);
     }

@@ -2,11 +2,13 @@
 field, against the FP64 oracle on the same seeded inputs, per element.
 
 The FP32 Q = M^T M of d = 3 lattices with 4 | Nx <= 32 runs in the persistent
-multi-vector kernel (slabs of 8 planes when 8 | Nx, else 4; the x halo by
-warp shuffles when a row of float4 groups divides a warp, else from shared
-memory); the shapes below cover both slab forms, both halo forms, slabs that
-wrap onto themselves (Nx = 4, 8), short and odd N_tau (uneven ranges per CTA),
-and the full 32^3 x 128 lattice.  Other operators, dtypes and lattices go
+multi-vector kernel (pipeline forms selected by HH_APPLY_MULTI_FORM: 4- or
+8-plane slabs, one or two parts, one float4 group per thread or, for
+Nx = 32, a pair of rows per thread; the x halo by warp shuffles when a row of
+float4 groups divides a warp, else from shared memory); the shapes below
+cover every form, both halo forms, slabs that wrap onto themselves (Nx = 4,
+8), short and odd N_tau (uneven ranges per CTA, ranges that cross from one
+vector to the next), and the full 32^3 x 128 lattice.  Other operators, dtypes and lattices go
 through one hh_apply per vector.  Tolerance as for the single applies:
 |y - y_ref|_i <= 2e-6 (|M| |x|)_i in FP32, 1e-12 in FP64.
 """
@@ -76,12 +78,23 @@ def test_multi_mtm_fp32_per_element(hh, nx, ntau, k):
     _run(hh, 3, nx, ntau, k)
 
 
-@pytest.mark.parametrize("nx,ntau,k", [(16, 10, 2), (32, 6, 3), (8, 5, 4)])
-def test_multi_mtm_fp32_four_plane_slabs(hh, monkeypatch, nx, ntau, k):
-    """The 4-plane pipeline (three stages, two t buffers) on lattices that would
-    take 8-plane slabs."""
-    monkeypatch.setenv("HH_APPLY_MULTI_TZ", "4")
+@pytest.mark.parametrize("form", [1, 2, 3, 4])
+@pytest.mark.parametrize("nx,ntau,k", [(32, 6, 3), (32, 3, 8), (32, 17, 5), (16, 10, 2), (8, 5, 4)])
+def test_multi_mtm_fp32_pipeline_forms(hh, monkeypatch, form, nx, ntau, k):
+    """Every pipeline form besides the defaults (form 5 for Nx = 32, form 2
+    otherwise), which run in the tests above; form 4 takes Nx = 32 only, other
+    lattices fall back to form 2."""
+    monkeypatch.setenv("HH_APPLY_MULTI_FORM", str(form))
     _run(hh, 3, nx, ntau, k)
+
+
+@pytest.mark.parametrize("form", [2, 4])
+def test_multi_mtm_other_forms_full_size(hh, monkeypatch, form):
+    """The one-row form 2 and the row-pair form 4 on the 32^3 x 128 lattice,
+    three vectors (the default form 5 runs in test_multi_mtm_full_size_lattice)."""
+    monkeypatch.setenv("HH_APPLY_MULTI_FORM", str(form))
+    wl = workloads.C2
+    _run(hh, wl.d, wl.nx, wl.ntau, 3, seed=wl.seed + 1)
 
 
 def test_multi_kernel_single_vector_path(hh, monkeypatch):
