@@ -740,7 +740,7 @@ def run_serve(args, world, rank, local, dev, stream):
         rates = [float(x) for x in (args.rates if arm == "mixed" else args.fp64_rates).split(",")]
         for rate in rates:
             below = rate < 1.0
-            n_req = args.requests_low if below else args.requests
+            n_req = (args.requests_low if arm == "mixed" else args.fp64_requests_low) if below else args.requests
             # below capacity: long enough for every arrival plus a minute of service
             cap = n_req / rate + 60.0 if below else args.serve_cap_s
             r = serve_one(args, rate, arm, rank, dev, stream, n_req, cap, args.serve_checks)
@@ -758,6 +758,7 @@ def run_serve(args, world, rank, local, dev, stream):
             "data": "synthetic",
             "config": {"workload": "serve_poisson", "seed": workloads.SERVE_SEED,
                        "requests_per_rate": args.requests, "requests_below_capacity": args.requests_low,
+                       "requests_below_capacity_fp64": args.fp64_requests_low,
                        "cap_s_per_rate": args.serve_cap_s,
                        "d1": {"nx": [64, 2048], "ntau": [64, 512]}, "d3": {"nx": [8, 24], "ntau": [40, 256]},
                        "trajectory_n_md": args.serve_n_md, "trajectory_dt": args.serve_dt,
@@ -792,7 +793,8 @@ def main():
     ap.add_argument("--fp64-rates", default="10,1000", help="serve: arrival rates of the FP64 arm")
     ap.add_argument("--serve-arms", default="mixed,fp64")
     ap.add_argument("--requests", type=int, default=200, help="serve: requests per rate")
-    ap.add_argument("--requests-low", type=int, default=30, help="serve: requests at rates below 1/s")
+    ap.add_argument("--requests-low", type=int, default=30, help="serve: requests at rates below 1/s (mixed arm)")
+    ap.add_argument("--fp64-requests-low", type=int, default=30, help="serve: requests at rates below 1/s (FP64 arm)")
     ap.add_argument("--serve-cap-s", type=float, default=100.0, help="serve: wall-time cap per rate")
     ap.add_argument("--serve-checks", type=int, default=2, help="serve: alone-vs-mix checks per rate")
     ap.add_argument("--serve-n-md", type=int, default=4)
