@@ -488,10 +488,9 @@ int hh_slab_solve(hh_slab *s, const double *b, double *x, hh_solve_info *info);
 
 /* ---- Allocation-free solve ------------------------------------------------
  * The paper has no counterpart of this entry point; it exists for callers
- * that cannot allocate memory when they need a solve: code running while its
- * stream is captured into a CUDA graph (cudaMalloc is not allowed there),
- * plug-ins inside applications that own the device allocator, and loops that
- * must not take allocator locks.  Everything the FP64 CG needs beyond the
+ * that cannot allocate memory when they need a solve: plug-ins inside
+ * applications that own the device allocator, and loops that must not take
+ * allocator locks.  Everything the FP64 CG needs beyond the
  * caller's sigma, b and x lives in one file-scope device array of
  * HH_NOALLOC_SCRATCH_MB (about 9 MiB), which every device that loads the
  * library keeps until the process exits.
@@ -507,14 +506,14 @@ int hh_slab_solve(hh_slab *s, const double *b, double *x, hh_solve_info *info);
  *   cuda_stream: the cudaStream_t to run on (NULL: legacy default stream).
  *   info: if non-NULL the call synchronises the stream and fills it, and
  *            returns the solve's status (HH_ENOCONV, HH_ETIMEOUT, HH_ENUMERIC).
- *            It must be NULL while the stream is being captured (the
- *            synchronisation is not allowed there; HH_EINVAL).  With info
+ *            A non-NULL info on a stream in capture mode is refused with
+ *            HH_EINVAL (the synchronisation is not allowed there).  With info
  *            NULL the call only enqueues the work and returns HH_OK: the
  *            solve's outcome is not reported, and the next call overwrites
  *            it in the shared array.
  * Every call looks up the array's device address, which stays valid if the
  * caller resets the device; the first call on a device also queries the
- * kernel's occupancy: make that first call before any stream capture.
+ * kernel's occupancy (which allocates nothing).
  * The call allocates no device or host memory.  All calls share the array and
  * overwrite it (the call clears what must start at zero); calls whose GPU work
  * overlaps in time race on it and must be serialised by the caller. */

@@ -1,10 +1,9 @@
 // A solve entry point that allocates nothing.
 //
 // Some callers cannot allocate memory at the point where they need a solve:
-// code running while a CUDA stream is being captured into a graph (where
-// cudaMalloc is not permitted), plug-ins hosted by an application that owns
-// the device allocator and forbids other allocations, or real-time loops that
-// must not take the allocator's locks.  hh_solve_noalloc serves them: the
+// plug-ins hosted by an application that owns the device allocator and
+// forbids other allocations, or real-time loops that must not take the
+// allocator's locks.  hh_solve_noalloc serves them: the
 // caller passes the field sigma, the right-hand side b and the output x, and
 // every other buffer the FP64 CG needs (links, CG vectors, the system table,
 // tiles, signal slots, the control block) lives in one file-scope
@@ -157,7 +156,7 @@ extern "C" int hh_solve_noalloc(const hh_lattice *lat, const hh_params *p, const
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (info) {
         // Filling info copies the outcome to the host and synchronises the
-        // stream, which a stream being captured into a graph does not allow.
+        // stream, which a stream in capture mode does not allow.
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return HH_ECUDA;
         if (cap != cudaStreamCaptureStatusNone) return HH_EINVAL;

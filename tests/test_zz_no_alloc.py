@@ -1,8 +1,8 @@
 """The allocation-free solve entry point against the context solver.
 
 hh_solve_noalloc is for callers that cannot allocate when they need a solve
-(inside CUDA-graph capture, inside applications that own the allocator); its
-scratch is a fixed device array shared by all calls.  This file is collected
+(inside applications that own the allocator, loops that must not take its
+locks); its scratch is a fixed device array shared by all calls.  This file is collected
 last on purpose.  It checks, through the C ABI, that two calls in a row (the
 second on a different lattice, over whatever the first left in the shared
 array) give the same solution as hh_solve within the solver tolerance the
