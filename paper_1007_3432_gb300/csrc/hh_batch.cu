@@ -25,6 +25,7 @@
 #include "../../include/hubhmc.h"
 #include "hh_engine.cuh"
 #include "hh_kernels.cuh"
+#include "hh_trace.cuh"
 
 using namespace hh;
 
@@ -689,6 +690,7 @@ int step(hh_batch *b)
         const char *e = getenv("HH_ENGINE_DROP_SIGNAL");
         c.drop_sig = e ? atoi(e) : 0;
     }
+    TraceRange tr("hh batch chunk");
     HB_TRY(cudaMemcpyAsync(b->d_ctl, &c, sizeof(c), cudaMemcpyHostToDevice, b->stream));
     rc = launch_chunk(b, grid);
     if (rc) return rc;

@@ -13,6 +13,7 @@
 #include "hh_apply.cuh"
 #include "hh_engine.cuh"
 #include "hh_kernels.cuh"
+#include "hh_trace.cuh"
 
 using namespace hh;
 
@@ -340,6 +341,7 @@ int ctx_force(hh_ctx *c, int n_rhs, double *pi, double eps, double *F_out, int *
 // Enqueue one complete solve of the current plan and fold its statistics.
 int run_engine(hh_ctx *c)
 {
+    TraceRange tr("hh engine solve");
     const Plan &P = c->plan;
     k_engine_reset<<<1, 256, 0, c->stream>>>(c->d_state[0], c->d_state[1], P.nsys, c->d_sig,
                                              c->max_tiles, c->d_ctl, c->timeout_ns, engine_drop_signal());
@@ -641,6 +643,7 @@ int hh_init_field_random(hh_ctx *c, uint64_t seed)
 
 int hh_apply(hh_ctx *c, int op, const void *x, void *y, int dtype)
 {
+    TraceRange tr("hh_apply");
     if (!c || !x || !y || x == y) return HH_EINVAL;
     if (op != HH_OP_M && op != HH_OP_MT && op != HH_OP_MTM) return HH_EINVAL;
     const double h = c->prm.t * c->prm.dtau;
@@ -744,6 +747,7 @@ int hh_set_timeout(hh_ctx *c, double seconds)
 
 int hh_apply_multi(hh_ctx *c, int op, const void *x, void *y, int n_vec, int dtype)
 {
+    TraceRange tr("hh_apply_multi");
     if (!c || !x || !y || n_vec < 1) return HH_EINVAL;
     if (op != HH_OP_M && op != HH_OP_MT && op != HH_OP_MTM) return HH_EINVAL;
     if (dtype != HH_DTYPE_F64 && dtype != HH_DTYPE_F32) return HH_EINVAL;
@@ -769,6 +773,7 @@ int hh_apply_multi(hh_ctx *c, int op, const void *x, void *y, int n_vec, int dty
 // One solve of the current plan from x = 0 (x0 = 0) or from the x passed in.
 static int solve_from(hh_ctx *c, const double *b, double *x, int n_rhs, int x0, hh_solve_info *info)
 {
+    TraceRange tr("hh_solve");
     if (!c || !b || !x || !aligned16(b) || !aligned16(x)) return HH_EINVAL;
     int rc = ensure_rhs(c, n_rhs);
     if (rc) return rc;
@@ -921,6 +926,7 @@ int leapfrog_enqueue(hh_ctx *c, double *pi, const double *chi, int n_rhs, int n_
     const int chrono = c->prm.chrono;
     const long long nx = (long long)n_rhs * c->N;
     for (int j = 0; j < forces; ++j) {
+        TraceRange tr("hh md force");
         md_schedule(c->prm.integrator, n_md, dt, j, &kick, &drift);
         // Chronological initial guess (chrono 1: the previous force's
         // solution, already in xsol; 2: the linear extrapolation of the last
@@ -984,17 +990,22 @@ int hh_trajectory(hh_ctx *c, int n_md, double dt, uint64_t traj, hh_traj_info *i
     k_zero_stats<<<1, 32, 0, c->stream>>>(c->d_stats);
     HH_TRY(cudaGetLastError());
     c->n_launch += 1;
+    TraceRange tr("hh_trajectory");
     // Momenta and pseudofermion heatbath chi_a = M^T xi_a (Eqs. (11)-(12)).
-    HH_TRY(launch_gaussian(c->pi, c->N, seed, 1, 0, traj, chain, c->stream));
-    for (int a = 0; a < npf; ++a) {
-        HH_TRY(launch_gaussian(c->tmp, c->N, seed, 2, a, traj, chain, c->stream));
-        HH_TRY(launch_apply_f64(c->geo, 1, h, c->L64, c->tmp, c->chi + (size_t)a * c->N, c->stream,
-                                c->prm.link_order));
+    {
+        TraceRange th("hh heatbath");
+        HH_TRY(launch_gaussian(c->pi, c->N, seed, 1, 0, traj, chain, c->stream));
+        for (int a = 0; a < npf; ++a) {
+            HH_TRY(launch_gaussian(c->tmp, c->N, seed, 2, a, traj, chain, c->stream));
+            HH_TRY(launch_apply_f64(c->geo, 1, h, c->L64, c->tmp, c->chi + (size_t)a * c->N, c->stream,
+                                    c->prm.link_order));
+        }
     }
     HH_TRY(cudaMemcpyAsync(c->sigma0, c->sigma, (size_t)c->N * sizeof(double),
                            cudaMemcpyDeviceToDevice, c->stream));
     int rc = leapfrog_enqueue(c, c->pi, c->chi, npf, n_md, dt, &c->d_sc->H0, &c->d_sc->H1);
     if (rc) return rc;
+    TraceRange tm("hh metropolis");
     HH_TRY(launch_metropolis(c->d_sc, seed, traj, chain, c->stream));
     HH_TRY(launch_restore(c->geo, c->prm.A, c->d_sc, c->sigma, c->sigma0, c->L64, c->L32, c->stream));
     HH_TRY(links16_after(c));

@@ -26,6 +26,7 @@
 #include "../../include/hubhmc.h"
 #include "hh_apply.cuh"
 #include "hh_kernels.cuh"
+#include "hh_trace.cuh"
 
 using namespace hh;
 
@@ -134,6 +135,7 @@ int grid_for(long long n)
 // and receives the previous rank's slice into recv_dev; dir = -1 the other way.
 int exchange_slice(hh_slab *s, int dir, const double *send_dev, double *recv_dev)
 {
+    TraceRange tr(dir > 0 ? "hh slab halo +1" : "hh slab halo -1");
     const size_t bytes = sizeof(double) * (size_t)s->V;
     double *hs = s->h_stage, *hr = s->h_stage + s->V;
     HS_TRY(cudaMemcpyAsync(hs, send_dev, bytes, cudaMemcpyDeviceToHost, s->stream));
@@ -289,6 +291,7 @@ int hh_slab_apply(hh_slab *s, int op, const double *x, double *y)
 
 int hh_slab_solve(hh_slab *s, const double *b, double *x, hh_solve_info *info)
 {
+    TraceRange tr("hh_slab_solve");
     if (!s || !b || !x) return HH_EINVAL;
     const size_t V = (size_t)s->V;
     const long long n = s->own;
