@@ -68,14 +68,16 @@ def test_engine_wait_runs_out_then_context_recovers(hh, monkeypatch, precision, 
         _check_solution(d, nx, ntau, sigma, b, x.cpu().numpy())
 
 
-def test_multi_apply_wait_runs_out_then_recovers(hh, monkeypatch):
+@pytest.mark.parametrize("form", ["5", "2"])
+def test_multi_apply_wait_runs_out_then_recovers(hh, monkeypatch, form):
     """The multi-vector apply's bounded waits for its bulk copies: when the
     first stage's barrier cannot complete, the kernel records HH_ETIMEOUT
     (reported by hh_counters_get), waits (bounded) for the copies it issued
     and leaves; without the injection the same context's apply matches the
-    oracle."""
+    oracle.  In the row-pair form (5) and the one-row form (2)."""
     from paper_1007_3432_gb300.binding import HH_ETIMEOUT, HHError
-    d, nx, ntau, k = 3, 16, 20, 3
+    monkeypatch.setenv("HH_APPLY_MULTI_FORM", form)
+    d, nx, ntau, k = 3, 32, 10, 3
     n = nx ** d * ntau
     sigma = workloads.sigma_field(n, seed=903)
     xs = np.stack([workloads.source(n, seed=904, rhs=a) for a in range(k)]).astype(np.float32)
