@@ -90,8 +90,8 @@ def bytes_per_site(kind, precision):
 # as it stands, from one ncu --set full capture each (dram__bytes_read.sum +
 # dram__bytes_write.sum over a 202-iteration launch; profiles/engine_kernel_*).
 # A launch's traffic scales with its iterations.
-ENGINE_DRAM_PER_ITER = {("d1_nx1024_nt512", "fp64"): (12760832 + 71143936) / 202.0,
-                        ("d3_nx32_nt128", "mixed"): (35681830000 + 27052524000) / 202.0}
+ENGINE_DRAM_PER_ITER = {("d1_nx1024_nt512", "fp64"): (12724992 + 70935296) / 202.0,
+                        ("d3_nx32_nt128", "mixed"): (35195983000 + 27069706000) / 202.0}
 
 # DRAM bytes (read + write) per launch of the Q apply from one ncu capture each
 # (profiles/mtm_*): (workload, dtype, vectors per launch) -> bytes.
