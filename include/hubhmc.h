@@ -486,6 +486,29 @@ int hh_slab_apply(hh_slab *s, int op, const double *x, double *y);
  * non-positive <p, Q p>. */
 int hh_slab_solve(hh_slab *s, const double *b, double *x, hh_solve_info *info);
 
+/* ---- Debug build: index checks ---------------------------------------------
+ * Not part of the method.  A library compiled with -DHH_BOUNDS_CHECK
+ * (libhubhmc_check.so, built by build(bounds_check=True); the Python binding
+ * loads it when HH_BOUNDS_CHECK=1) checks the neighbour indices of every
+ * stencil (scalar and W-site groups, the shifts by one time slice), the tile
+ * ranges of the CG engine and the source ranges of the multi-vector apply's
+ * bulk copies.  An index outside its range is recorded in a device error word
+ * (the first per translation unit) and replaced by an in-range one, so no
+ * access leaves its buffer and nothing traps; results are then wrong and the
+ * record says where.
+ *   op: HH_BOUNDS_READ reads and clears the records; HH_BOUNDS_SELFTEST first
+ *       runs a one-thread kernel whose check of an index past its range must
+ *       fail (nothing is accessed), then reads and clears (synchronises the
+ *       device).
+ *   enabled (may be NULL): 1 in the checked build, 0 otherwise.
+ *   record (may be NULL): the first record, (check code << 32) | index, or 0.
+ * Returns HH_EBOUNDS if a check failed since the last read, HH_OK otherwise
+ * (always HH_OK in the default build), HH_ECUDA if the device cannot be read. */
+#define HH_EBOUNDS (-9)     /* an index check of the debug build failed */
+#define HH_BOUNDS_READ 0
+#define HH_BOUNDS_SELFTEST 1
+int hh_bounds_check(int op, int *enabled, long long *record);
+
 /* ---- Allocation-free solve ------------------------------------------------
  * The paper has no counterpart of this entry point; it exists for callers
  * that cannot allocate memory when they need a solve: plug-ins inside

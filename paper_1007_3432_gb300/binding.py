@@ -11,10 +11,13 @@ import re
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libhubhmc.so")
+# The debug build with index checks (HH_BOUNDS_CHECK=1 selects it).
+LIB_CHECK_PATH = os.path.join(HERE, "lib", "libhubhmc_check.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "hubhmc.h")
 
 HH_OK, HH_EINVAL, HH_ENOMEM, HH_ECUDA = 0, -1, -2, -3
-HH_ENOCONV, HH_ENUMERIC, HH_ETIMEOUT, HH_EBUSY, HH_ESIZE = -4, -5, -6, -7, -8
+HH_ENOCONV, HH_ENUMERIC, HH_ETIMEOUT, HH_EBUSY, HH_ESIZE, HH_EBOUNDS = -4, -5, -6, -7, -8, -9
+HH_BOUNDS_READ, HH_BOUNDS_SELFTEST = 0, 1
 HH_NOALLOC_MAX_SITES = 262144
 HH_FP64, HH_MIXED, HH_MIXED_BF16LINK, HH_MIXED_FIX16LINK = 0, 1, 2, 3
 PRECISIONS = {"fp64": HH_FP64, "mixed": HH_MIXED, "mixed-bf16link": HH_MIXED_BF16LINK,
@@ -122,13 +125,16 @@ INTEGRATORS = {"leapfrog": HH_LEAPFROG, "omelyan": HH_OMELYAN}
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load the CUDA library; raises if it has not been built."""
+def load(path: str = None):
+    """Load the CUDA library (the index-checking debug build when
+    HH_BOUNDS_CHECK=1); raises if it has not been built."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = LIB_CHECK_PATH if os.environ.get("HH_BOUNDS_CHECK") == "1" else LIB_PATH
     if not os.path.exists(path):
-        raise ImportError("libhubhmc.so not built (run __graft_entry__.build()): %s" % path)
+        raise ImportError("%s not built (run __graft_entry__.build()): %s" % (os.path.basename(path), path))
     L = ctypes.CDLL(path)
     vp, i, d, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint64
     sig = {
@@ -153,6 +159,7 @@ def load(path: str = LIB_PATH):
         "hh_batch_set_timeout": (i, [vp, d]),
         "hh_counters_reset": (i, [vp, i]),
         "hh_counters_get": (i, [vp, ctypes.POINTER(hh_counters)]),
+        "hh_bounds_check": (i, [i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong)]),
         "hh_solve_noalloc": (i, [ctypes.POINTER(hh_lattice), ctypes.POINTER(hh_params), vp, vp, vp, vp,
                                  ctypes.POINTER(hh_solve_info)]),
         "hh_slab_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(hh_lattice), ctypes.POINTER(hh_params), i, i,
@@ -343,6 +350,19 @@ class Context:
         c = hh_counters()
         check(self._lib.hh_counters_get(self._h, ctypes.byref(c)), "hh_counters_get")
         return c.as_dict()
+
+
+def bounds_check(selftest=False):
+    """Index-check records of the debug build: (status, enabled, record);
+    status HH_EBOUNDS if a check failed since the last call."""
+    L = load()
+    en = ctypes.c_int(0)
+    rec = ctypes.c_longlong(0)
+    rc = L.hh_bounds_check(HH_BOUNDS_SELFTEST if selftest else HH_BOUNDS_READ, ctypes.byref(en),
+                           ctypes.byref(rec))
+    if rc not in (HH_OK, HH_EBOUNDS):
+        check(rc, "hh_bounds_check")
+    return rc, en.value, rec.value
 
 
 def solve_noalloc(d, nx, ntau, sigma, b, x, t=1.0, dtau=0.05, A=0.5, cg_tol=1e-10, cg_maxit=1000000,

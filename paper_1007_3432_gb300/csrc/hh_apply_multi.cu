@@ -262,12 +262,29 @@ struct Issuer {
                 break;
             }
             const int slot = (int)(issued % NS);
+#ifdef HH_BOUNDS_CHECK
+            {
+                // The copy's vector and slice, and each run's planes, inside x.
+                int vv = v, ts = wrap_once(tau + 1, c.g.ntau);
+                HH_CHECK(vv, 0, c.k, BC_COPY);
+                HH_CHECK(ts, 0, c.g.ntau, BC_COPY);
+                v = vv;
+                tau = ts - 1;
+                for (int r = 0; r < kMaxRuns; ++r)
+                    if (r < xr.nr) {
+                        int zend = xr.z[r] + xr.n[r], oend = xr.off[r] + xr.n[r];
+                        HH_CHECK(zend, 1, c.g.nx + 1, BC_COPY);
+                        HH_CHECK(oend, 1, XPL + 1, BC_COPY);
+                        if (zend != xr.z[r] + xr.n[r] || oend != xr.off[r] + xr.n[r]) xr.n[r] = 0;
+                    }
+            }
+#endif
             const float *xb = x + (size_t)v * c.g.N + (size_t)wrap_once(tau + 1, c.g.ntau) * c.g.V;
             float *dst = XS + (size_t)slot * XPL * P;
             mbar_expect_tx(&full[slot], stage_bytes + (issued == 0 ? extra0 : 0u));
 #pragma unroll
             for (int r = 0; r < kMaxRuns; ++r)
-                if (r < xr.nr) bulk_g2s(dst + (size_t)xr.off[r] * P, xb + (size_t)xr.z[r] * P,
+                if (r < xr.nr && xr.n[r] > 0) bulk_g2s(dst + (size_t)xr.off[r] * P, xb + (size_t)xr.z[r] * P,
                          (unsigned)(xr.n[r] * P * sizeof(float)), &full[slot]);
             ++issued;
             prefetch_next(c, x, L);

@@ -444,6 +444,57 @@ void hh_default_params(hh_params *p)
     p->link_order = 0;
 }
 
+#ifdef HH_BOUNDS_CHECK
+}  // extern "C"
+namespace hh {
+namespace bounds {
+static std::vector<Reader> &readers()
+{
+    static std::vector<Reader> r;
+    return r;
+}
+// Called by each translation unit's registrar while the library loads.
+void register_reader(Reader r)
+{
+    readers().push_back(r);
+}
+}  // namespace bounds
+}  // namespace hh
+namespace {
+__global__ void k_bounds_selftest(int n)
+{
+    int idx = n;   // one past [0, n): the check records it and substitutes 0
+    HH_CHECK(idx, 0, n, hh::BC_SELFTEST);
+}
+}  // namespace
+extern "C" {
+#endif
+
+int hh_bounds_check(int op, int *enabled, long long *record)
+{
+    if (op != HH_BOUNDS_READ && op != HH_BOUNDS_SELFTEST) return HH_EINVAL;
+#ifdef HH_BOUNDS_CHECK
+    if (enabled) *enabled = 1;
+    if (op == HH_BOUNDS_SELFTEST) {
+        k_bounds_selftest<<<1, 1>>>(1000);
+        if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return HH_ECUDA;
+    } else if (cudaDeviceSynchronize() != cudaSuccess) {
+        return HH_ECUDA;
+    }
+    unsigned long long first = 0;
+    for (hh::bounds::Reader r : hh::bounds::readers()) {
+        const unsigned long long v = r();
+        if (v && !first) first = v;
+    }
+    if (record) *record = (long long)(first & ~(1ull << 63));
+    return first ? HH_EBOUNDS : HH_OK;
+#else
+    if (enabled) *enabled = 0;
+    if (record) *record = 0;
+    return HH_OK;
+#endif
+}
+
 const char *hh_strerror(int code)
 {
     switch (code) {
@@ -455,6 +506,8 @@ const char *hh_strerror(int code)
     case HH_ENUMERIC: return "NaN or Inf in a reduction";
     case HH_ETIMEOUT: return "device-side wait timed out";
     case HH_EBUSY: return "no free slot or memory budget";
+    case HH_ESIZE: return "problem larger than the static scratch";
+    case HH_EBOUNDS: return "an index check of the debug build failed";
     default: return "unknown error";
     }
 }

@@ -12,6 +12,54 @@
 namespace hh {
 
 // ---------------------------------------------------------------------------
+// Index checks of the debug build (compiled with -DHH_BOUNDS_CHECK): an index
+// outside [lo, hi) is recorded in a device error word (the first one per
+// translation unit: check code << 32 | index, top bit set) and replaced by lo,
+// so the access stays in bounds and nothing traps.  hh_bounds_check_status
+// reads and clears the words of every translation unit.  In the default
+// build the checks compile to nothing.
+// ---------------------------------------------------------------------------
+enum BoundsCode : int {
+    BC_NEIGHBOUR = 1,   // a neighbour site of the scalar stencil
+    BC_GROUP = 2,       // a neighbour row of a W-site group
+    BC_ROW = 3,         // a site shifted by one time slice
+    BC_TILE = 4,        // a tile range of the CG engine
+    BC_COPY = 5,        // a bulk copy of the multi-vector apply (source plane range)
+    BC_SELFTEST = 15,   // the self-test kernel
+};
+
+#ifdef HH_BOUNDS_CHECK
+namespace bounds {
+static __device__ unsigned long long word;   // one per translation unit
+using Reader = unsigned long long (*)();
+void register_reader(Reader r);               // in hh_capi.cu
+static unsigned long long read_and_clear()
+{
+    unsigned long long v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, word, sizeof(v)) != cudaSuccess) return 0;
+    cudaMemcpyToSymbol(word, &z, sizeof(z));
+    return v;
+}
+static struct Registrar {
+    Registrar() { register_reader(&read_and_clear); }
+} registrar;
+}  // namespace bounds
+
+__device__ __forceinline__ int check_index(int idx, int lo, int hi, int code)
+{
+    if (idx < lo || idx >= hi) {
+        atomicCAS(&bounds::word, 0ull,
+                  (1ull << 63) | ((unsigned long long)(unsigned)code << 32) | (unsigned long long)(unsigned)idx);
+        return lo;
+    }
+    return idx;
+}
+#define HH_CHECK(idx, lo, hi, code) ((idx) = ::hh::check_index((idx), (lo), (hi), (code)))
+#else
+#define HH_CHECK(idx, lo, hi, code) ((void)0)
+#endif
+
+// ---------------------------------------------------------------------------
 // Division by a run-time invariant 32-bit divisor (Granlund & Montgomery,
 // "Division by invariant integers using multiplication", PLDI 1994, round-up
 // variant with a 33-bit multiplier): q = (umulhi(n, m) + n) >> s.
@@ -94,6 +142,11 @@ __device__ __forceinline__ void neighbours(const Geo &g, int i, Nbr &nb)
     }
     nb.prev = (tau == 0) ? i + (g.ntau - 1) * g.V : i - g.V;
     nb.next = ((int)tau == g.ntau - 1) ? i - (g.ntau - 1) * g.V : i + g.V;
+#ifdef HH_BOUNDS_CHECK
+    for (int k = 0; k < 2 * g.d; ++k) HH_CHECK(nb.sp[k], 0, g.N, BC_NEIGHBOUR);
+    HH_CHECK(nb.prev, 0, g.N, BC_NEIGHBOUR);
+    HH_CHECK(nb.next, 0, g.N, BC_NEIGHBOUR);
+#endif
 }
 
 // Sum of the 2d spatial neighbours in a fixed order.
@@ -196,11 +249,15 @@ __device__ __forceinline__ void prefetch_l2(const void *p)
 // Site j shifted one slice earlier / later (cyclic in tau).
 __device__ __forceinline__ int row_prev(const Geo &g, int j)
 {
-    return j >= g.V ? j - g.V : j + (g.ntau - 1) * g.V;
+    int r = j >= g.V ? j - g.V : j + (g.ntau - 1) * g.V;
+    HH_CHECK(r, 0, g.N, BC_ROW);
+    return r;
 }
 __device__ __forceinline__ int row_next(const Geo &g, int j)
 {
-    return j < g.N - g.V ? j + g.V : j - (g.ntau - 1) * g.V;
+    int r = j < g.N - g.V ? j + g.V : j - (g.ntau - 1) * g.V;
+    HH_CHECK(r, 0, g.N, BC_ROW);
+    return r;
 }
 
 template <typename T, int W>
@@ -347,6 +404,19 @@ __device__ __forceinline__ void group_nbrs(const Geo &g, int i, GroupNbr &nb)
     }
     nb.prev = (tau == 0) ? i + (g.ntau - 1) * g.V : i - g.V;
     nb.next = ((int)tau == g.ntau - 1) ? i - (g.ntau - 1) * g.V : i + g.V;
+#ifdef HH_BOUNDS_CHECK
+    // single sites x - 1 and x + W; W-site rows elsewhere
+    HH_CHECK(nb.left, 0, g.N, BC_GROUP);
+    HH_CHECK(nb.right, 0, g.N, BC_GROUP);
+    if (D == 3) {
+        HH_CHECK(nb.yp, 0, g.N - W + 1, BC_GROUP);
+        HH_CHECK(nb.ym, 0, g.N - W + 1, BC_GROUP);
+        HH_CHECK(nb.zp, 0, g.N - W + 1, BC_GROUP);
+        HH_CHECK(nb.zm, 0, g.N - W + 1, BC_GROUP);
+    }
+    HH_CHECK(nb.prev, 0, g.N - W + 1, BC_GROUP);
+    HH_CHECK(nb.next, 0, g.N - W + 1, BC_GROUP);
+#endif
 }
 
 // Spatial hopping sums of a group: for site u the x neighbours are the

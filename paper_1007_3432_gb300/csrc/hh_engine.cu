@@ -789,6 +789,15 @@ __device__ double slotA(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 template <int SLOT, int FD>
 __device__ double run_slot(const EngSystem &Y, const TileCtl &c, const EngTile &T)
 {
+#ifdef HH_BOUNDS_CHECK
+    {
+        // A tile outside its system is recorded and skipped.
+        int b = T.begin, e = T.end;
+        HH_CHECK(b, 0, Y.g.N + 1, BC_TILE);
+        HH_CHECK(e, b, Y.g.N + 1, BC_TILE);
+        if (b != T.begin || e != T.end) return 0.0;
+    }
+#endif
     if (FD == 4) {
         // Exact-block form: scalar loops, three-slot form (ENGINE_EXBLOCK).
         if (SLOT == 1) {

@@ -35,6 +35,19 @@ def test_strerror_and_defaults_need_no_gpu(lib):
     assert L.hh_destroy(None) == 0
 
 
+def test_bounds_check_is_off_in_the_default_build(lib):
+    """The default library compiles the index checks out: hh_bounds_check
+    reports them disabled, with no record, without touching the device, and
+    refuses an unknown op."""
+    from paper_1007_3432_gb300 import binding
+    L = binding.load()
+    en, rec = ctypes.c_int(7), ctypes.c_longlong(7)
+    assert L.hh_bounds_check(binding.HH_BOUNDS_READ, ctypes.byref(en), ctypes.byref(rec)) == binding.HH_OK
+    assert en.value == 0 and rec.value == 0
+    assert L.hh_bounds_check(5, None, None) == binding.HH_EINVAL
+    assert L.hh_strerror(binding.HH_EBOUNDS).decode().startswith("an index check")
+
+
 def test_create_rejects_bad_shapes_before_touching_the_device(lib):
     from paper_1007_3432_gb300 import binding
     L = binding.load()
