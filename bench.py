@@ -605,6 +605,66 @@ def run_batch(args, world, rank, local, dev, stream):
         print(json.dumps(line), flush=True)
 
 
+def run_slab(args, wl, world, rank, local, dev, stream):
+    """--mode slab: the time-slab decomposition of one lattice over the ranks
+    (hh_slab_*; halos and sums staged through host memory by the
+    torch.distributed callbacks over a gloo group), FP64 CG on one
+    right-hand side, capped at --cg-maxit iterations (default 2000 here).
+    Reports the wall time per CG iteration, max over ranks, beside the
+    context solver's on the same lattice (rank 0, one GPU)."""
+    import torch
+    from paper_1007_3432_gb300 import Context
+    from paper_1007_3432_gb300.binding import HH_ENOCONV, Slab, TorchDistComm
+    group = None
+    if world > 1:
+        import torch.distributed as dist
+        group = dist.new_group(backend="gloo")
+    maxit = args.cg_maxit if args.cg_maxit < 1000000 else 2000
+    V, n = wl.nx ** wl.d, wl.nsites
+    t0, t1 = rank * wl.ntau // world, (rank + 1) * wl.ntau // world
+    sigma = workloads.sigma_field(n, seed=wl.seed)
+    b = workloads.source(n, seed=wl.seed, rhs=0)
+    sig_d = torch.from_numpy(sigma[t0 * V:t1 * V].copy()).to(dev)
+    b_d = torch.from_numpy(b[t0 * V:t1 * V].copy()).to(dev)
+    x_d = torch.zeros_like(b_d)
+    per_it = []
+    with Slab(wl.d, wl.nx, wl.ntau, t0, t1, comm=TorchDistComm(group), stream=stream, cg_maxit=maxit) as sl:
+        sl.set_field(sig_d)
+        for k in range(args.warmup + args.steps):
+            barrier(world)
+            torch.cuda.synchronize(dev)
+            w0 = time.perf_counter()
+            rc, info = sl.solve(b_d, x_d, allow=(HH_ENOCONV,))
+            torch.cuda.synchronize(dev)
+            w = time.perf_counter() - w0
+            if k >= args.warmup:
+                per_it.append(w / max(1, info["iterations"]))
+    us_slab = 1e6 * max_over_ranks(world, statistics.median(per_it))
+    us_ctx = None
+    if rank == 0:
+        with Context(wl.d, wl.nx, wl.ntau, cg_maxit=maxit, stream=stream) as ctx:
+            ctx.set_field(torch.from_numpy(sigma).to(dev))
+            bb = torch.from_numpy(b).to(dev).reshape(1, -1)
+            xx = torch.zeros_like(bb)
+            ctx.solve(bb, xx, 1, allow=(HH_ENOCONV,))
+            torch.cuda.synchronize(dev)
+            w0 = time.perf_counter()
+            rc, cinfo = ctx.solve(bb, xx, 1, allow=(HH_ENOCONV,))
+            torch.cuda.synchronize(dev)
+            us_ctx = 1e6 * (time.perf_counter() - w0) / max(1, cinfo["iterations"])
+    line = {"metric": METRIC, "value": us_slab, "unit": "us per CG iteration (wall)", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": us_slab * maxit / 1000.0,
+            "higher_is_better": False, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": dict(config_of(args, wl), mode="slab", step="FP64 CG, one right-hand side, %d iterations" % maxit,
+                           parallelism="tau-slabs%d" % world,
+                           halo="one slice per exchange, host-staged (pinned), gloo between ranks"),
+            "context_solver_us_per_iteration": us_ctx,
+            "slab_iterations": info["iterations"], "e2e": None, "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def default_extras(rank, dev, stream, budget_gb):
     """The spec comparisons, measured in the same run as the headline
     trajectory line: the C2 FP32 M^T M apply (16 vectors per launch, and one),
@@ -783,7 +843,7 @@ def main():
     ap.add_argument("--n-md", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--mode", default="trajectory", choices=["trajectory", "solve", "apply", "batch", "serve"])
+    ap.add_argument("--mode", default="trajectory", choices=["trajectory", "solve", "apply", "batch", "serve", "slab"])
     ap.add_argument("--cg-maxit", type=int, default=1000000)
     ap.add_argument("--cheb", type=int, default=0, help="Chebyshev preconditioner degree n (FP64; solve and trajectory)")
     ap.add_argument("--integrator", default="leapfrog", choices=["leapfrog", "omelyan"])
@@ -829,6 +889,8 @@ def main():
         return run_batch(args, world, rank, local, dev, stream)
     if args.mode == "serve":
         return run_serve(args, world, rank, local, dev, stream)
+    if args.mode == "slab":
+        return run_slab(args, wl, world, rank, local, dev, stream)
     if args.mode != "trajectory":
         return run_part(args, wl, world, rank, local, dev, stream)
     n = wl.nsites

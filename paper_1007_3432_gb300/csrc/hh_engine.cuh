@@ -175,7 +175,8 @@ enum EngKind : int {
 // When the launch starts, the signal slots of every system entering as
 // MODE_NEW must be empty (kSigEmpty), ctl->error must be zero, and ctl->k must
 // hold the iteration counter the state buffers were written at (0 for a fresh
-// plan).  Returns a cudaError_t from the launch.
+// plan).  Launches with more than ENGINE_MAX_SYSTEMS systems are refused
+// (cudaErrorInvalidValue).  Returns a cudaError_t from the launch.
 cudaError_t engine_launch(const EngLaunch &L, int grid, int block, cudaStream_t stream, int kind);
 
 // The engine kernel of a kind, for CUDA-graph kernel nodes.
