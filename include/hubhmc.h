@@ -440,30 +440,42 @@ int hh_batch_autotune(const hh_request *sample, int n, size_t hbm_budget_bytes, 
  * index, so it stays with the rank owning slice N_tau - 1.  Ranks form a ring:
  * the rank owning slice 0 has the rank owning N_tau - 1 as its previous one.
  *
- * The library is communication-agnostic and stages every halo through host
- * memory between kernel launches (no kernel waits for another rank): the
- * caller supplies the two callbacks of hh_comm, called from the calling
- * thread after the slab's stream has been synchronised; they must complete
- * before returning and return 0 on success (any other value: HH_ECUDA).
+ * The library is communication-agnostic: the caller supplies the callbacks
+ * of hh_comm, which move halo slices and sums between kernel launches (no
+ * kernel ever waits for another rank).  Each returns 0 on success (any other
+ * value: HH_ECUDA).  Two forms; a slab uses the device form when both of its
+ * callbacks are set, else the host form:
+ *   host form, called after the slab's stream has been synchronised, on host
+ *   buffers, complete on return:
  *   exchange(user, dir, send, recv, bytes): dir = +1: send the host buffer
  *     send (bytes) to the next rank and receive the previous rank's into recv;
  *     dir = -1: send to the previous rank and receive from the next.  With
  *     one rank, copy send into recv.
  *   allreduce_sum(user, vals, n): replace the n host doubles by their sums
- *     over all ranks. */
+ *     over all ranks.
+ *   device form, on device buffers (the slab's own slices and scalars): the
+ *   callback enqueues the transfer on cuda_stream (the slab's stream) and may
+ *   return before it completes, e.g. NCCL send/recv and all-reduce on that
+ *   stream or peer copies staged into the receiving slab's buffer; the slab
+ *   then runs its CG iterations without synchronising, with the CG scalars on
+ *   the device, and reads them every few iterations to test convergence.
+ *   exchange_device(user, dir, send, recv, bytes, cuda_stream): as exchange.
+ *   allreduce_sum_device(user, vals, n, cuda_stream): as allreduce_sum. */
 typedef struct hh_slab hh_slab;
 
 typedef struct {
     int (*exchange)(void *user, int dir, const void *send, void *recv, size_t bytes);
     int (*allreduce_sum)(void *user, double *vals, int n);
     void *user;
+    int (*exchange_device)(void *user, int dir, const void *send, void *recv, size_t bytes, void *cuda_stream);
+    int (*allreduce_sum_device)(void *user, double *vals, int n, void *cuda_stream);
 } hh_comm;
 
 /* Slab of slices [tau0, tau1) of the lattice lat (FP64 only, link_order 0,
  * no preconditioner).  Allocates the slab's field, links and work vectors on
  * the current device; stream: cudaStream_t (NULL: legacy default stream).
- * Errors: HH_EINVAL (shapes, empty slab, missing callbacks, other precision),
- * HH_ENOMEM, HH_ECUDA. */
+ * Errors: HH_EINVAL (shapes, empty slab, neither callback form complete,
+ * other precision), HH_ENOMEM, HH_ECUDA. */
 int hh_slab_create(hh_slab **out, const hh_lattice *lat, const hh_params *p, int tau0, int tau1,
                    const hh_comm *comm, void *cuda_stream);
 int hh_slab_destroy(hh_slab *s);

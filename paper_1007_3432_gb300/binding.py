@@ -114,8 +114,33 @@ EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctyp
 ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int)
 
 
+EXCHANGE_DEV_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_size_t, ctypes.c_void_p)
+ALLREDUCE_DEV_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p)
+
+
 class hh_comm(ctypes.Structure):
-    _fields_ = [("exchange", EXCHANGE_FN), ("allreduce_sum", ALLREDUCE_FN), ("user", ctypes.c_void_p)]
+    _fields_ = [("exchange", EXCHANGE_FN), ("allreduce_sum", ALLREDUCE_FN), ("user", ctypes.c_void_p),
+                ("exchange_device", EXCHANGE_DEV_FN), ("allreduce_sum_device", ALLREDUCE_DEV_FN)]
+
+
+class _CudaBuffer:
+    """A device buffer given by its address, viewed by torch.as_tensor without
+    a copy (CUDA array interface)."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f8", "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def _device_doubles(ptr, n):
+    import torch
+    return torch.as_tensor(_CudaBuffer(ptr, n), device="cuda")
+
+
+def _stream_of(handle):
+    import torch
+    return torch.cuda.ExternalStream(int(handle)) if handle else torch.cuda.default_stream()
 
 
 HH_REQ_SOLVE, HH_REQ_TRAJECTORY = 0, 1
@@ -534,9 +559,30 @@ class TorchDistComm:
         if self.world > 1:
             self.dist.all_reduce(vals, op=self.dist.ReduceOp.SUM, group=self.group)
 
-    def c_callbacks(self):
+    def device_capable(self):
+        """The device form needs one rank or an NCCL group."""
+        return self.world == 1 or self.dist.get_backend(self.group) == "nccl"
+
+    def exchange_device(self, direction, send, recv):
+        """send, recv: CUDA tensors; enqueued on the current stream."""
+        if self.world == 1:
+            recv.copy_(send, non_blocking=True)
+            return
+        nxt, prv = (self.rank + 1) % self.world, (self.rank - 1) % self.world
+        to, frm = (nxt, prv) if direction > 0 else (prv, nxt)
+        ops = [self.dist.P2POp(self.dist.isend, send, to, self.group),
+               self.dist.P2POp(self.dist.irecv, recv, frm, self.group)]
+        for w in self.dist.batch_isend_irecv(ops):
+            w.wait()   # NCCL: the current stream waits, not the host
+
+    def allreduce_device(self, vals):
+        if self.world > 1:
+            self.dist.all_reduce(vals, op=self.dist.ReduceOp.SUM, group=self.group)
+
+    def c_callbacks(self, device=False):
         """An hh_comm whose callbacks call the methods above (keep the returned
-        object alive while the slab exists)."""
+        object alive while the slab exists); device=True adds the device form
+        (the slab then uses it)."""
         import torch
 
         def _exchange(user, direction, send, recv, nbytes):
@@ -564,17 +610,43 @@ class TorchDistComm:
 
         self._ex = EXCHANGE_FN(_exchange)
         self._ar = ALLREDUCE_FN(_allreduce)
-        return hh_comm(self._ex, self._ar, None)
+        if not device:
+            return hh_comm(self._ex, self._ar, None, EXCHANGE_DEV_FN(), ALLREDUCE_DEV_FN())
+
+        def _exchange_dev(user, direction, send, recv, nbytes, stream):
+            try:
+                n = int(nbytes) // 8
+                with torch.cuda.stream(_stream_of(stream)):
+                    self.exchange_device(int(direction), _device_doubles(send, n), _device_doubles(recv, n))
+                return 0
+            except Exception as e:
+                self.error = e
+                return 1
+
+        def _allreduce_dev(user, vals, n, stream):
+            try:
+                with torch.cuda.stream(_stream_of(stream)):
+                    self.allreduce_device(_device_doubles(vals, n))
+                return 0
+            except Exception as e:
+                self.error = e
+                return 1
+
+        self._exd = EXCHANGE_DEV_FN(_exchange_dev)
+        self._ard = ALLREDUCE_DEV_FN(_allreduce_dev)
+        return hh_comm(self._ex, self._ar, None, self._exd, self._ard)
 
 
 class Slab:
     """The slices [tau0, tau1) of one lattice on this rank (hh_slab_*)."""
 
-    def __init__(self, d, nx, ntau, tau0, tau1, comm=None, stream=None, **prm):
+    def __init__(self, d, nx, ntau, tau0, tau1, comm=None, stream=None, device_comm=False, **prm):
         L = load()
         self._lib = L
         self.comm = comm if comm is not None else TorchDistComm()
-        self._c = self.comm.c_callbacks()
+        if device_comm and not self.comm.device_capable():
+            raise ValueError("the device form of the callbacks needs one rank or an NCCL group")
+        self._c = self.comm.c_callbacks(device=device_comm)
         self.lat = hh_lattice(d, nx, ntau)
         p = make_params(**prm)
         h = ctypes.c_void_p()

@@ -7,12 +7,18 @@
 // sign of the wrap link N_tau - 1 -> 0 is taken from the global slice index, so
 // it stays with the rank that owns slice N_tau - 1.
 //
-// The library is communication-agnostic: the caller supplies two callbacks
-// (hh_comm), one that exchanges a time slice with the neighbouring ranks and
-// one that sums a few doubles over all ranks.  Halo slices are staged through
-// pinned host buffers between launches: the library synchronises its stream,
-// copies the slice to send into host memory, calls the exchange, and copies
-// the received slice back; no kernel ever waits for another rank.
+// The library is communication-agnostic: the caller supplies callbacks
+// (hh_comm) that exchange a time slice with the neighbouring ranks and sum a
+// few doubles over all ranks, between kernel launches; no kernel ever waits
+// for another rank.  Host form: the library synchronises its stream, stages
+// the slice through pinned host memory and calls the exchange; the CG
+// scalars live on the host.  Device form: the callbacks enqueue the transfers
+// on the slab's stream (NCCL or peer copies) straight into the halo slots;
+// the CG scalars (dot products, alpha, beta, convergence) stay on the device,
+// each iteration is a sequence of launches with no synchronisation, and the
+// host reads the scalars every kCheckEvery iterations.
+
+
 //
 // Layout of a slab vector: nl = tau1 - tau0 own slices; the library's device
 // vectors carry nl + 2 slices (halo before, own, halo after), so the standard
@@ -98,6 +104,116 @@ __global__ void k_slab_sub(double *out, const double *a, const double *b, long l
         out[i] = a[i] - b[i];
 }
 
+// CG scalars of the device form.
+struct SlabScalars {
+    double bb, rr, pq, rr_new, tol2;
+    int done;   // the recursive residual met the tolerance: the vector kernels leave the vectors alone
+    int bad;    // a non-finite or non-positive <p, Q p> or |r|^2 was met
+    int it;     // CG iterations run
+};
+
+constexpr int kCheckEvery = 8;   // device form: iterations between host reads of the scalars
+
+// Block sums of a block's values, written to part[blockIdx.x]; the last block
+// to finish adds the partials in block order (so the result does not depend
+// on timing), stores the total in *out and resets the counter.
+__device__ void block_total(double acc, double *part, unsigned *count, double *out)
+{
+    __shared__ double red[kRedBlock];
+    __shared__ bool last;
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = kRedBlock / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = red[0];
+        __threadfence();
+        last = atomicAdd(count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double t = 0.0;
+        for (unsigned j = 0; j < gridDim.x; ++j) t += ((volatile double *)part)[j];
+        *out = t;
+        *count = 0;
+    }
+}
+
+// *out = sum_i a_i b_i over [0, n) (skipped once the solve is done, if sc).
+__global__ void k_dev_dot(const double *a, const double *b, long long n, double *part, unsigned *count, double *out,
+                          const SlabScalars *sc)
+{
+    if (sc && (sc->done || sc->bad)) return;
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc = fma(a[i], b[i], acc);
+    block_total(acc, part, count, out);
+}
+
+// alpha = rr / <p, Q p>; x += alpha p, r -= alpha q; rr_new = |r|^2 (local).
+__global__ void k_dev_update(double *x, const double *p, double *r, const double *q, long long n, SlabScalars *sc,
+                             double *part, unsigned *count)
+{
+    if (sc->done || sc->bad) return;
+    const double pq = sc->pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {   // every block takes this branch alike
+        if (blockIdx.x == 0 && threadIdx.x == 0) sc->bad = 1;
+        return;
+    }
+    const double alpha = sc->rr / pq;
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        acc = fma(ri, ri, acc);
+    }
+    block_total(acc, part, count, &sc->rr_new);
+}
+
+// p = r + (rr_new / rr) p, unless the new residual meets the tolerance.
+__global__ void k_dev_direction(double *p, const double *r, long long n, const SlabScalars *sc)
+{
+    if (sc->done || sc->bad) return;
+    const double rn = sc->rr_new;
+    if (!(rn > sc->tol2) || !isfinite(rn)) return;
+    const double beta = rn / sc->rr;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = fma(beta, p[i], r[i]);
+}
+
+// End of an iteration: rr = rr_new, count it, test the recursive residual.
+__global__ void k_dev_scalars(SlabScalars *sc)
+{
+    if (sc->done || sc->bad) return;
+    sc->it += 1;
+    const double rn = sc->rr_new;
+    if (!isfinite(rn)) {
+        sc->bad = 1;
+        return;
+    }
+    sc->rr = rn;
+    if (rn <= sc->tol2) sc->done = 1;
+}
+
+// Start (or restart from the true residual rr_true = *rr_src): rr, tol2, flags.
+__global__ void k_dev_start(SlabScalars *sc, double tol, int first)
+{
+    if (first) {
+        sc->tol2 = tol * tol * sc->bb;
+        sc->rr = sc->bb;
+        sc->it = 0;
+        sc->done = sc->bb == 0.0 ? 1 : 0;
+    } else {
+        sc->rr = sc->rr_new;
+        sc->done = 0;
+    }
+    sc->bad = 0;
+}
+
 }  // namespace
 
 struct hh_slab {
@@ -114,6 +230,9 @@ struct hh_slab {
     double *part, *dsum;
     double *h_stage;         // pinned: 2 slices (send, receive) + scalars
     int nb;
+    int dev_mode;            // the device form of the callbacks
+    SlabScalars *sc;         // device form: the CG scalars
+    unsigned *count;         // device form: block counter of the last-block sums
 };
 
 namespace {
@@ -137,6 +256,9 @@ int exchange_slice(hh_slab *s, int dir, const double *send_dev, double *recv_dev
 {
     TraceRange tr(dir > 0 ? "hh slab halo +1" : "hh slab halo -1");
     const size_t bytes = sizeof(double) * (size_t)s->V;
+    if (s->dev_mode)   // enqueued on the stream, straight into the halo slot
+        return s->comm.exchange_device(s->comm.user, dir, send_dev, recv_dev, bytes, (void *)s->stream) ? HH_ECUDA
+                                                                                                       : HH_OK;
     double *hs = s->h_stage, *hr = s->h_stage + s->V;
     HS_TRY(cudaMemcpyAsync(hs, send_dev, bytes, cudaMemcpyDeviceToHost, s->stream));
     HS_TRY(cudaStreamSynchronize(s->stream));
@@ -193,7 +315,99 @@ void free_slab(hh_slab *s)
 {
     for (double *p : {s->sigma_ext, s->L_ext, s->xe, s->te, s->pe, s->r, s->q, s->xs, s->part, s->dsum})
         if (p) cudaFree(p);
+    if (s->sc) cudaFree(s->sc);
+    if (s->count) cudaFree(s->count);
     if (s->h_stage) cudaFreeHost(s->h_stage);
+}
+
+// Device form of the CG of hh_slab_solve: no synchronisation inside an
+// iteration; the host reads the scalars every kCheckEvery iterations.
+int slab_solve_device(hh_slab *s, const double *b, double *x, hh_solve_info *info)
+{
+    const size_t V = (size_t)s->V;
+    const long long n = s->own;
+    const int g = s->nb;
+    double *p = s->xe + V;
+    SlabScalars *sc = s->sc;
+    HS_TRY(cudaMemsetAsync(s->xs, 0, sizeof(double) * n, s->stream));
+    HS_TRY(cudaMemcpyAsync(s->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
+    HS_TRY(cudaMemcpyAsync(p, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
+    k_dev_dot<<<g, kRedBlock, 0, s->stream>>>(b, b, n, s->part, s->count, &sc->bb, nullptr);
+    HS_TRY(cudaGetLastError());
+    if (s->comm.allreduce_sum_device(s->comm.user, &sc->bb, 1, (void *)s->stream) != 0) return HH_ECUDA;
+    k_dev_start<<<1, 1, 0, s->stream>>>(sc, s->prm.cg_tol, 1);
+    HS_TRY(cudaGetLastError());
+    SlabScalars *hs = reinterpret_cast<SlabScalars *>(s->h_stage + 2 * V);
+    auto read = [&]() -> int {
+        HS_TRY(cudaMemcpyAsync(hs, sc, sizeof(SlabScalars), cudaMemcpyDeviceToHost, s->stream));
+        HS_TRY(cudaStreamSynchronize(s->stream));
+        return HH_OK;
+    };
+    int rc = read();
+    if (rc) return rc;
+    const double bb = hs->bb;
+    int status = HH_OK, n_true = 0;
+    double true_rel = bb > 0.0 ? 1.0 : 0.0;
+    bool done = bb == 0.0;
+    while (!done) {
+        if (hs->bad) {
+            status = HH_ENUMERIC;
+            break;
+        }
+        if (!hs->done) {
+            if (hs->it >= s->prm.cg_maxit) {
+                status = HH_ENOCONV;
+                break;
+            }
+            const int k = s->prm.cg_maxit - hs->it < kCheckEvery ? s->prm.cg_maxit - hs->it : kCheckEvery;
+            for (int j = 0; j < k; ++j) {
+                rc = slab_apply_ext(s, HH_OP_MTM, s->q);
+                if (rc) return rc;
+                k_dev_dot<<<g, kRedBlock, 0, s->stream>>>(p, s->q, n, s->part, s->count, &sc->pq, sc);
+                if (s->comm.allreduce_sum_device(s->comm.user, &sc->pq, 1, (void *)s->stream) != 0) return HH_ECUDA;
+                k_dev_update<<<g, kRedBlock, 0, s->stream>>>(s->xs, p, s->r, s->q, n, sc, s->part, s->count);
+                if (s->comm.allreduce_sum_device(s->comm.user, &sc->rr_new, 1, (void *)s->stream) != 0)
+                    return HH_ECUDA;
+                k_dev_direction<<<g, kRedBlock, 0, s->stream>>>(p, s->r, n, sc);
+                k_dev_scalars<<<1, 1, 0, s->stream>>>(sc);
+            }
+            HS_TRY(cudaGetLastError());
+            rc = read();
+            if (rc) return rc;
+            continue;
+        }
+        // The recursive residual met the tolerance: confirm with the true
+        // residual b - Q x, and continue from it if it is not met.
+        HS_TRY(cudaMemcpyAsync(s->xe + V, s->xs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
+        rc = slab_apply_ext(s, HH_OP_MTM, s->q);
+        if (rc) return rc;
+        k_slab_sub<<<g, 256, 0, s->stream>>>(s->r, b, s->q, n);
+        k_dev_dot<<<g, kRedBlock, 0, s->stream>>>(s->r, s->r, n, s->part, s->count, &sc->rr_new, nullptr);
+        HS_TRY(cudaGetLastError());
+        if (s->comm.allreduce_sum_device(s->comm.user, &sc->rr_new, 1, (void *)s->stream) != 0) return HH_ECUDA;
+        rc = read();
+        if (rc) return rc;
+        ++n_true;
+        true_rel = std::sqrt(hs->rr_new / bb);
+        if (hs->rr_new <= hs->tol2) {
+            done = true;
+            break;
+        }
+        HS_TRY(cudaMemcpyAsync(p, s->r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
+        k_dev_start<<<1, 1, 0, s->stream>>>(sc, s->prm.cg_tol, 0);
+        HS_TRY(cudaGetLastError());
+        rc = read();
+        if (rc) return rc;
+    }
+    HS_TRY(cudaMemcpyAsync(x, s->xs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
+    HS_TRY(cudaStreamSynchronize(s->stream));
+    if (info) {
+        info->iterations = hs->it;
+        info->reliable_updates = n_true;
+        info->true_relres = true_rel;
+        info->converged = (done && status == HH_OK) ? 1 : 0;
+    }
+    return status;
 }
 
 }  // namespace
@@ -203,7 +417,9 @@ extern "C" {
 int hh_slab_create(hh_slab **out, const hh_lattice *lat, const hh_params *p, int tau0, int tau1,
                    const hh_comm *comm, void *cuda_stream)
 {
-    if (!out || !lat || !p || !comm || !comm->exchange || !comm->allreduce_sum) return HH_EINVAL;
+    if (!out || !lat || !p || !comm) return HH_EINVAL;
+    const bool dev_form = comm->exchange_device && comm->allreduce_sum_device;
+    if (!dev_form && !(comm->exchange && comm->allreduce_sum)) return HH_EINVAL;
     *out = nullptr;
     if (lat->d != 1 && lat->d != 3) return HH_EINVAL;
     if (lat->nx < 2 || lat->ntau < 2 || tau0 < 0 || tau1 > lat->ntau || tau1 - tau0 < 1) return HH_EINVAL;
@@ -226,6 +442,7 @@ int hh_slab_create(hh_slab **out, const hh_lattice *lat, const hh_params *p, int
     s->own = V * s->nl;
     s->gext = make_geo(lat->d, lat->nx, (int)ne);
     s->nb = grid_for(s->own) < 512 ? grid_for(s->own) : 512;
+    s->dev_mode = dev_form ? 1 : 0;
     const size_t ext = (size_t)(V * ne);
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&s->sigma_ext, sizeof(double) * ext);
@@ -238,7 +455,11 @@ int hh_slab_create(hh_slab **out, const hh_lattice *lat, const hh_params *p, int
     if (e == cudaSuccess) e = cudaMalloc(&s->xs, sizeof(double) * s->own);
     if (e == cudaSuccess) e = cudaMalloc(&s->part, sizeof(double) * 512);
     if (e == cudaSuccess) e = cudaMalloc(&s->dsum, sizeof(double) * 8);
-    if (e == cudaSuccess) e = cudaMallocHost(&s->h_stage, sizeof(double) * (2 * (size_t)V + 8));
+    if (e == cudaSuccess) e = cudaMalloc(&s->sc, sizeof(SlabScalars));
+    if (e == cudaSuccess) e = cudaMalloc(&s->count, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->count, 0, sizeof(unsigned), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->sc, 0, sizeof(SlabScalars), s->stream);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_stage, sizeof(double) * (2 * (size_t)V + 16));
     if (e == cudaSuccess) e = cudaMemsetAsync(s->sigma_ext, 0, sizeof(double) * ext, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->xe, 0, sizeof(double) * ext, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->te, 0, sizeof(double) * ext, s->stream);
@@ -293,6 +514,7 @@ int hh_slab_solve(hh_slab *s, const double *b, double *x, hh_solve_info *info)
 {
     TraceRange tr("hh_slab_solve");
     if (!s || !b || !x) return HH_EINVAL;
+    if (s->dev_mode) return slab_solve_device(s, b, x, info);
     const size_t V = (size_t)s->V;
     const long long n = s->own;
     const int g = grid_for(n);

@@ -3,11 +3,12 @@
 Usage: _slab_worker.py comm OUTDIR
          exercise the host-side communication adapter of the slab (exchange of
          a slice with the ring neighbours, sums over ranks), no GPU needed;
-       _slab_worker.py gpu OUTDIR D NX NTAU
+       _slab_worker.py gpu OUTDIR D NX NTAU [device]
          every rank owns its part of the time slices of one lattice (on the
          same GPU when there is one), applies M, M^T and Q to its part of a
          seeded x and solves Q x = b; the parts go to OUTDIR for the test to
-         assemble and check against the oracle.
+         assemble and check against the oracle.  With "device" (one rank)
+         the slab uses the device form of the callbacks.
 """
 import ctypes
 import os
@@ -53,7 +54,7 @@ def comm_check(out):
     dist.destroy_process_group()
 
 
-def gpu_run(out, d, nx, ntau):
+def gpu_run(out, d, nx, ntau, device=False):
     import torch
     import torch.distributed as dist
     import workloads
@@ -71,7 +72,7 @@ def gpu_run(out, d, nx, ntau):
     b = workloads.source(n, seed=702)
     part = slice(V * t0, V * t1)
     res = {"range": np.array([t0, t1])}
-    with Slab(d, nx, ntau, t0, t1) as s:
+    with Slab(d, nx, ntau, t0, t1, device_comm=device) as s:
         s.set_field(sigma[part].copy())
         xd = torch.from_numpy(x[part].copy()).cuda()
         y = torch.empty_like(xd)
@@ -91,4 +92,5 @@ if __name__ == "__main__":
     if sys.argv[1] == "comm":
         comm_check(sys.argv[2])
     else:
-        gpu_run(sys.argv[2], int(sys.argv[3]), int(sys.argv[4]), int(sys.argv[5]))
+        gpu_run(sys.argv[2], int(sys.argv[3]), int(sys.argv[4]), int(sys.argv[5]),
+                device=len(sys.argv) > 6 and sys.argv[6] == "device")

@@ -8,7 +8,9 @@ compared per element with the oracle's applies on the whole lattice (1e-12 of
 the magnitude of the terms), and the assembled CG solution's true residual,
 recomputed by the oracle, must be <= 1e-10.  The wrap link's sign and the
 ring's end (the rank owning slice 0 receives from the rank owning N_tau - 1)
-are covered by every case.
+are covered by every case.  The device form of the callbacks (transfers and
+sums enqueued on the slab's stream, CG scalars on the device) runs with one
+rank: several ranks in that form need one GPU each (NCCL).
 """
 import os
 import socket
@@ -36,15 +38,17 @@ def _free_port():
     return p
 
 
-@pytest.mark.parametrize("world,d,nx,ntau", [(1, 1, 32, 16), (2, 1, 48, 13), (2, 3, 8, 12), (3, 3, 6, 11)])
-def test_slab_apply_and_solve_match_oracle(tmp_path, world, d, nx, ntau):
+@pytest.mark.parametrize("world,d,nx,ntau,form", [(1, 1, 32, 16, "host"), (2, 1, 48, 13, "host"),
+                                                  (2, 3, 8, 12, "host"), (3, 3, 6, 11, "host"),
+                                                  (1, 1, 40, 18, "device"), (1, 3, 8, 10, "device")])
+def test_slab_apply_and_solve_match_oracle(tmp_path, world, d, nx, ntau, form):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1007_3432_gb300 import build
     build.build()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", str(world),
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
-           os.path.join(ROOT, "tests", "_slab_worker.py"), "gpu", str(tmp_path), str(d), str(nx), str(ntau)]
+           os.path.join(ROOT, "tests", "_slab_worker.py"), "gpu", str(tmp_path), str(d), str(nx), str(ntau), form]
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-3000:]
     parts = [np.load(os.path.join(tmp_path, "rank%d.npz" % k)) for k in range(world)]
