@@ -629,12 +629,13 @@ def run_slab(args, wl, world, rank, local, dev, stream):
     b_d = torch.from_numpy(b[t0 * V:t1 * V].copy()).to(dev)
     x_d = torch.zeros_like(b_d)
     forms = {}
+    side = torch.cuda.Stream(dev)   # a stream of its own (the device form replays its iterations as a graph)
     for form in ("host", "device"):
         comm = TorchDistComm(group)
         if form == "device" and not comm.device_capable():
             continue
         per_it = []
-        with Slab(wl.d, wl.nx, wl.ntau, t0, t1, comm=comm, stream=stream, cg_maxit=maxit,
+        with Slab(wl.d, wl.nx, wl.ntau, t0, t1, comm=comm, stream=side, cg_maxit=maxit,
                   device_comm=form == "device") as sl:
             sl.set_field(sig_d)
             for k in range(args.warmup + args.steps):

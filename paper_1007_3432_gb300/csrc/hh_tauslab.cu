@@ -233,6 +233,11 @@ struct hh_slab {
     int dev_mode;            // the device form of the callbacks
     SlabScalars *sc;         // device form: the CG scalars
     unsigned *count;         // device form: block counter of the last-block sums
+    // device form: kCheckEvery iterations as one CUDA graph (captured at the
+    // first full batch; 0 not tried, 1 captured, -1 capture failed: launch
+    // the iterations one by one)
+    int graph_state;
+    cudaGraphExec_t graph;
 };
 
 namespace {
@@ -317,7 +322,57 @@ void free_slab(hh_slab *s)
         if (p) cudaFree(p);
     if (s->sc) cudaFree(s->sc);
     if (s->count) cudaFree(s->count);
+    if (s->graph) cudaGraphExecDestroy(s->graph);
     if (s->h_stage) cudaFreeHost(s->h_stage);
+}
+
+// k iterations of the device-form CG, enqueued on the slab's stream.
+int enqueue_iterations(hh_slab *s, int k)
+{
+    const size_t V = (size_t)s->V;
+    const long long n = s->own;
+    const int g = s->nb;
+    double *p = s->xe + V;
+    SlabScalars *sc = s->sc;
+    for (int j = 0; j < k; ++j) {
+        int rc = slab_apply_ext(s, HH_OP_MTM, s->q);
+        if (rc) return rc;
+        k_dev_dot<<<g, kRedBlock, 0, s->stream>>>(p, s->q, n, s->part, s->count, &sc->pq, sc);
+        if (s->comm.allreduce_sum_device(s->comm.user, &sc->pq, 1, (void *)s->stream) != 0) return HH_ECUDA;
+        k_dev_update<<<g, kRedBlock, 0, s->stream>>>(s->xs, p, s->r, s->q, n, sc, s->part, s->count);
+        if (s->comm.allreduce_sum_device(s->comm.user, &sc->rr_new, 1, (void *)s->stream) != 0) return HH_ECUDA;
+        k_dev_direction<<<g, kRedBlock, 0, s->stream>>>(p, s->r, n, sc);
+        k_dev_scalars<<<1, 1, 0, s->stream>>>(sc);
+    }
+    HS_TRY(cudaGetLastError());
+    return HH_OK;
+}
+
+// A batch of kCheckEvery iterations: replayed from a CUDA graph once one has
+// been captured (the iterations' pointers are fixed per slab and their
+// scalars live on the device, so the graph serves every later batch and
+// solve).  The capture is tried once, on a stream of the caller's (not the
+// legacy default stream); if it fails the iterations are launched directly.
+int run_batch(hh_slab *s)
+{
+    if (s->graph_state == 0 && s->stream != nullptr) {
+        s->graph_state = -1;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+            const int rc = enqueue_iterations(s, kCheckEvery);
+            const cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+            if (rc == HH_OK && e == cudaSuccess && g &&
+                cudaGraphInstantiate(&s->graph, g, 0) == cudaSuccess)
+                s->graph_state = 1;
+            if (g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();
+    }
+    if (s->graph_state == 1) {
+        HS_TRY(cudaGraphLaunch(s->graph, s->stream));
+        return HH_OK;
+    }
+    return enqueue_iterations(s, kCheckEvery);
 }
 
 // Device form of the CG of hh_slab_solve: no synchronisation inside an
@@ -360,18 +415,8 @@ int slab_solve_device(hh_slab *s, const double *b, double *x, hh_solve_info *inf
                 break;
             }
             const int k = s->prm.cg_maxit - hs->it < kCheckEvery ? s->prm.cg_maxit - hs->it : kCheckEvery;
-            for (int j = 0; j < k; ++j) {
-                rc = slab_apply_ext(s, HH_OP_MTM, s->q);
-                if (rc) return rc;
-                k_dev_dot<<<g, kRedBlock, 0, s->stream>>>(p, s->q, n, s->part, s->count, &sc->pq, sc);
-                if (s->comm.allreduce_sum_device(s->comm.user, &sc->pq, 1, (void *)s->stream) != 0) return HH_ECUDA;
-                k_dev_update<<<g, kRedBlock, 0, s->stream>>>(s->xs, p, s->r, s->q, n, sc, s->part, s->count);
-                if (s->comm.allreduce_sum_device(s->comm.user, &sc->rr_new, 1, (void *)s->stream) != 0)
-                    return HH_ECUDA;
-                k_dev_direction<<<g, kRedBlock, 0, s->stream>>>(p, s->r, n, sc);
-                k_dev_scalars<<<1, 1, 0, s->stream>>>(sc);
-            }
-            HS_TRY(cudaGetLastError());
+            rc = k == kCheckEvery ? run_batch(s) : enqueue_iterations(s, k);
+            if (rc) return rc;
             rc = read();
             if (rc) return rc;
             continue;

@@ -72,7 +72,9 @@ def gpu_run(out, d, nx, ntau, device=False):
     b = workloads.source(n, seed=702)
     part = slice(V * t0, V * t1)
     res = {"range": np.array([t0, t1])}
-    with Slab(d, nx, ntau, t0, t1, device_comm=device) as s:
+    # the device form on a stream of its own (its iterations replay as a CUDA graph)
+    stream = torch.cuda.Stream() if device else None
+    with Slab(d, nx, ntau, t0, t1, device_comm=device, stream=stream) as s:
         s.set_field(sigma[part].copy())
         xd = torch.from_numpy(x[part].copy()).cuda()
         y = torch.empty_like(xd)
@@ -81,7 +83,11 @@ def gpu_run(out, d, nx, ntau, device=False):
             res[name] = y.cpu().numpy()
         bd = torch.from_numpy(b[part].copy()).cuda()
         xs = torch.zeros_like(bd)
+        if stream is not None:
+            stream.wait_stream(torch.cuda.current_stream())
         rc, info = s.solve(bd, xs)
+        if stream is not None:
+            torch.cuda.current_stream().wait_stream(stream)
         res["x"] = xs.cpu().numpy()
         res["info"] = np.array([rc, info["iterations"], info["true_relres"], info["converged"]])
     np.savez(os.path.join(out, "rank%d.npz" % r), **res)
