@@ -808,21 +808,23 @@ __device__ double run_slot(const EngSystem &Y, const TileCtl &c, const EngTile &
         if (SLOT == 3) return slot3_ex(Y, c, T);
         return 0.0;
     }
-    // The generic kernel (FD = 0) carries both dimensions' loops; it is
-    // compiled without the prefetches to stay within its registers.  FD = 5
-    // and 7 are the d = 1 and d = 3 kernels whose FP32 steps read 16-bit
-    // links.
+    // The generic kernel (FD = 0) carries both dimensions' loops, with the L2
+    // prefetch in the d = 3 ones only (the d = 1 systems run without it in
+    // every kernel); measured on the 64-chain d = 3 batch forced onto this
+    // kernel, the prefetch takes it from 29.0 to 32.9 mixed solves/s (the
+    // d = 3 kernel: 34.8).  FD = 5 and 7 are the d = 1 and d = 3 kernels
+    // whose FP32 steps read 16-bit links.
     constexpr bool L16 = FD == 5 || FD == 7;
 #define HH_SLOT_CALL(D, W)                                   \
     if (SLOT == 1) {                                         \
-        slot1<D, W, FD != 0>(Y, c, T);                       \
+        slot1<D, W, FD != 0 || D == 3>(Y, c, T);             \
         return 0.0;                                          \
     } else if (SLOT == 2) {                                  \
-        return slot2<D, W, FD != 0, L16>(Y, c, T);           \
+        return slot2<D, W, FD != 0 || D == 3, L16>(Y, c, T); \
     } else if (SLOT == 4) {                                  \
-        return slotA<D, W, FD != 0, L16>(Y, c, T);           \
+        return slotA<D, W, FD != 0 || D == 3, L16>(Y, c, T); \
     } else {                                                 \
-        return slot3<D, W, FD != 0, L16>(Y, c, T);           \
+        return slot3<D, W, FD != 0 || D == 3, L16>(Y, c, T); \
     }
     const int w = Y.w;
     if (FD == 3 || FD == 7 || (FD == 0 && Y.g.d == 3)) {
