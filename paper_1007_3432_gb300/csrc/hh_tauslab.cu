@@ -174,29 +174,39 @@ __global__ void k_dev_update(double *x, const double *p, double *r, const double
     block_total(acc, part, count, &sc->rr_new);
 }
 
-// p = r + (rr_new / rr) p, unless the new residual meets the tolerance.
-__global__ void k_dev_direction(double *p, const double *r, long long n, const SlabScalars *sc)
+// End of an iteration: p = r + (rr_new / rr) p unless the new residual meets
+// the tolerance; then the last block to finish (every block has read the
+// scalars by then) counts the iteration, sets rr = rr_new and tests the
+// recursive residual.
+__global__ void k_dev_direction(double *p, const double *r, long long n, SlabScalars *sc, unsigned *count)
 {
-    if (sc->done || sc->bad) return;
-    const double rn = sc->rr_new;
-    if (!(rn > sc->tol2) || !isfinite(rn)) return;
-    const double beta = rn / sc->rr;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        p[i] = fma(beta, p[i], r[i]);
-}
-
-// End of an iteration: rr = rr_new, count it, test the recursive residual.
-__global__ void k_dev_scalars(SlabScalars *sc)
-{
-    if (sc->done || sc->bad) return;
-    sc->it += 1;
-    const double rn = sc->rr_new;
-    if (!isfinite(rn)) {
-        sc->bad = 1;
-        return;
+    const bool live = !(sc->done || sc->bad);
+    const double rn = sc->rr_new, tol2 = sc->tol2;
+    if (live && rn > tol2 && isfinite(rn)) {
+        const double beta = rn / sc->rr;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x)
+            p[i] = fma(beta, p[i], r[i]);
     }
-    sc->rr = rn;
-    if (rn <= sc->tol2) sc->done = 1;
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        if (live) {
+            sc->it += 1;
+            if (!isfinite(rn)) {
+                sc->bad = 1;
+            } else {
+                sc->rr = rn;
+                if (rn <= tol2) sc->done = 1;
+            }
+        }
+        *count = 0;
+    }
 }
 
 // Start (or restart from the true residual rr_true = *rr_src): rr, tol2, flags.
@@ -226,7 +236,7 @@ struct hh_slab {
     Geo gext;                // the lattice of nl + 2 slices the sweeps run on
     double *sigma_ext, *L_ext;
     double *xe, *te, *pe;    // extended work vectors (nl + 2 slices)
-    double *r, *q, *xs;      // own-slice CG vectors
+    double *r, *q, *xs;      // own-slice CG vectors (q: the own slices of pe, the M^T sweep's output)
     double *part, *dsum;
     double *h_stage;         // pinned: 2 slices (send, receive) + scalars
     int nb;
@@ -312,13 +322,14 @@ int slab_apply_ext(hh_slab *s, int op, double *q_own)
     int rc = exchange_slice(s, -1, s->te + V, s->te + V * (s->nl + 1));
     if (rc) return rc;
     HS_TRY(launch_sweep_f64(s->gext, true, h, s->L_ext, s->te, s->pe, s->stream));
-    HS_TRY(cudaMemcpyAsync(q_own, s->pe + V, sizeof(double) * s->own, cudaMemcpyDeviceToDevice, s->stream));
+    if (q_own != s->pe + V)
+        HS_TRY(cudaMemcpyAsync(q_own, s->pe + V, sizeof(double) * s->own, cudaMemcpyDeviceToDevice, s->stream));
     return HH_OK;
 }
 
 void free_slab(hh_slab *s)
 {
-    for (double *p : {s->sigma_ext, s->L_ext, s->xe, s->te, s->pe, s->r, s->q, s->xs, s->part, s->dsum})
+    for (double *p : {s->sigma_ext, s->L_ext, s->xe, s->te, s->pe, s->r, s->xs, s->part, s->dsum})
         if (p) cudaFree(p);
     if (s->sc) cudaFree(s->sc);
     if (s->count) cudaFree(s->count);
@@ -341,8 +352,7 @@ int enqueue_iterations(hh_slab *s, int k)
         if (s->comm.allreduce_sum_device(s->comm.user, &sc->pq, 1, (void *)s->stream) != 0) return HH_ECUDA;
         k_dev_update<<<g, kRedBlock, 0, s->stream>>>(s->xs, p, s->r, s->q, n, sc, s->part, s->count);
         if (s->comm.allreduce_sum_device(s->comm.user, &sc->rr_new, 1, (void *)s->stream) != 0) return HH_ECUDA;
-        k_dev_direction<<<g, kRedBlock, 0, s->stream>>>(p, s->r, n, sc);
-        k_dev_scalars<<<1, 1, 0, s->stream>>>(sc);
+        k_dev_direction<<<g, kRedBlock, 0, s->stream>>>(p, s->r, n, sc, s->count);
     }
     HS_TRY(cudaGetLastError());
     return HH_OK;
@@ -496,7 +506,7 @@ int hh_slab_create(hh_slab **out, const hh_lattice *lat, const hh_params *p, int
     if (e == cudaSuccess) e = cudaMalloc(&s->te, sizeof(double) * ext);
     if (e == cudaSuccess) e = cudaMalloc(&s->pe, sizeof(double) * ext);
     if (e == cudaSuccess) e = cudaMalloc(&s->r, sizeof(double) * s->own);
-    if (e == cudaSuccess) e = cudaMalloc(&s->q, sizeof(double) * s->own);
+
     if (e == cudaSuccess) e = cudaMalloc(&s->xs, sizeof(double) * s->own);
     if (e == cudaSuccess) e = cudaMalloc(&s->part, sizeof(double) * 512);
     if (e == cudaSuccess) e = cudaMalloc(&s->dsum, sizeof(double) * 8);
@@ -505,6 +515,7 @@ int hh_slab_create(hh_slab **out, const hh_lattice *lat, const hh_params *p, int
     if (e == cudaSuccess) e = cudaMemsetAsync(s->count, 0, sizeof(unsigned), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->sc, 0, sizeof(SlabScalars), s->stream);
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_stage, sizeof(double) * (2 * (size_t)V + 16));
+    if (e == cudaSuccess) s->q = s->pe + V;
     if (e == cudaSuccess) e = cudaMemsetAsync(s->sigma_ext, 0, sizeof(double) * ext, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->xe, 0, sizeof(double) * ext, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->te, 0, sizeof(double) * ext, s->stream);
