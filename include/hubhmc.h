@@ -460,7 +460,12 @@ int hh_batch_autotune(const hh_request *sample, int n, size_t hbm_budget_bytes, 
  *   then runs its CG iterations without synchronising, with the CG scalars on
  *   the device, and reads them every few iterations to test convergence.
  *   exchange_device(user, dir, send, recv, bytes, cuda_stream): as exchange.
- *   allreduce_sum_device(user, vals, n, cuda_stream): as allreduce_sum. */
+ *   allreduce_sum_device(user, vals, n, cuda_stream): as allreduce_sum.
+ *   The slab records its first full batch of iterations into a CUDA graph
+ *   (stream capture of cuda_stream, unless it is the legacy default stream)
+ *   and replays it; a device callback that cannot be captured must return
+ *   non-zero before enqueuing anything when the stream is capturing, and the
+ *   slab then launches its iterations directly. */
 typedef struct hh_slab hh_slab;
 
 typedef struct {

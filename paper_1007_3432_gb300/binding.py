@@ -613,10 +613,18 @@ class TorchDistComm:
         if not device:
             return hh_comm(self._ex, self._ar, None, EXCHANGE_DEV_FN(), ALLREDUCE_DEV_FN())
 
+        # With several ranks the transfers are not captured into the slab's
+        # CUDA graph: a callback refuses before enqueuing anything, on every
+        # rank alike, and the slab then launches its iterations directly.
+        def _refuse_capture():
+            return self.world > 1 and torch.cuda.is_current_stream_capturing()
+
         def _exchange_dev(user, direction, send, recv, nbytes, stream):
             try:
                 n = int(nbytes) // 8
                 with torch.cuda.stream(_stream_of(stream)):
+                    if _refuse_capture():
+                        return 1
                     self.exchange_device(int(direction), _device_doubles(send, n), _device_doubles(recv, n))
                 return 0
             except Exception as e:
@@ -626,6 +634,8 @@ class TorchDistComm:
         def _allreduce_dev(user, vals, n, stream):
             try:
                 with torch.cuda.stream(_stream_of(stream)):
+                    if _refuse_capture():
+                        return 1
                     self.allreduce_device(_device_doubles(vals, n))
                 return 0
             except Exception as e:
