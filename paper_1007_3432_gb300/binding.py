@@ -250,14 +250,46 @@ def _stream_handle(stream):
     return stream.cuda_stream
 
 
+class MetricsLog:
+    """Per-call records as JSON lines (one object per line): solves
+    (iterations, reliable updates, true relative residual), trajectories
+    (H0, dH, u, accept, CG iterations, solves), served results (status,
+    latency, queueing, service) with the queue depth when they were polled.
+    target: a path (appended to) or an open text file."""
+
+    def __init__(self, target):
+        self._own = isinstance(target, (str, os.PathLike))
+        self._f = open(target, "a") if self._own else target
+
+    def write(self, record, **fields):
+        """One line: {"record": record, "time": unix seconds, **fields}."""
+        import json
+        import time
+        rec = {"record": record, "time": time.time()}
+        rec.update(fields)
+        self._f.write(json.dumps(rec) + "\n")
+        self._f.flush()
+
+    def close(self):
+        if self._own and not self._f.closed:
+            self._f.close()
+
+
+def _as_log(log):
+    return log if log is None or isinstance(log, MetricsLog) else MetricsLog(log)
+
+
 class Context:
-    """One lattice and one Markov chain on the current CUDA device."""
+    """One lattice and one Markov chain on the current CUDA device.  log: a
+    MetricsLog (or a path for one) that receives a record per solve, force,
+    action and trajectory."""
 
     def __init__(self, d, nx, ntau, t=1.0, dtau=0.05, A=0.5, precision=HH_FP64, cg_tol=1e-10,
                  cg_maxit=1000000, reliable_delta=0.1, seed=0, n_pf=2, chain_id=0, stream=None,
-                 cheb_degree=0, cheb_eps=1e-3, integrator="leapfrog", chrono=0, link_order=0):
+                 cheb_degree=0, cheb_eps=1e-3, integrator="leapfrog", chrono=0, link_order=0, log=None):
         L = load()
         self._lib = L
+        self.log = _as_log(log)
         self.lat = hh_lattice(d, nx, ntau)
         p = hh_params()
         L.hh_default_params(ctypes.byref(p))
@@ -276,6 +308,11 @@ class Context:
                           _stream_handle(stream)), "hh_create")
         self._h = h
         self.N = int(L.hh_nsites(h))
+
+    def _record(self, record, info, **extra):
+        if self.log is not None and info is not None:
+            self.log.write(record, d=self.lat.d, nx=self.lat.nx, ntau=self.lat.ntau,
+                           precision=int(self.params.precision), **extra, **info)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -331,19 +368,27 @@ class Context:
         fn = self._lib.hh_solve_guess if guess else self._lib.hh_solve
         rc = fn(self._h, _ptr(b), _ptr(x), n_rhs, ctypes.byref(inf) if info else None)
         check(rc, "hh_solve_guess" if guess else "hh_solve", allow)
-        return (rc, inf.as_dict()) if info else rc
+        if not info:
+            return rc
+        out = inf.as_dict()
+        self._record("solve", out, status=rc, n_rhs=n_rhs)
+        return rc, out
 
     def force(self, chi, n_rhs, F, info=True):
         inf = hh_solve_info() if info else None
         rc = self._lib.hh_force(self._h, _ptr(chi), n_rhs, _ptr(F), ctypes.byref(inf) if info else None)
         check(rc, "hh_force")
-        return inf.as_dict() if info else None
+        out = inf.as_dict() if info else None
+        self._record("force", out, n_rhs=n_rhs)
+        return out
 
     def action(self, chi, n_rhs):
         S = ctypes.c_double()
         inf = hh_solve_info()
         check(self._lib.hh_action(self._h, _ptr(chi), n_rhs, ctypes.byref(S), ctypes.byref(inf)), "hh_action")
-        return S.value, inf.as_dict()
+        out = inf.as_dict()
+        self._record("action", out, S=S.value, n_rhs=n_rhs)
+        return S.value, out
 
     def leapfrog(self, pi, chi, n_rhs, n_md, dt, info=True):
         inf = hh_solve_info() if info else None
@@ -356,7 +401,9 @@ class Context:
         inf = hh_traj_info() if info else None
         rc = self._lib.hh_trajectory(self._h, n_md, dt, traj_index, ctypes.byref(inf) if info else None)
         check(rc, "hh_trajectory", allow)
-        return inf.as_dict() if info else None
+        out = inf.as_dict() if info else None
+        self._record("trajectory", out, status=rc, n_md=n_md, dt=dt, traj_index=traj_index)
+        return out
 
     def observables(self, n_noise, traj=0):
         """Noise estimators of diag M^{-1} at the current field (hh_observables)."""
@@ -437,12 +484,15 @@ def make_request(kind, d, nx, ntau, sigma=None, b=None, out=None, n_md=0, dt=0.0
 
 
 class Batch:
-    """Batched multi-chain engine / serving loop (hh_batch_*)."""
+    """Batched multi-chain engine / serving loop (hh_batch_*).  log: a
+    MetricsLog (or a path for one) that receives a record per polled result,
+    with the queue depth (queued and active requests) at that poll."""
 
     def __init__(self, max_slots=64, hbm_budget_bytes=4 << 30, chunk_iters=32, tile_sites=4096,
-                 max_active_sites=0, stream=None):
+                 max_active_sites=0, stream=None, log=None):
         L = load()
         self._lib = L
+        self.log = _as_log(log)
         cfg = hh_batch_config()
         L.hh_batch_default_config(ctypes.byref(cfg))
         cfg.max_slots, cfg.hbm_budget_bytes = max_slots, hbm_budget_bytes
@@ -501,6 +551,10 @@ class Batch:
         out = [arr[j].as_dict() for j in range(n.value)]
         for r in out:
             self._keep.pop(r["ticket"], None)
+        if self.log is not None and out:
+            queued, active = self.pending()
+            for r in out:
+                self.log.write("result", queued=queued, active=active, **r)
         return out
 
     def pending(self):
