@@ -241,6 +241,52 @@ def test_trajectories_match_oracle(hh, precision):
             assert np.max(np.abs(got.cpu().numpy() - s_ref)) <= 1e-6
 
 
+OVL = dict(d=1, nx=128, ntau=96, seed=1013, n_md=4, dt=0.005, trajs=2)
+
+
+@pytest.fixture(scope="module")
+def overlapped_reference():
+    """The oracle's trajectories of the lattice below (about 20 s each)."""
+    lat = oracle.lattice(OVL["d"], OVL["nx"], OVL["ntau"])
+    s = workloads.sigma_field(oracle.nsites(lat), seed=OVL["seed"])
+    prm = oracle.params(seed=OVL["seed"], n_pf=2)
+    out = []
+    for traj in range(OVL["trajs"]):
+        s, oinfo = oracle.trajectory(lat, prm, s, OVL["n_md"], OVL["dt"], traj)
+        out.append((s.copy(), oinfo))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_overlapped_layout_trajectories_match_oracle(hh, monkeypatch, overlapped_reference, precision):
+    """The engine form of the C1 trajectories (every right-hand side tiled
+    over the whole grid, control warp, two-slot iterations), forced onto a
+    d = 1, 128 x 96 lattice that the oracle runs in seconds: identical
+    accept/reject decisions, matching energies and fields over two
+    trajectories."""
+    monkeypatch.setenv("HH_ENGINE_OVERLAP", "1")
+    d, nx, ntau, seed = OVL["d"], OVL["nx"], OVL["ntau"], OVL["seed"]
+    n = nx * ntau
+    sigma = workloads.sigma_field(n, seed=seed)
+    n_md, dt = OVL["n_md"], OVL["dt"]
+    with hh.Context(d, nx, ntau, seed=seed, n_pf=2, precision=precision) as ctx:
+        ctx.set_field(dev(sigma))
+        for traj in range(OVL["trajs"]):
+            info = ctx.trajectory(n_md, dt, traj)
+            s_ref, oinfo = overlapped_reference[traj]
+            assert info["n_solves"] == 2 * (n_md + 1) and info["max_true_relres"] <= 1e-10
+            assert info["u"] == oinfo["u"]
+            assert abs(info["H0"] - oinfo["H0"]) <= 1e-8 * abs(oinfo["H0"])
+            assert abs(info["dH"] - oinfo["dH"]) <= 1e-6 + 1e-9 * abs(oinfo["H0"]), (info, oinfo)
+            if abs(oinfo["dH"] + np.log(oinfo["u"])) > 1e-5:
+                assert info["accepted"] == oinfo["accepted"]
+            if info["accepted"] != oinfo["accepted"]:
+                break
+            got = torch.empty(n, dtype=torch.float64, device="cuda")
+            ctx.get_field(got)
+            assert np.max(np.abs(got.cpu().numpy() - s_ref)) <= 1e-6
+
+
 def test_leapfrog_reversible_on_gpu(hh):
     d, nx, ntau = 1, 16, 16
     n = nx * ntau
